@@ -1,0 +1,550 @@
+"""Seeded BGP workloads drawn from concrete instances of a synthetic graph.
+
+A BGP is a list of triple patterns (s, p, o) whose subject and object are
+either variables or constants; the predicate is always a constant, because
+the method assumes known predicates (Sec. 6.3).  Every query is read off a
+concrete subgraph instance of the graph (a walk, a star, a snowflake or a
+closed walk), so its result is never empty; a constant, when a query has
+one, is that instance's value at the replaced position.
+
+Size control: for each query the generator computes an upper bound on the
+number of rows that any connected sub-pattern can produce (a walk-count
+dynamic program over a spanning forest of the sub-pattern; dropped cycle
+edges and dropped membership tests only loosen the bound) and redraws the
+query when the bound exceeds the configuration's row limit.  This keeps
+every intermediate table of every join order within the limit, independent
+of the planner.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import itertools
+
+import numpy as np
+
+from .graphs import CONFIGS, GraphConfig, make_graph
+
+
+@dataclasses.dataclass
+class BGP:
+    """A basic graph pattern.
+
+    ``patterns`` holds tuples (s, p, o, s_is_var, o_is_var); a variable end
+    stores its variable number in 0..n_vars-1, a constant end stores an
+    entity id.  ``p`` is a predicate id.
+    """
+
+    patterns: list
+    n_vars: int
+    shape: str = ""
+    name: str = ""
+
+    def as_array(self) -> np.ndarray:
+        """(n_patterns, 6) int64 array: s, p, o, s_var, p_var(0), o_var."""
+        rows = [(s, p, o, int(sv), 0, int(ov)) for (s, p, o, sv, ov) in self.patterns]
+        return np.asarray(rows, dtype=np.int64).reshape(-1, 6)
+
+    def permuted(self, order) -> "BGP":
+        return BGP([self.patterns[i] for i in order], self.n_vars, self.shape, self.name)
+
+
+# ----------------------------------------------------------------------------
+# adjacency used for sampling instances
+
+
+class _Adjacency:
+    def __init__(self, triples: np.ndarray, n_entities: int):
+        t = np.asarray(triples)
+        self.s = t[:, 0].astype(np.int64)
+        self.p = t[:, 1].astype(np.int64)
+        self.o = t[:, 2].astype(np.int64)
+        self.n = t.shape[0]
+        self.E = int(max(n_entities, int(t[:, [0, 2]].max()) + 1))
+        self.by_s = np.argsort(self.s, kind="stable")
+        self.by_o = np.argsort(self.o, kind="stable")
+        self.s_ptr = np.searchsorted(self.s[self.by_s], np.arange(self.E + 1))
+        self.o_ptr = np.searchsorted(self.o[self.by_o], np.arange(self.E + 1))
+        # pair keys for adjacency tests in any orientation
+        pair = self.s * self.E + self.o
+        self.pair_sorted = np.sort(pair)
+        self.preds = np.unique(self.p)
+
+    def out_deg(self, v):
+        return self.s_ptr[np.asarray(v) + 1] - self.s_ptr[np.asarray(v)]
+
+    def in_deg(self, v):
+        return self.o_ptr[np.asarray(v) + 1] - self.o_ptr[np.asarray(v)]
+
+    def random_incident(self, rng, v, direction=None):
+        """A random triple index incident to entity v; direction 'out', 'in'
+        or None (either, proportional to degree).  Returns (idx, dir) or
+        (None, None) when v has no such edge."""
+        od, idg = int(self.out_deg(v)), int(self.in_deg(v))
+        if direction == "out":
+            idg = 0
+        elif direction == "in":
+            od = 0
+        tot = od + idg
+        if tot == 0:
+            return None, None
+        r = int(rng.integers(tot))
+        if r < od:
+            return int(self.by_s[self.s_ptr[v] + r]), "out"
+        return int(self.by_o[self.o_ptr[v] + r - od]), "in"
+
+    def has_pair(self, a, b):
+        """Vectorised: is there a triple a->b (any predicate)?"""
+        key = np.asarray(a, dtype=np.int64) * self.E + np.asarray(b, dtype=np.int64)
+        pos = np.searchsorted(self.pair_sorted, key)
+        pos = np.minimum(pos, self.pair_sorted.size - 1)
+        return self.pair_sorted[pos] == key
+
+    def find_pair(self, rng, a, b):
+        """A random triple index with s=a, o=b, or None."""
+        lo, hi = self.s_ptr[a], self.s_ptr[a + 1]
+        idx = self.by_s[lo:hi]
+        hit = idx[self.o[idx] == b]
+        if hit.size == 0:
+            return None
+        return int(hit[rng.integers(hit.size)])
+
+
+# ----------------------------------------------------------------------------
+# instance templates: each returns a list of (subject_slot, triple_idx,
+# object_slot) "edges" over instance slots plus slot -> entity values
+
+
+def _inst_chain(adj, rng, hops):
+    for _ in range(1000):
+        t = int(rng.integers(adj.n))
+        vals = [int(adj.s[t]), int(adj.o[t])]
+        edges = [(0, t, 1)]
+        ok = True
+        for h in range(1, hops):
+            cur = vals[-1]
+            idx, d = adj.random_incident(rng, cur)
+            if idx is None:
+                ok = False
+                break
+            nxt_slot = len(vals)
+            if d == "out":
+                vals.append(int(adj.o[idx]))
+                edges.append((h, idx, nxt_slot))
+            else:
+                vals.append(int(adj.s[idx]))
+                edges.append((nxt_slot, idx, h))
+        if ok:
+            return edges, vals
+    raise RuntimeError("could not sample a chain")
+
+
+def _inst_star(adj, rng, k):
+    for _ in range(1000):
+        t = int(rng.integers(adj.n))
+        x = int(adj.s[t])
+        vals = [x]
+        edges = []
+        for _i in range(k):
+            idx, _ = adj.random_incident(rng, x, "out")
+            vals.append(int(adj.o[idx]))
+            edges.append((0, idx, len(vals) - 1))
+        return edges, vals
+    raise RuntimeError("could not sample a star")
+
+
+def _inst_snowflake(adj, rng, n_pat):
+    # centre with a arms; 1-2 arm ends carry their own out-stars
+    for _ in range(1000):
+        t = int(rng.integers(adj.n))
+        x = int(adj.s[t])
+        n_arms = int(rng.integers(2, max(3, n_pat - 1)))
+        n_arms = min(n_arms, n_pat - 1)
+        vals = [x]
+        edges = []
+        for _i in range(n_arms):
+            idx, _ = adj.random_incident(rng, x, "out")
+            vals.append(int(adj.o[idx]))
+            edges.append((0, idx, len(vals) - 1))
+        rest = n_pat - n_arms
+        arm_slots = list(range(1, n_arms + 1))
+        rng.shuffle(arm_slots)
+        ok = True
+        j = 0
+        while rest > 0:
+            slot = arm_slots[j % len(arm_slots)]
+            idx, _ = adj.random_incident(rng, vals[slot], "out")
+            if idx is None:
+                j += 1
+                if j > 4 * len(arm_slots):
+                    ok = False
+                    break
+                continue
+            vals.append(int(adj.o[idx]))
+            edges.append((slot, idx, len(vals) - 1))
+            rest -= 1
+        if ok and len(edges) == n_pat:
+            return edges, vals
+    raise RuntimeError("could not sample a snowflake")
+
+
+def _inst_cycle(adj, rng, length):
+    """A closed walk a0 - a1 - ... - a_{L-1} - a0, edges in any orientation."""
+    batch = 4096
+    for _ in range(200):
+        t = rng.integers(adj.n, size=batch)
+        path = [adj.s[t], adj.o[t]]
+        for _h in range(length - 2):
+            cur = path[-1]
+            od = adj.out_deg(cur)
+            idg = adj.in_deg(cur)
+            tot = od + idg
+            good = tot > 0
+            r = (rng.random(batch) * np.maximum(tot, 1)).astype(np.int64)
+            out_pick = r < od
+            nxt = np.where(
+                out_pick,
+                adj.o[adj.by_s[np.minimum(adj.s_ptr[cur] + r, adj.n - 1)]],
+                adj.s[adj.by_o[np.minimum(adj.o_ptr[cur] + np.maximum(r - od, 0), adj.n - 1)]],
+            )
+            nxt = np.where(good, nxt, -1)
+            path.append(nxt)
+        last, first = path[-1], path[0]
+        valid = last >= 0
+        closes = valid & (adj.has_pair(np.maximum(last, 0), first) | adj.has_pair(first, np.maximum(last, 0)))
+        # prefer closed walks over distinct vertices
+        P = np.stack(path, axis=1)
+        distinct = np.array([len(set(row.tolist())) == length for row in P]) if closes.any() else closes
+        cand = np.flatnonzero(closes & distinct)
+        if cand.size == 0:
+            cand = np.flatnonzero(closes)
+        if cand.size == 0:
+            continue
+        row = P[int(cand[rng.integers(cand.size)])]
+        vals = [int(v) for v in row]
+        edges = []
+        for h in range(length):
+            a, b = vals[h], vals[(h + 1) % length]
+            idx = adj.find_pair(rng, a, b)
+            if idx is not None and (h > 0 or True):
+                edges.append((h, idx, (h + 1) % length))
+                continue
+            idx = adj.find_pair(rng, b, a)
+            if idx is None:
+                break
+            edges.append(((h + 1) % length, idx, h))
+        if len(edges) == length:
+            return edges, vals
+    raise RuntimeError("could not sample a cycle")
+
+
+# ----------------------------------------------------------------------------
+# size bound
+
+
+class _BoundIndex:
+    """Per-predicate sparse 0/1 matrices for the walk-count bound."""
+
+    def __init__(self, triples, n_entities):
+        import scipy.sparse as sp
+
+        t = np.asarray(triples)
+        self.E = int(max(n_entities, int(t[:, [0, 2]].max()) + 1))
+        self.mats = {}
+        self.outdeg = {}
+        self.indeg = {}
+        order = np.argsort(t[:, 1], kind="stable")
+        ps = t[order, 1]
+        cuts = np.flatnonzero(np.diff(ps)) + 1
+        for seg in np.split(order, cuts):
+            if seg.size == 0:
+                continue
+            p = int(t[seg[0], 1])
+            s = t[seg, 0].astype(np.int64)
+            o = t[seg, 2].astype(np.int64)
+            m = sp.csr_matrix((np.ones(seg.size), (s, o)), shape=(self.E, self.E))
+            self.mats[p] = m
+            self.outdeg[p] = np.bincount(s, minlength=self.E).astype(np.float64)
+            self.indeg[p] = np.bincount(o, minlength=self.E).astype(np.float64)
+        self._mt = {}
+
+    def mat_t(self, p):
+        if p not in self._mt:
+            self._mt[p] = self.mats[p].T.tocsr()
+        return self._mt[p]
+
+
+def _component_bound(bi: _BoundIndex, pats, var_set):
+    """Upper bound on the rows of the sub-BGP ``pats`` (all vars in var_set
+    connected through pats)."""
+    E = bi.E
+    unary = {}
+    adj = {v: [] for v in var_set}
+    parent = {v: v for v in var_set}
+
+    def find(v):
+        while parent[v] != v:
+            parent[v] = parent[parent[v]]
+            v = parent[v]
+        return v
+
+    def mul_unary(v, vec):
+        unary[v] = vec if v not in unary else unary[v] * vec
+
+    for (s, p, o, sv, ov) in pats:
+        if p not in bi.mats:
+            return 0.0
+        m = bi.mats[p]
+        if sv and ov:
+            if s == o:
+                mul_unary(s, m.diagonal().astype(np.float64))
+            else:
+                rs, ro = find(s), find(o)
+                if rs != ro:
+                    parent[rs] = ro
+                    adj[s].append((o, p, "out"))  # s -p-> o
+                    adj[o].append((s, p, "in"))
+                # else: a cycle edge; dropping it keeps an upper bound
+        elif sv:
+            col = np.zeros(E)
+            if 0 <= o < E:
+                mt = bi.mat_t(p)
+                col[mt.indices[mt.indptr[o]:mt.indptr[o + 1]]] = 1.0
+            mul_unary(s, col)
+        elif ov:
+            row = np.zeros(E)
+            if 0 <= s < E:
+                row[m.indices[m.indptr[s]:m.indptr[s + 1]]] = 1.0
+            mul_unary(o, row)
+    # root: the variable with the most tree edges
+    root = max(var_set, key=lambda v: len(adj[v]))
+
+    def f(v, par):
+        vec = unary.get(v)
+        for (c, p, d) in adj[v]:
+            if c == par:
+                continue
+            fc = f(c, v)
+            if fc is None:
+                msg = bi.outdeg[p] if d == "out" else bi.indeg[p]
+            else:
+                msg = (bi.mats[p] @ fc) if d == "out" else (bi.mat_t(p) @ fc)
+            vec = msg if vec is None else vec * msg
+        return vec
+
+    top = f(root, None)
+    return float(E) if top is None else float(top.sum())
+
+
+def _pattern_vars(pt):
+    s, p, o, sv, ov = pt
+    vs = set()
+    if sv:
+        vs.add(s)
+    if ov:
+        vs.add(o)
+    return vs
+
+
+def _connected(pats):
+    if not pats:
+        return True
+    seen_vars = set(_pattern_vars(pats[0]))
+    left = list(pats[1:])
+    changed = True
+    while left and changed:
+        changed = False
+        for pt in list(left):
+            vs = _pattern_vars(pt)
+            if vs & seen_vars:
+                seen_vars |= vs
+                left.remove(pt)
+                changed = True
+    return not left
+
+
+def _components(pats):
+    comps = []
+    for i, pt in enumerate(pats):
+        vs = _pattern_vars(pt)
+        merged = [c for c in comps if c[1] & vs]
+        new = ([i], set(vs))
+        for c in merged:
+            comps.remove(c)
+            new = (new[0] + c[0], new[1] | c[1])
+        comps.append(new)
+    return comps
+
+
+def bgp_row_bound(bi: _BoundIndex, bgp: BGP, limit: float = float("inf")) -> float:
+    """Max over join prefixes any planner may build: for every connected
+    subset S of one component, bound(S) times the full bounds of the other
+    components.  Returns early with a value above ``limit`` as soon as one
+    subset exceeds it."""
+    comps = _components(bgp.patterns)
+    full = []
+    sub_max = []
+    for idx, vars_ in comps:
+        pats = [bgp.patterns[i] for i in idx]
+        best = 0.0
+        full_b = None
+        for r in range(1, len(pats) + 1):
+            for sub in itertools.combinations(range(len(pats)), r):
+                sp_ = [pats[i] for i in sub]
+                if not _connected(sp_):
+                    continue
+                vs = set().union(*[_pattern_vars(x) for x in sp_])
+                if not vs:
+                    b = 1.0
+                else:
+                    b = _component_bound(bi, sp_, vs)
+                if b > limit:
+                    return b
+                best = max(best, b)
+                if r == len(pats):
+                    full_b = b
+        full.append(full_b if full_b is not None else best)
+        sub_max.append(best)
+    worst = 0.0
+    for i in range(len(comps)):
+        prod = sub_max[i]
+        for j in range(len(comps)):
+            if j != i:
+                prod *= max(full[j], 1.0)
+        worst = max(worst, prod)
+    return worst
+
+
+# ----------------------------------------------------------------------------
+# instance -> BGP
+
+
+def _to_bgp(adj, edges, vals, const_slot, shape):
+    """Convert instance edges over slots into patterns; slot const_slot (or
+    None) becomes a constant, other slots become variables numbered by first
+    appearance."""
+    var_of = {}
+    pats = []
+    for (a, t, b) in edges:
+        p = int(adj.p[t])
+        ends = []
+        for slot in (a, b):
+            if slot == const_slot:
+                ends.append((vals[slot], False))
+            else:
+                if slot not in var_of:
+                    var_of[slot] = len(var_of)
+                ends.append((var_of[slot], True))
+        pats.append((ends[0][0], p, ends[1][0], ends[0][1], ends[1][1]))
+    return BGP(pats, len(var_of), shape)
+
+
+_SHAPES = {
+    "chain": _inst_chain,
+    "star": _inst_star,
+    "snowflake": _inst_snowflake,
+    "cycle": _inst_cycle,
+}
+
+
+def _draw(adj, bi, rng, shape, n_pat, p_const, limit, max_tries=400):
+    last = None
+    for attempt in range(max_tries):
+        edges, vals = _SHAPES[shape](adj, rng, n_pat)
+        n_slots = len(vals)
+        # later attempts force a constant: unselective draws are the ones
+        # rejected by the bound
+        use_const = rng.random() < p_const or attempt >= max_tries // 4
+        const_slot = int(rng.integers(n_slots)) if use_const else None
+        bgp = _to_bgp(adj, edges, vals, const_slot, shape)
+        if bgp.n_vars == 0:
+            continue
+        b = bgp_row_bound(bi, bgp, limit)
+        last = (bgp, b)
+        if b <= limit:
+            bgp.bound = b
+            return bgp
+    raise RuntimeError(f"no {shape}/{n_pat} query within {limit} rows (last bound {last[1] if last else None})")
+
+
+_PLANS = {
+    # (shape, n_patterns) per query
+    "tiny": [("chain", 2), ("chain", 3), ("star", 3), ("chain", 2), ("chain", 3),
+             ("star", 3), ("chain", 2), ("chain", 3), ("star", 3), ("cycle", 3)],
+}
+
+_LIMITS = {"tiny": 2_000_000, "medium": 100_000_000, "large": 1_000_000_000}
+_PCONST = {"tiny": 0.5, "medium": 0.5, "large": 0.3}
+
+_INDEX_CACHE: dict = {}
+
+
+def _indexes(cfg, triples):
+    key = (cfg.name, id(triples))
+    if key not in _INDEX_CACHE:
+        _INDEX_CACHE.clear()
+        _INDEX_CACHE[key] = (_Adjacency(triples, cfg.n_entities), _BoundIndex(triples, cfg.n_entities))
+    return _INDEX_CACHE[key]
+
+
+def _plan_for(cfg: GraphConfig, rng):
+    if cfg.name in _PLANS:
+        return _PLANS[cfg.name]
+    if cfg.name == "medium":
+        plan = []
+        for i in range(39):
+            shape = ("star", "chain", "snowflake")[i % 3]
+            lo = 4 if shape == "snowflake" else 3
+            plan.append((shape, int(rng.integers(lo, 7))))
+        plan.insert(int(rng.integers(40)), ("cycle", 4))
+        return plan
+    if cfg.name == "large":
+        plan = []
+        for i in range(20):
+            shape = ("star", "chain", "snowflake", "star", "chain")[i % 5]
+            plan.append((shape, int(rng.integers(4, 9))))
+        return plan
+    raise ValueError(cfg.name)
+
+
+def make_queries(cfg: GraphConfig | str, triples: np.ndarray | None = None, seed: int | None = None):
+    """The configuration's BGP workload (list of BGP)."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    if triples is None:
+        triples = make_graph(cfg)
+    seed = cfg.query_seed if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed))
+    adj, bi = _indexes(cfg, triples)
+    out = []
+    for qi, (shape, n_pat) in enumerate(_plan_for(cfg, rng)):
+        bgp = _draw(adj, bi, rng, shape, n_pat, _PCONST[cfg.name], _LIMITS[cfg.name])
+        bgp.name = f"{cfg.name}-q{qi:02d}-{shape}{n_pat}"
+        out.append(bgp)
+    return out
+
+
+def make_batched_queries(n_queries: int = 4096, triples: np.ndarray | None = None, seed: int = 7691 + 3,
+                         limit: int = 1_000_000):
+    """Mixed workload over the medium graph: 2-8 patterns, shapes
+    star:chain:snowflake:cycle = 4:3:2:1, a mix of constant and
+    constant-free queries."""
+    cfg = CONFIGS["medium"]
+    if triples is None:
+        triples = make_graph(cfg)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    adj, bi = _indexes(cfg, triples)
+    shapes = ["star"] * 4 + ["chain"] * 3 + ["snowflake"] * 2 + ["cycle"]
+    out = []
+    for qi in range(n_queries):
+        shape = shapes[int(rng.integers(len(shapes)))]
+        if shape == "cycle":
+            n_pat = int(rng.integers(3, 5))
+        elif shape == "snowflake":
+            n_pat = int(rng.integers(3, 9))
+        else:
+            n_pat = int(rng.integers(2, 9))
+        bgp = _draw(adj, bi, rng, shape, n_pat, 0.5, limit)
+        bgp.name = f"batched-q{qi:04d}-{shape}{n_pat}"
+        out.append(bgp)
+    return out

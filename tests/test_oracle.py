@@ -1,0 +1,286 @@
+"""Pins of the oracle against what the paper and mathematics fix (CPU only).
+
+Each test names the passage it checks.  The oracle is compared with worked
+examples printed in the paper, brute-force enumeration, a matrix-product
+closed form and invariants; never with itself.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import planner, storage
+from tests.helpers import brute_force, golden, is_sorted_unique, random_bgp, satisfies_all
+
+
+# --------------------------------------------------------------------------
+# Worked example D_G (Sec. 3.1, 5.2, 5.3, 6.3)
+
+
+def test_dg_answer_is_the_papers_single_row():
+    g = golden("dg_example.json")
+    ix = oracle.OracleIndex(np.array(g["cube_spo"]))
+    rows = ix.query(g["query"], 4)
+    assert rows.tolist() == g["answer_xyzw"]
+    # the paper prints it over (X, W, Z, Y)
+    x, y, z, w = rows[0]
+    assert [x, w, z, y] == g["answer_XWZY"]
+
+
+def test_dg_intermediate_rows_in_paper_plan_order():
+    g = golden("dg_example.json")
+    ix = oracle.OracleIndex(np.array(g["cube_spo"]))
+    q = [g["query"][i] for i in g["plan_order"]]
+    rows, steps = ix.query(q, 4, return_steps=True)
+    assert steps.tolist() == g["plan_step_rows"]
+
+
+def test_dg_matrices_and_statistics():
+    g = golden("dg_example.json")
+    mats = storage.sparse_matrices(np.array(g["cube_spo"]))
+    assert {str(k): v.tolist() for k, v in mats.items()} == g["matrices"]
+    stats = storage.statistics(np.array(g["cube_spo"]))
+    assert [stats[h]["nnz"] for h in (1, 2, 3)] == [3, 4, 2]
+    # Sec. 5.3: 9 pairs = 18 units against 7*7*3 = 147 for adjacency storage
+    assert sum(2 * s["nnz"] for s in stats.values()) == g["storage_units"]["sm_units"]
+    assert len(g["h_so"]) * len(g["h_so"]) * len(g["h_p"]) == g["storage_units"]["adjacency_units"]
+
+
+def test_dg_auxiliary_arrays():
+    g = golden("dg_example.json")
+    M1 = storage.sparse_matrices(np.array(g["cube_spo"]))[1]
+    assert storage.aux_arrays(M1, 0).tolist() == g["aux_A_X"]
+    assert g["aux_B_W_entry"] in storage.aux_arrays(M1, 1).tolist()
+
+
+def test_dg_first_intermediate_row():
+    g = golden("dg_example.json")
+    ix = oracle.OracleIndex(np.array(g["cube_spo"]))
+    # ?X likes ?W . ?Z likes ?W over variables X=0, W=1, Z=2
+    rows = ix.query([(0, 1, 1, 1, 1), (2, 1, 1, 1, 1)], 3)
+    assert g["first_C_row_XWZ"] == rows[0].tolist()
+
+
+def test_dg_plan_order_matches_bgp_sequence():
+    g = golden("dg_example.json")
+    cube = np.array(g["cube_spo"])
+    stats = storage.statistics(cube)
+    keys = [stats[p[1]]["nnz"] for p in g["query"]]
+    assert planner.plan_order(g["query"], keys) == g["plan_order"]
+
+
+# --------------------------------------------------------------------------
+# Join without accumulation (Sec. 6.1)
+
+
+def test_spgemm_example_join_keeps_all_columns():
+    g = golden("spgemm_example.json")
+    L = g["letters"]
+    A, B = 10, 11
+    trip = [(L[a], A, L[b]) for a, b in g["A"]] + [(L[a], B, L[b]) for a, b in g["B"]]
+    rows = oracle.oracle_query(np.array(trip), [(0, A, 1, 1, 1), (1, B, 2, 1, 1)], 3)
+    want = sorted([L[a], L[b], L[c]] for a, b, c in g["join_rows"])
+    assert rows.tolist() == want
+    # accumulated value c_it = 2 appears as two distinct rows (i,k,t), (i,l,t)
+    for a, c, v in g["C_product"]:
+        n = sum(1 for r in rows.tolist() if r[0] == L[a] and r[2] == L[c])
+        assert n == v
+
+
+def _adj(triples, p, n):
+    M = np.zeros((n, n), dtype=np.int64)
+    for s, pp, o in np.asarray(triples).tolist():
+        if pp == p:
+            M[s, o] = 1
+    return M
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_chain_counts_equal_boolean_matrix_product(seed):
+    """For ?x p1 ?y . ?y p2 ?z, the number of rows with given (x, z) is
+    (A1 A2)[x, z] (Sec. 6.1: the join is the product without accumulation)."""
+    n = 9
+    t = synth.small_random_graph(n, 3, 60, seed=seed)
+    p1, p2 = 0, (seed % 3)
+    rows = oracle.oracle_query(t, [(0, p1, 1, 1, 1), (1, p2, 2, 1, 1)], 3)
+    C = _adj(t, p1, n) @ _adj(t, p2, n)
+    got = np.zeros((n, n), dtype=np.int64)
+    for x, y, z in rows.tolist():
+        got[x, z] += 1
+    assert (got == C).all()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_star_counts_equal_degree_products(seed):
+    """A constant-free star ?x p_i ?y_i has sum_x prod_i deg_{p_i}(x) rows."""
+    n = 10
+    t = synth.small_random_graph(n, 3, 80, seed=100 + seed)
+    ps = [seed % 3, (seed + 1) % 3, 0]
+    rows = oracle.oracle_query(t, [(0, p, i + 1, 1, 1) for i, p in enumerate(ps)], 4)
+    deg = [_adj(t, p, n).sum(axis=1) for p in ps]
+    assert rows.shape[0] == int(np.prod(deg, axis=0).sum())
+
+
+# --------------------------------------------------------------------------
+# Brute force on tiny graphs
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n_ent = int(rng.integers(3, 9))
+    t = synth.small_random_graph(n_ent, 3, int(rng.integers(5, 40)), seed=seed, pred_ids=np.array([5, 9, 1000]))
+    pats, V = random_bgp(rng, t, n_vars_max=4, n_pats_max=5)
+    want = brute_force(t, pats, V)
+    got = oracle.oracle_query(t, pats, V)
+    assert got.shape == want.shape
+    assert (got == want).all()
+
+
+def test_duplicate_input_triples_are_one_triple():
+    t = np.array([(1, 7, 2), (1, 7, 2), (2, 7, 3), (1, 7, 2)])
+    rows = oracle.oracle_query(t, [(0, 7, 1, 1, 1)], 2)
+    assert rows.tolist() == [[1, 2], [2, 3]]
+
+
+def test_edge_cases():
+    t = np.array([(1, 7, 2), (2, 7, 3), (3, 7, 3), (2, 8, 1)])
+    ix = oracle.OracleIndex(t)
+    # repeated variable
+    assert ix.query([(0, 7, 0, 1, 1)], 1).tolist() == [[3]]
+    # both ends constant: present / absent
+    assert ix.query([(1, 7, 2, 0, 0), (0, 7, 1, 1, 1)], 2).shape == (3, 2)
+    assert ix.query([(1, 7, 3, 0, 0), (0, 7, 1, 1, 1)], 2).shape == (0, 2)
+    # absent predicate: empty, not an error
+    assert ix.query([(0, 99, 1, 1, 1)], 2).shape == (0, 2)
+    # disconnected: Cartesian product
+    assert ix.query([(0, 7, 1, 1, 1), (2, 8, 3, 1, 1)], 4).shape == (3, 4)
+    # no variables at all
+    assert ix.query([(1, 7, 2, 0, 0)], 0).shape == (1, 0)
+    assert ix.query([(1, 7, 9, 0, 0)], 0).shape == (0, 0)
+    # variable predicate is unsupported (Sec. 6.3 assumes known predicates)
+    with pytest.raises(oracle.OracleError) as e:
+        ix.query(np.array([[0, 0, 1, 1, 1, 1]]), 2)
+    assert e.value.code == 2
+    # a declared variable that no pattern uses is invalid
+    with pytest.raises(oracle.OracleError):
+        ix.query([(0, 7, 1, 1, 1)], 3)
+
+
+# --------------------------------------------------------------------------
+# Invariants on the tiny workload
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    t = synth.make_graph("tiny")
+    return t, oracle.OracleIndex(t), synth.make_queries("tiny", t)
+
+
+def test_tiny_workload_invariants(tiny):
+    t, ix, qs = tiny
+    for q in qs:
+        rows = ix.query(q)
+        assert rows.shape[0] > 0, q.name  # drawn from an instance
+        assert is_sorted_unique(rows)
+        assert satisfies_all(t, q.patterns, rows)
+
+
+def test_tiny_order_invariance(tiny):
+    t, ix, qs = tiny
+    rng = np.random.default_rng(3)
+    for q in qs[:6]:
+        base = ix.query(q)
+        perm = rng.permutation(len(q.patterns))
+        assert (ix.query(q.permuted(perm)) == base).all()
+
+
+def test_renaming_invariance(tiny):
+    """Applying a bijection to entity ids maps the result by the same
+    bijection (the method never interprets ids)."""
+    t, ix, qs = tiny
+    rng = np.random.default_rng(5)
+    E = int(t[:, [0, 2]].max()) + 1
+    f = rng.permutation(E).astype(np.int64) + 1000
+    t2 = t.astype(np.int64).copy()
+    t2[:, 0] = f[t2[:, 0]]
+    t2[:, 2] = f[t2[:, 2]]
+    ix2 = oracle.OracleIndex(t2)
+    for q in qs[:5]:
+        q2 = [(s if sv else int(f[s]), p, o if ov else int(f[o]), sv, ov) for (s, p, o, sv, ov) in q.patterns]
+        a = ix.query(q)
+        b = ix2.query(q2, q.n_vars)
+        mapped = f[a.astype(np.int64)]
+        mapped = mapped[np.lexsort(mapped.T[::-1])] if mapped.size else mapped
+        assert (mapped == b).all()
+
+
+# --------------------------------------------------------------------------
+# Planner and cost bounds (Sec. 6.2)
+
+
+def test_upper_bound_sum_and_thm2_ascending_minimises():
+    assert planner.upper_bound_sum([2, 3, 4]) == 2 * 3 + 2 * 3 * 4
+    rng = np.random.default_rng(0)
+    for _ in range(30):
+        sizes = rng.integers(1, 50, size=int(rng.integers(2, 6))).tolist()
+        best = min(planner.upper_bound_sum(p) for p in itertools.permutations(sizes))
+        assert planner.upper_bound_sum(sorted(sizes)) == best
+
+
+def test_thm1_upper_bound_holds_for_oracle_intermediates(tiny):
+    t, ix, qs = tiny
+    stats = storage.statistics(t)
+    for q in qs:
+        rows, steps = ix.query(q, return_steps=True)
+        sizes = [stats[p[1]]["nnz"] for p in q.patterns]
+        assert int(steps[1:].sum()) <= planner.upper_bound_sum(sizes)
+        assert int(steps[0]) <= sizes[0]
+
+
+def _connected(pats):
+    seen = set(planner.pattern_vars(pats[0]))
+    left = list(pats[1:])
+    while left:
+        nxt = [p for p in left if planner.pattern_vars(p) & seen]
+        if not nxt:
+            return False
+        for p in nxt:
+            seen |= planner.pattern_vars(p)
+            left.remove(p)
+    return True
+
+
+def test_plan_never_takes_a_cartesian_step_on_connected_bgps():
+    """Sec. 6.2.1 step 3: every pattern after the first shares a variable
+    with those taken before it, whenever the BGP allows it."""
+    rng = np.random.default_rng(2)
+    n_checked = 0
+    for _ in range(300):
+        n = int(rng.integers(2, 7))
+        pats = [(int(rng.integers(4)), 1, int(rng.integers(4)), 1, 1) for _ in range(n)]
+        if not _connected(pats):
+            continue
+        n_checked += 1
+        keys = rng.integers(0, 100, size=n).tolist()
+        order = planner.plan_order(pats, keys)
+        assert sorted(order) == list(range(n))
+        seen = set(planner.pattern_vars(pats[order[0]]))
+        for i in order[1:]:
+            assert planner.pattern_vars(pats[i]) & seen
+            seen |= planner.pattern_vars(pats[i])
+    assert n_checked > 50
+
+
+def test_plan_first_pattern_has_smallest_key():
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        n = int(rng.integers(1, 7))
+        pats = [(int(rng.integers(3)), 1, int(rng.integers(3)), 1, 1) for _ in range(n)]
+        keys = rng.integers(0, 5, size=n).tolist()
+        order = planner.plan_order(pats, keys)
+        assert keys[order[0]] == min(keys)
+        assert order[0] == keys.index(min(keys))
