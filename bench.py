@@ -1,0 +1,390 @@
+"""Benchmark of the plain SM-based BGP join on one B300 (or N replicas).
+
+A step is one pass of the whole hot path over the medium synthetic workload
+(10^6 entities, 64 predicates, 10^7 distinct int32 triples; 40 BGPs of 3-6
+patterns):  gsmat_load of the device-resident triples (sort, dedupe,
+CSR/CSC, predicate index) followed by the 40 queries (plan, joins,
+canonical sort), each result left on the device.  The metric is queries/s
+of whole steps; result rows/s, per-query p50/p99 latency and the dominant
+kernel's HBM roofline are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsmat|reference]
+
+--impl reference times the CPU oracle (the plain nested-loop join over the
+raw triple list) on a bounded sample of the same workload.
+Multi-GPU (torchrun): every rank runs the same workload on its own GPU
+(independent replicas, no collective on the data path); value = all ranks'
+queries / max rank time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "queries/s"
+CONFIG_NAME = "medium"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    import synth
+
+    t0 = time.time()
+    triples = synth.make_graph(CONFIG_NAME)
+    queries = synth.make_queries(CONFIG_NAME, triples)
+    return triples, queries, time.time() - t0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if sm:
+            out["sm_mhz"] = float(np.median(sm))
+            out["sm_max_mhz"] = float(max(mx))
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def _flush_l2(torch, buf):
+    buf.add_(1)
+
+
+def run_gsmat(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1807_07691_b300 as gs
+
+    triples, queries, gen_s = _workload()
+    nq = len(queries)
+    d_tri = torch.from_numpy(np.ascontiguousarray(triples)).cuda()
+    h_tri = torch.from_numpy(np.ascontiguousarray(triples)).pin_memory()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(profile_rows=None, lat=None):
+        S = gs.Store(d_tri, stream=stream)
+        tabs = []
+        rows = 0
+        for q in queries:
+            if lat is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            T = S.query(q, stream=stream)
+            if lat is not None:
+                e1.record(stream)
+                lat.append((e0, e1))
+            rows += T.rows
+            tabs.append(T)
+        for T in tabs:
+            T.free()
+        S.free()
+        return rows
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    # timed region: K steps, each bracketed by events; L2 flushed between
+    gs.profile_read(reset=True)
+    gs.profile_enable(True)
+    step_ms = []
+    lat = []
+    rows_total = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.time()
+        for _ in range(args.steps):
+            _flush_l2(torch, flush)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            rows_total += step(lat=lat)
+            b.record(stream)
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+        barrier()
+        t_wall = time.time() - t_wall
+    gs.profile_enable(False)
+    prof = gs.profile_read(reset=True)
+    my_ms = float(sum(step_ms))
+    if ws > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([my_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    else:
+        total_ms = my_ms
+    q_lat = np.array([e0.elapsed_time(e1) for (e0, e1) in lat])
+
+    # end-to-end through the public API with host buffers: H2D of the triples
+    # inside gsmat_load, D2H of every result table
+    e2e_ms = []
+    d2h = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S = gs.Store(h_tri.numpy(), stream=stream)
+        d2h = 0
+        for q in queries:
+            T = S.query(q, stream=stream)
+            arr = T.to_numpy(stream=stream)
+            d2h += arr.nbytes
+            T.free()
+        S.free()
+        b.record(stream)
+        b.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return None
+
+    peak, peak_kind = _peaks()
+    # dominant kernel by total event time
+    top = max(prof.items(), key=lambda kv: kv[1]["total_ms"]) if prof else None
+    roof = None
+    if top:
+        name, p = top
+        achieved = p["algo_bytes"] / 1e9 / (p["total_ms"] / 1e3) if p["total_ms"] > 0 else 0.0
+        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "per_launch_ms": round(p["total_ms"] / max(1, p["launches"]), 4),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+    launches = int(sum(p["launches"] for p in prof.values()))
+    value = ws * args.steps * nq / (total_ms / 1e3)
+    rows_per_s = ws * rows_total / (total_ms / 1e3)
+    e2e_value = nq / (float(np.median(e2e_ms)) / 1e3)
+    out = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {
+            "workload": "plain SM-join, medium: 10^6 entities, 64 predicates, 10^7 int32 triples, 40 BGPs of 3-6 "
+                        "patterns; step = gsmat_load + 40 queries (sorted results kept on device)",
+            "queries_per_step": nq,
+            "triples": int(triples.shape[0]),
+            "l2": "flushed between timed steps (256 MB write)",
+            "parallelism": f"replicas x{ws}",
+        },
+        "result_rows_per_s": round(rows_per_s, 1),
+        "result_rows_per_step": int(rows_total / max(1, args.steps)),
+        "latency_ms": {"p50": round(float(np.percentile(q_lat, 50)), 4),
+                       "p99": round(float(np.percentile(q_lat, 99)), 4),
+                       "note": "per-query device time inside the timed steps (store resident)"},
+        "e2e": {"value": round(e2e_value, 2), "unit": "queries/s", "h2d_bytes_per_step": int(triples.nbytes),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(float(np.median(e2e_ms)), 3)},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                        "GBps": round(v["algo_bytes"] / 1e9 / (v["total_ms"] / 1e3), 1) if v["total_ms"] else None}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])},
+        "clocks": clk.summary(),
+        "generation_s": round(gen_s, 1),
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(triples, queries, budget_s=args.cpu_budget)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(triples, queries, budget_s=20.0):
+    """The oracle as it stands, single-threaded, on a bounded sample: its
+    index build plus queries in workload order until the budget is spent."""
+    import oracle
+
+    t0 = time.perf_counter()
+    ix = oracle.OracleIndex(triples)
+    t_index = time.perf_counter() - t0
+    done = 0
+    t_q = 0.0
+    skipped = []
+    for q in queries:
+        if t_index + t_q > budget_s:
+            break
+        a = time.perf_counter()
+        try:
+            ix.query(q, row_limit=30_000_000)
+            t_q += time.perf_counter() - a
+            done += 1
+        except oracle.OracleError:
+            t_q += time.perf_counter() - a
+            skipped.append(q.name)
+    value = done / t_q if t_q > 0 else None
+    return {"value": round(value, 3) if value else None, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"index build ({t_index:.1f} s, not in value) + the first {done} of {len(queries)} medium "
+                      f"queries in workload order ({t_q:.1f} s); queries above 3e7 intermediate rows skipped: "
+                      f"{len(skipped)}"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return None
+    triples, queries, _ = _workload()
+    import oracle
+
+    ix = oracle.OracleIndex(triples)
+    # each step: a bounded sample (the first queries of the workload)
+    sample = queries[:8]
+    times = []
+    for i in range(args.warmup + args.steps):
+        a = time.perf_counter()
+        n = 0
+        for q in sample:
+            try:
+                ix.query(q, row_limit=30_000_000)
+                n += 1
+            except oracle.OracleError:
+                pass
+        dt = time.perf_counter() - a
+        if i >= args.warmup:
+            times.append((n, dt))
+    n_tot = sum(n for n, _ in times)
+    t_tot = sum(dt for _, dt in times)
+    value = n_tot / t_tot if t_tot > 0 else 0.0
+    return {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t_tot / max(1, args.steps), 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "plain SM-join, medium (oracle on the first 8 of 40 queries per step)",
+                   "queries_per_step": len(sample)},
+        "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 8 medium queries per step, index prebuilt"},
+        "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsmat", choices=["gsmat", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_gsmat(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,270 @@
+/*
+ * gsmat.h -- C ABI of libgsmat: sparse-matrix-based (SM-based) evaluation of
+ * SPARQL basic graph patterns on one B300 GPU (sm_103a).
+ *
+ * The problem statement follows arXiv 1807.07691: an RDF dataset is a set of
+ * (subject, predicate, object) triples (Sec. 3.1) stored as one sparse matrix
+ * per predicate (Sec. 5.3); a basic graph pattern (BGP) is a set of triple
+ * patterns whose subject and object are variables or constants and whose
+ * predicate is known (Sec. 3.2, Sec. 6.3); its answer is the relation over
+ * all of its variables obtained by joining the patterns' relations
+ * (Sec. 6, evaluation procedure), each join being a sparse-matrix product
+ * without accumulation (Sec. 6.1).
+ *
+ * Conventions for every call:
+ *  - Return value: an int status, GSMAT_OK (0) or a GSMAT_ERR_* code.  On
+ *    error no output handle is written and nothing is leaked;
+ *    gsmat_last_error() gives a human-readable detail for the calling thread.
+ *  - Streams: `gsmat_stream_t` is a cudaStream_t (NULL = the legacy default
+ *    stream).  Work is stream-ordered; calls that return host-visible values
+ *    synchronise the stream they were given.
+ *  - Memory: every device buffer the library owns comes from the allocator
+ *    hook (gsmat_set_allocator); the default is cudaMallocAsync/cudaFreeAsync
+ *    on the call's stream.  Handles own their buffers; free them with the
+ *    matching *_free call.
+ *  - Ids: entity and predicate ids are int32 >= 0; entity ids and predicate
+ *    ids are separate id spaces (the bijections h_so and h_p of Sec. 5.1).
+ *  - Threading: a store is read-only after gsmat_load, so queries on one
+ *    store may run concurrently from several host threads on different
+ *    streams.  gsmat_set_allocator and gsmat_profile_* are process-global.
+ */
+#ifndef GSMAT_H_
+#define GSMAT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GSMAT_API __attribute__((visibility("default")))
+#else
+#define GSMAT_API
+#endif
+
+typedef struct CUstream_st *gsmat_stream_t; /* == cudaStream_t */
+
+/* Status codes. */
+#define GSMAT_OK 0
+#define GSMAT_ERR_INVALID_ARG 1  /* bad pointer, size, id or BGP shape */
+#define GSMAT_ERR_UNSUPPORTED 2  /* a variable predicate (Sec. 6.3 assumes known predicates) */
+#define GSMAT_ERR_OOM 3          /* the allocator hook returned NULL */
+#define GSMAT_ERR_CAPACITY 4     /* a table would exceed the library's row/offset limits */
+#define GSMAT_ERR_CUDA 5         /* a CUDA runtime call failed */
+#define GSMAT_ERR_DEVICE_CHECK 6 /* a kernel's own check fired (bounded wait expired) */
+
+typedef struct gsmat_store gsmat_store; /* device-resident SM storage */
+typedef struct gsmat_table gsmat_table; /* device-resident binding table */
+
+/* ------------------------------------------------------------------------ */
+/* Errors, version, allocator                                                */
+
+/* Static description of a status code; never NULL. */
+GSMAT_API const char *gsmat_strerror(int status);
+
+/* Detail of the calling thread's last failed call ("" if none). */
+GSMAT_API const char *gsmat_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+GSMAT_API int gsmat_version(void);
+
+/* Device allocation hook.  alloc(bytes, ctx, stream) returns device memory
+ * usable in stream order on `stream` (NULL on failure -> GSMAT_ERR_OOM);
+ * free(ptr, ctx, stream) releases it in stream order.  Passing alloc = NULL
+ * restores the default (cudaMallocAsync / cudaFreeAsync).  Process-global;
+ * set it before creating stores or tables and keep it until they are freed.
+ * Returns GSMAT_ERR_INVALID_ARG if exactly one of alloc/free is NULL. */
+typedef void *(*gsmat_alloc_fn)(size_t bytes, void *ctx, gsmat_stream_t stream);
+typedef void (*gsmat_free_fn)(void *ptr, void *ctx, gsmat_stream_t stream);
+GSMAT_API int gsmat_set_allocator(gsmat_alloc_fn alloc, gsmat_free_fn free_fn, void *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* SM storage (Sec. 5)                                                       */
+
+/* Build the device store from n triples (s, p, o), row-major int32 n x 3.
+ *  triples            host pointer (triples_on_device = 0; copied to the
+ *                     device inside the call) or device pointer (= 1; read
+ *                     only, not retained).
+ *  n                  0 <= n <= 2^31 - 1.
+ * The input is a multiset; duplicates are removed, since a dataset is a set
+ * of triples (Sec. 3.1).  The store holds, per predicate h, the matrix M_h
+ * (Sec. 5.3) twice: rows by subject (CSR) and rows by object (CSC), each
+ * row's entries sorted, with the non-zero-row auxiliary arrays of Sec. 6.3
+ * (row id, entry count, first position) precomputed, plus a predicate hash
+ * index and the per-predicate statistics m = nnz(M_h) (Sec. 5.1, Sec. 5.3).
+ * Errors: INVALID_ARG for a NULL pointer, n out of range or a negative id;
+ * OOM; CUDA.  The call synchronises `stream`. */
+GSMAT_API int gsmat_load(const int32_t *triples, int64_t n, int triples_on_device,
+                         gsmat_stream_t stream, gsmat_store **out);
+
+typedef struct {
+    int64_t n_input;      /* triples passed to gsmat_load */
+    int64_t n_unique;     /* distinct triples stored */
+    int32_t n_predicates; /* distinct predicates */
+    int32_t max_entity;   /* largest subject/object id (-1 if empty) */
+    int32_t max_predicate;
+    int32_t n_dense_rows_s; /* predicates whose CSR side uses a dense row pointer */
+    int32_t n_dense_rows_o; /* same for the CSC side */
+    int32_t _reserved;
+    int64_t device_bytes; /* bytes held on the device by the store */
+} gsmat_store_info_t;
+
+GSMAT_API int gsmat_store_info(const gsmat_store *store, gsmat_store_info_t *info);
+
+/* Per-predicate statistics, in ascending predicate-id order. */
+typedef struct {
+    int32_t pred_id; /* predicate id as given to gsmat_load */
+    int32_t nnz;     /* m: number of (s, o) pairs of M_h (Sec. 5.3) */
+    int32_t nr_s;    /* non-zero rows on the subject side */
+    int32_t nr_o;    /* non-zero rows on the object side */
+} gsmat_pred_stats;
+
+/* Copy min(cap, n_predicates) entries into out (host); returns their count
+ * through *n_out. */
+GSMAT_API int gsmat_store_pred_stats(const gsmat_store *store, gsmat_pred_stats *out, int32_t cap,
+                                     int32_t *n_out);
+
+/* Copy one predicate's matrix to host buffers, for inspection and tests.
+ *  side 0: rows by subject (CSR): row_ids = distinct subjects ascending,
+ *          entries = objects; side 1: rows by object (CSC).
+ *  row_ids   host int32[nr]       (may be NULL)
+ *  row_ptr   host int64[nr + 1]   offsets into entries, row_ptr[0] = 0
+ *  entries   host int32[nnz]      each row's entries ascending
+ * Sizes come from gsmat_store_pred_stats.  INVALID_ARG if the predicate is
+ * absent.  Synchronises `stream`. */
+GSMAT_API int gsmat_store_export(const gsmat_store *store, int32_t pred_id, int side, int32_t *row_ids,
+                                 int64_t *row_ptr, int32_t *entries, gsmat_stream_t stream);
+
+/* Look up the predicate hash index on the host: slot of pred_id in the
+ * ascending predicate order, or -1 if absent. */
+GSMAT_API int32_t gsmat_store_pred_index(const gsmat_store *store, int32_t pred_id);
+
+GSMAT_API void gsmat_store_free(gsmat_store *store);
+
+/* ------------------------------------------------------------------------ */
+/* BGP evaluation (Sec. 6, Alg. 1-3)                                         */
+
+/* One triple pattern.  For each of s, p, o: *_var = 1 means the field holds
+ * a variable number in 0..n_vars-1, *_var = 0 means it holds a constant id. */
+typedef struct {
+    int32_t s, p, o;
+    uint8_t s_var, p_var, o_var, _pad;
+} gsmat_pattern;
+
+/* Query flags. */
+#define GSMAT_SORTED 0u       /* columns = variables 0..V-1, rows ascending lexicographically */
+#define GSMAT_PLAN_ORDER 1u   /* columns in the order the plan binds variables, rows ascending
+                                 in that column order (no final sort) */
+#define GSMAT_COUNT_ONLY 2u   /* compute the row count only; the table has no columns */
+
+/* Evaluate a BGP.
+ *  pats, n_pats   host array of 1 <= n_pats <= 64 patterns.
+ *  n_vars         0 <= n_vars <= 32; every variable 0..n_vars-1 must occur.
+ * The plan is Alg. 1 (connected minimal upper bound) with the
+ * intermediate-size estimate of Sec. 6.2; each step is one SM-based join
+ * (Alg. 3) of the running relation with the next pattern's matrix:
+ * a gather-expand along the pattern's CSR or CSC rows when one end is bound,
+ * a membership filter with prefix-sum compaction when both ends are bound,
+ * a Cartesian product when neither is.  Result semantics: every assignment
+ * of the variables that puts every pattern's triple in the store, each once
+ * (no projection, no DISTINCT, no accumulation -- Sec. 6.1).
+ * A predicate that is absent from the store gives an empty result.
+ * Errors: INVALID_ARG (bad shape, unused or out-of-range variable, negative
+ * constant), UNSUPPORTED (variable predicate), OOM, CAPACITY (more than
+ * 2^32 - 1 rows in a table), CUDA, DEVICE_CHECK.  Synchronises `stream`. */
+GSMAT_API int gsmat_query(const gsmat_store *store, const gsmat_pattern *pats, int n_pats, int n_vars,
+                          uint32_t flags, gsmat_stream_t stream, gsmat_table **out);
+
+/* Shape of a result.  col_vars (host int32[cols], may be NULL) receives the
+ * variable number held by each column. */
+GSMAT_API int gsmat_table_info(const gsmat_table *table, int64_t *rows, int32_t *cols, int32_t *col_vars);
+
+/* Device pointer to column `col` (int32[rows], owned by the table). */
+GSMAT_API int gsmat_table_column(const gsmat_table *table, int32_t col, const int32_t **d_col);
+
+/* Copy the table as row-major int32[rows][cols] into dst (host memory when
+ * dst_on_device = 0, device memory otherwise).  Synchronises `stream`. */
+GSMAT_API int gsmat_table_copy(const gsmat_table *table, int32_t *dst, int dst_on_device, gsmat_stream_t stream);
+
+/* Per-query record: plan and per-step row counts. */
+#define GSMAT_MAX_PATTERNS 64
+typedef struct {
+    int32_t n_steps;
+    int32_t order[GSMAT_MAX_PATTERNS]; /* pattern index per plan step */
+    int32_t kind[GSMAT_MAX_PATTERNS];  /* GSMAT_STEP_* per plan step */
+    double est_rows[GSMAT_MAX_PATTERNS]; /* planner estimate after each step */
+    int64_t rows[GSMAT_MAX_PATTERNS];    /* actual rows after each step */
+    double est_cost;                     /* sum of est_rows */
+    int64_t result_rows;
+} gsmat_query_stats;
+
+#define GSMAT_STEP_CROSS 0    /* no end bound: Cartesian product with the pattern's relation */
+#define GSMAT_STEP_EXPAND_S 1 /* subject end known, object new: expand along CSR rows */
+#define GSMAT_STEP_EXPAND_O 2 /* object end known, subject new: expand along CSC rows */
+#define GSMAT_STEP_FILTER 3   /* both ends known: membership filter + compaction */
+
+GSMAT_API int gsmat_table_stats(const gsmat_table *table, gsmat_query_stats *stats);
+
+GSMAT_API void gsmat_table_free(gsmat_table *table);
+
+/* ------------------------------------------------------------------------ */
+/* Host planner (Alg. 1; Sec. 6.2), callable without a GPU                   */
+
+/* Order a BGP's patterns and estimate the intermediate sizes.
+ *  keys[i]    the sort statistic of pattern i: m = nnz(M_p) for a pattern
+ *             without constants, the row size of its constant otherwise.
+ *  stats[i]   nnz, nr_s, nr_o of pattern i's predicate (zeros if absent).
+ *  order_out  int32[n_pats]: pattern index per plan step.
+ *  kinds_out  int32[n_pats]: GSMAT_STEP_* per plan step (may be NULL).
+ *  est_out    double[n_pats]: running estimate after each step (may be NULL).
+ * Stable sort by key, then repeatedly the first remaining pattern sharing a
+ * variable with those taken (the smallest remaining one if none does).
+ * The estimate multiplies, per step: CROSS -> key; EXPAND from a constant ->
+ * key; EXPAND from a bound variable -> nnz / nr on that side; FILTER ->
+ * min(1, nnz / (nr_s * nr_o)); starting from 1. */
+GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
+                         const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out,
+                         double *est_out);
+
+/* ------------------------------------------------------------------------ */
+/* Device primitives used by the store builder and the join (exported so     */
+/* that they can be tested and reused on their own)                          */
+
+/* Stable LSD radix sort of n uint64 keys on bits [begin_bit, end_bit),
+ * 8 bits per pass, with an optional uint32 payload (d_vals may be NULL).
+ * d_keys / d_vals are device arrays, sorted in place.  0 <= n < 2^32.
+ * Scratch comes from the allocator hook.  Does not synchronise. */
+GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int begin_bit, int end_bit,
+                                   gsmat_stream_t stream);
+
+/* Exclusive prefix sum of n int32 counts (each >= 0) into d_out[0..n]
+ * (int64; d_out[n] = total), single pass with decoupled look-back over
+ * tiles.  Scratch (tile descriptors) comes from the allocator hook.
+ * Does not synchronise. */
+GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int64_t n, gsmat_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Kernel timing (CUDA events on the launching stream)                       */
+
+typedef struct {
+    char name[32];         /* kernel family */
+    int64_t launches;
+    double total_ms;       /* sum of event-timed durations */
+    double algo_bytes;     /* sum of algorithmic bytes moved (see docs per kernel) */
+    double items;          /* sum of items processed (rows or keys) */
+} gsmat_kernel_profile;
+
+/* Enable (1) or disable (0) per-launch event timing in all later calls. */
+GSMAT_API int gsmat_profile_enable(int on);
+
+/* Copy up to cap kernel families into out; *n_out gets their count.
+ * reset = 1 clears the counters after reading. */
+GSMAT_API int gsmat_profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSMAT_H_ */

@@ -1,0 +1,173 @@
+// The C ABI of libgsmat (include/gsmat.h): argument checks and dispatch.
+#include <string.h>
+
+#include "plan.h"
+#include "query.cuh"
+#include "store.cuh"
+
+namespace gs {
+const char *last_error();
+int set_allocator(gsmat_alloc_fn a, gsmat_free_fn f, void *ctx);
+int profile_enable(int on);
+int profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset);
+}  // namespace gs
+
+using gs::set_error;
+
+extern "C" {
+
+GSMAT_API const char *gsmat_strerror(int status) {
+    switch (status) {
+        case GSMAT_OK: return "ok";
+        case GSMAT_ERR_INVALID_ARG: return "invalid argument";
+        case GSMAT_ERR_UNSUPPORTED: return "unsupported (variable predicate)";
+        case GSMAT_ERR_OOM: return "out of device memory";
+        case GSMAT_ERR_CAPACITY: return "capacity exceeded";
+        case GSMAT_ERR_CUDA: return "CUDA error";
+        case GSMAT_ERR_DEVICE_CHECK: return "device-side check failed";
+        default: return "unknown status";
+    }
+}
+
+GSMAT_API const char *gsmat_last_error(void) { return gs::last_error(); }
+
+GSMAT_API int gsmat_version(void) { return 100; }
+
+GSMAT_API int gsmat_set_allocator(gsmat_alloc_fn alloc, gsmat_free_fn free_fn, void *ctx) {
+    gs::clear_error();
+    return gs::set_allocator(alloc, free_fn, ctx);
+}
+
+GSMAT_API int gsmat_load(const int32_t *triples, int64_t n, int triples_on_device, gsmat_stream_t stream,
+                         gsmat_store **out) {
+    gs::clear_error();
+    return gs::store_build(triples, n, triples_on_device, (cudaStream_t)stream, out);
+}
+
+GSMAT_API int gsmat_store_info(const gsmat_store *S, gsmat_store_info_t *info) {
+    gs::clear_error();
+    if (!S || !info) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->n_input = S->n_input;
+    info->n_unique = S->n_unique;
+    info->n_predicates = S->n_pred;
+    info->max_entity = S->max_entity;
+    info->max_predicate = S->max_pred;
+    info->n_dense_rows_s = S->n_dense[0];
+    info->n_dense_rows_o = S->n_dense[1];
+    info->device_bytes = S->device_bytes();
+    return GSMAT_OK;
+}
+
+GSMAT_API int gsmat_store_pred_stats(const gsmat_store *S, gsmat_pred_stats *out, int32_t cap, int32_t *n_out) {
+    gs::clear_error();
+    if (!S || (!out && cap > 0)) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    const int32_t n = S->n_pred < cap ? S->n_pred : cap;
+    for (int32_t i = 0; i < n; ++i) {
+        out[i].pred_id = S->pred_ids[i];
+        out[i].nnz = S->side[0][i].nnz;
+        out[i].nr_s = S->side[0][i].nrows;
+        out[i].nr_o = S->side[1][i].nrows;
+    }
+    if (n_out) *n_out = n;
+    return GSMAT_OK;
+}
+
+GSMAT_API int32_t gsmat_store_pred_index(const gsmat_store *S, int32_t pred_id) {
+    if (!S) return -1;
+    return S->slot_of(pred_id);
+}
+
+GSMAT_API int gsmat_store_export(const gsmat_store *S, int32_t pred_id, int side, int32_t *row_ids, int64_t *row_ptr,
+                                 int32_t *entries, gsmat_stream_t stream) {
+    gs::clear_error();
+    if (!S || (side != 0 && side != 1)) return set_error(GSMAT_ERR_INVALID_ARG, "bad store or side");
+    const int32_t slot = S->slot_of(pred_id);
+    if (slot < 0) return set_error(GSMAT_ERR_INVALID_ARG, "predicate %d not in the store", pred_id);
+    cudaStream_t st = (cudaStream_t)stream;
+    const gs::PredSide &ps = S->side[side][slot];
+    std::vector<int32_t> off((size_t)ps.nrows + 1);
+    if (row_ids && ps.nrows > 0) {
+        GS_CUDA(cudaMemcpyAsync(row_ids, S->rowid[side].as<int32_t>() + ps.row_base, sizeof(int32_t) * ps.nrows,
+                                cudaMemcpyDeviceToHost, st));
+    }
+    GS_CUDA(cudaMemcpyAsync(off.data(), S->rowoff[side].as<int32_t>() + ps.row_base, sizeof(int32_t) * (ps.nrows + 1),
+                            cudaMemcpyDeviceToHost, st));
+    if (entries && ps.nnz > 0) {
+        GS_CUDA(cudaMemcpyAsync(entries, S->val[side].as<int32_t>() + ps.ent_base, sizeof(int32_t) * ps.nnz,
+                                cudaMemcpyDeviceToHost, st));
+    }
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (row_ptr) {
+        for (int32_t r = 0; r <= ps.nrows; ++r) row_ptr[r] = (int64_t)off[r] - ps.ent_base;
+    }
+    return GSMAT_OK;
+}
+
+GSMAT_API void gsmat_store_free(gsmat_store *S) { delete S; }
+
+GSMAT_API int gsmat_query(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags,
+                          gsmat_stream_t stream, gsmat_table **out) {
+    gs::clear_error();
+    return gs::query_run(S, pats, n_pats, n_vars, flags, (cudaStream_t)stream, out);
+}
+
+GSMAT_API int gsmat_table_info(const gsmat_table *T, int64_t *rows, int32_t *cols, int32_t *col_vars) {
+    gs::clear_error();
+    if (!T) return set_error(GSMAT_ERR_INVALID_ARG, "table is NULL");
+    if (rows) *rows = T->rows;
+    if (cols) *cols = T->ncols;
+    if (col_vars) {
+        for (int c = 0; c < T->ncols; ++c) col_vars[c] = T->vars[c];
+    }
+    return GSMAT_OK;
+}
+
+GSMAT_API int gsmat_table_column(const gsmat_table *T, int32_t col, const int32_t **d_col) {
+    gs::clear_error();
+    if (!T || !d_col || col < 0 || col >= T->ncols) return set_error(GSMAT_ERR_INVALID_ARG, "bad table or column");
+    *d_col = T->col[col];
+    return GSMAT_OK;
+}
+
+GSMAT_API int gsmat_table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::table_copy(T, dst, dst_on_device, (cudaStream_t)stream);
+}
+
+GSMAT_API int gsmat_table_stats(const gsmat_table *T, gsmat_query_stats *stats) {
+    gs::clear_error();
+    if (!T || !stats) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    *stats = T->stats;
+    return GSMAT_OK;
+}
+
+GSMAT_API void gsmat_table_free(gsmat_table *T) { delete T; }
+
+GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
+                         const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out, double *est_out) {
+    gs::clear_error();
+    GS_TRY(gs::validate_bgp(pats, n_pats, n_vars));
+    if (!keys || !stats || !order_out) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    return gs::plan_bgp(pats, n_pats, keys, stats, order_out, kinds_out, est_out);
+}
+
+GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int begin_bit, int end_bit,
+                                   gsmat_stream_t stream) {
+    gs::clear_error();
+    if (n > 0 && !d_keys) return set_error(GSMAT_ERR_INVALID_ARG, "keys is NULL");
+    return gs::radix_sort_u64(d_keys, d_vals, n, begin_bit, end_bit, (cudaStream_t)stream);
+}
+
+GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int64_t n, gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::exclusive_scan_i32(d_in, d_out, n, (cudaStream_t)stream, nullptr);
+}
+
+GSMAT_API int gsmat_profile_enable(int on) { return gs::profile_enable(on); }
+
+GSMAT_API int gsmat_profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset) {
+    return gs::profile_read(out, cap, n_out, reset);
+}
+
+}  // extern "C"

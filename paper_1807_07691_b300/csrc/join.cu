@@ -1,0 +1,410 @@
+// Kernels of one SM-based join step (Alg. 3, Sec. 6.3) on the GPU.
+//
+// The paper's GPU join (Sec. 7.2) assigns one thread to each non-zero row of
+// the left matrix and pre-computes per-row output counts N and offsets P
+// (Alg. 4).  Here the count and the offset scan are fused into one
+// single-pass kernel, and the expansion is output-slot parallel: each CTA
+// owns a fixed slab of output rows and finds the parent row of each slot by
+// a search over the offsets, so a hub row with 10^6 matches is spread over
+// many CTAs instead of serialising one thread (power-law degrees, Sec. 1).
+// Rows whose other join variables must also match (Alg. 3, the "other join
+// variables" test) are kept by a membership filter with single-pass
+// prefix-sum compaction, which preserves row order.
+#include "join.cuh"
+#include "select.cuh"
+
+namespace gs {
+namespace {
+
+// ---------------------------------------------------------------------------
+// count + scan
+
+constexpr int kCsBlock = 256;
+constexpr int kCsItems = 4;
+constexpr int kCsTile = kCsBlock * kCsItems;
+
+__global__ void __launch_bounds__(kCsBlock) count_scan_kernel(SideView sv, PredSide ps,
+                                                              const int32_t *__restrict__ x, int64_t n,
+                                                              int64_t *__restrict__ off, int32_t *__restrict__ first,
+                                                              int64_t *__restrict__ d_total, LookbackScratch ls) {
+    __shared__ int tile_sm;
+    __shared__ int64_t scan_sm[kCsBlock / 32 + 1];
+    __shared__ int64_t prefix_sm;
+    const int tile = acquire_tile_id(ls, &tile_sm);
+    const int64_t i0 = (int64_t)tile * kCsTile + (int64_t)threadIdx.x * kCsItems;
+    int cnt[kCsItems];
+    int fst[kCsItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kCsItems; ++j) {
+        const int64_t i = i0 + j;
+        cnt[j] = 0;
+        fst[j] = 0;
+        if (i < n) {
+            const int2 r = row_range(sv, ps, __ldg(x + i));
+            cnt[j] = r.y - r.x;
+            fst[j] = r.x;
+        }
+        sum += cnt[j];
+    }
+    int64_t tot;
+    const int64_t ex = block_exclusive_sum<kCsBlock>(sum, scan_sm, &tot);
+    const int64_t pre = tile_lookback(ls, tile, tot, &prefix_sm);
+    int64_t run = pre + ex;
+#pragma unroll
+    for (int j = 0; j < kCsItems; ++j) {
+        const int64_t i = i0 + j;
+        if (i < n) {
+            off[i] = run;
+            first[i] = fst[j];
+        }
+        run += cnt[j];
+    }
+    if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) {
+        off[n] = pre + tot;
+        *d_total = pre + tot;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// expand
+
+constexpr int kExBlock = 256;
+constexpr int kExVec = 4;
+constexpr int kExIter = 4;
+constexpr int kExSlots = kExBlock * kExVec * kExIter;  // output rows per CTA
+constexpr int kExSmemRows = kExSlots + 2;
+
+struct ExpandArgs {
+    const int32_t *val;  // the side's entry array
+    Cols in;
+    int k;
+    int64_t n_in;
+    const int64_t *off;
+    const int32_t *first;
+    int64_t total;
+    OutCols out;
+};
+
+// Largest r in [lo, hi] with off[r] <= j (off[lo] <= j is required).
+__device__ __forceinline__ int64_t parent_global(const int64_t *__restrict__ off, int64_t lo, int64_t hi, int64_t j) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kExBlock) expand_kernel(ExpandArgs a) {
+    __shared__ int64_t soff[kExSmemRows];
+    __shared__ int64_t range_sm[2];
+    const int64_t j0 = (int64_t)blockIdx.x * kExSlots;
+    const int64_t j1 = (j0 + kExSlots < a.total) ? j0 + kExSlots : a.total;
+    if (threadIdx.x == 0) {
+        const int64_t lo = parent_global(a.off, 0, a.n_in - 1, j0);
+        range_sm[0] = lo;
+        range_sm[1] = parent_global(a.off, lo, a.n_in - 1, j1 - 1);
+    }
+    __syncthreads();
+    const int64_t r_lo = range_sm[0];
+    const int64_t nr = range_sm[1] - r_lo + 1;  // parent rows of this slab
+    const bool staged = nr + 1 <= kExSmemRows;
+    if (staged) {
+        for (int i = threadIdx.x; i <= nr; i += kExBlock) soff[i] = __ldg(a.off + r_lo + i);
+    }
+    __syncthreads();
+    const int k = a.k;
+#pragma unroll 1
+    for (int it = 0; it < kExIter; ++it) {
+        const int64_t jb = j0 + (int64_t)it * (kExBlock * kExVec) + (int64_t)threadIdx.x * kExVec;
+        if (jb >= j1) break;
+        // parent of the first slot
+        int64_t r;
+        if (staged) {
+            int lo = 0, hi = (int)nr - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (soff[mid] <= jb) lo = mid; else hi = mid - 1;
+            }
+            r = r_lo + lo;
+        } else {
+            r = parent_global(a.off, r_lo, r_lo + nr - 1, jb);
+        }
+        int64_t r_beg = staged ? soff[r - r_lo] : __ldg(a.off + r);
+        int64_t r_end = staged ? soff[r - r_lo + 1] : __ldg(a.off + r + 1);
+        int64_t rr[kExVec];
+        int32_t nv[kExVec];
+#pragma unroll
+        for (int q = 0; q < kExVec; ++q) {
+            const int64_t j = jb + q;
+            rr[q] = r;
+            nv[q] = 0;
+            if (j < j1) {
+                while (j >= r_end) {
+                    ++r;
+                    r_beg = r_end;
+                    r_end = staged ? soff[r - r_lo + 1] : __ldg(a.off + r + 1);
+                }
+                rr[q] = r;
+                nv[q] = __ldg(a.val + __ldg(a.first + r) + (j - r_beg));
+            }
+        }
+        if (jb + kExVec <= j1) {
+            for (int c = 0; c < k; ++c) {
+                const int32_t *src = a.in.c[c];
+                int4 v;
+                v.x = __ldg(src + rr[0]);
+                v.y = __ldg(src + rr[1]);
+                v.z = __ldg(src + rr[2]);
+                v.w = __ldg(src + rr[3]);
+                *reinterpret_cast<int4 *>(a.out.c[c] + jb) = v;
+            }
+            *reinterpret_cast<int4 *>(a.out.c[k] + jb) = make_int4(nv[0], nv[1], nv[2], nv[3]);
+        } else {
+            for (int q = 0; q < kExVec; ++q) {
+                const int64_t j = jb + q;
+                if (j >= j1) break;
+                for (int c = 0; c < k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + rr[q]);
+                a.out.c[k][j] = nv[q];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// filter (membership test of (s, o) in the predicate) + compaction
+
+// Rows this short are searched directly, without looking up the other side.
+constexpr int kShortRow = 64;
+
+struct FilterOp {
+    SideView s0, s1;
+    PredSide ps_s, ps_o;
+    ValueSrc s, o;
+    Cols in;
+    int k;
+    OutCols out;
+    __device__ bool flag(int64_t i) const {
+        const int32_t x = s.at(i), y = o.at(i);
+        const int2 a = row_range(s0, ps_s, x);
+        const int la = a.y - a.x;
+        if (la <= 0) return false;
+        if (la <= kShortRow) return sorted_contains(s0.val, a.x, a.y, y);
+        const int2 b = row_range(s1, ps_o, y);
+        const int lb = b.y - b.x;
+        if (lb <= 0) return false;
+        if (la <= lb) return sorted_contains(s0.val, a.x, a.y, y);
+        return sorted_contains(s1.val, b.x, b.y, x);
+    }
+    __device__ void emit(int64_t i, int64_t j) const {
+        for (int c = 0; c < k; ++c) out.c[c][j] = __ldg(in.c[c] + i);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Cartesian product
+
+__global__ void __launch_bounds__(256) cross_kernel(Cols in, int k, Cols rel, int rc, uint32_t m, uint64_t total,
+                                                    OutCols out) {
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < total; j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t jj = (uint32_t)j;
+        const uint32_t r = jj / m;
+        const uint32_t q = jj - r * m;
+        for (int c = 0; c < k; ++c) out.c[c][jj] = __ldg(in.c[c] + r);
+        for (int c = 0; c < rc; ++c) out.c[k + c][jj] = __ldg(rel.c[c] + q);
+    }
+}
+
+struct DiagOp {
+    const int32_t *key, *val;
+    int32_t *out;
+    __device__ bool flag(int64_t i) const { return key[i] == val[i]; }
+    __device__ void emit(int64_t i, int64_t j) const { out[j] = key[i]; }
+};
+
+__global__ void const_lookup_kernel(StoreView sv, const PredSide *__restrict__ sides, int n_pred,
+                                    const int32_t *__restrict__ req, int n_req, int32_t *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_req) return;
+    const int slot = req[3 * i], side = req[3 * i + 1], x = req[3 * i + 2];
+    int2 r = make_int2(0, 0);
+    if (slot >= 0 && slot < n_pred && (side == 0 || side == 1)) {
+        r = row_range(side == 0 ? sv.side[0] : sv.side[1], sides[side * n_pred + slot], x);
+    }
+    out[2 * i] = r.x;
+    out[2 * i + 1] = r.y;
+}
+
+// ---------------------------------------------------------------------------
+// canonical ordering helpers
+
+__global__ void pack_rows_kernel(Cols cols, int nc, int bits, const uint32_t *__restrict__ perm, int64_t n,
+                                 uint64_t *__restrict__ keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = perm ? __ldg(perm + i) : (uint32_t)i;
+        uint64_t key = 0;
+        for (int c = 0; c < nc; ++c) key = (key << bits) | (uint64_t)(uint32_t)__ldg(cols.c[c] + r);
+        keys[i] = key;
+    }
+}
+
+__global__ void iota_u32_kernel(uint32_t *v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        v[i] = (uint32_t)i;
+    }
+}
+
+__global__ void gather_rows_kernel(Cols in, int k, const uint32_t *__restrict__ perm, int64_t n, OutCols out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = __ldg(perm + i);
+        for (int c = 0; c < k; ++c) out.c[c][i] = __ldg(in.c[c] + r);
+    }
+}
+
+__global__ void interleave_kernel(Cols in, int k, int64_t n, int32_t *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < k; ++c) dst[i * k + c] = __ldg(in.c[c] + i);
+    }
+}
+
+__global__ void copy_cols_kernel(Cols in, int k, int64_t n, OutCols out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < k; ++c) out.c[c][i] = __ldg(in.c[c] + i);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+
+int launch_count_scan(const StoreView &sv, int side, const PredSide &ps, const int32_t *x, int64_t n, int64_t *off,
+                      int32_t *first, int64_t *d_total, int *err, cudaStream_t st) {
+    if (n <= 0) {
+        GS_CUDA(cudaMemsetAsync(off, 0, sizeof(int64_t), st));
+        GS_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int64_t), st));
+        return GSMAT_OK;
+    }
+    const int64_t ntiles = (n + kCsTile - 1) / kCsTile;
+    if (ntiles > INT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "count over %lld rows", (long long)n);
+    LookbackBuf lb;
+    GS_TRY(lb.make(ntiles, st, err));
+    // algorithmic bytes: bound column, one row lookup (8 B), offsets + first
+    KernelTimer t("count_scan", st, (double)n * (4.0 + 8.0 + 8.0 + 4.0), (double)n);
+    count_scan_kernel<<<(unsigned)ntiles, kCsBlock, 0, st>>>(sv.side[side], ps, x, n, off, first, d_total, lb.view);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t n_in, const int64_t *off,
+                  const int32_t *first, int64_t total, OutCols out, cudaStream_t st) {
+    if (total <= 0) return GSMAT_OK;
+    ExpandArgs a;
+    a.val = sv.side[side].val;
+    a.in = in;
+    a.k = k;
+    a.n_in = n_in;
+    a.off = off;
+    a.first = first;
+    a.total = total;
+    a.out = out;
+    const int64_t grid = (total + kExSlots - 1) / kExSlots;
+    // algorithmic bytes (per the method): read k bound columns and the
+    // offsets once per parent row, one neighbour id per output row, write
+    // k + 1 columns per output row.
+    KernelTimer t("expand", st, (double)n_in * (4.0 * k + 8.0 + 4.0) + (double)total * (4.0 + 4.0 * (k + 1)),
+                  (double)total);
+    expand_kernel<<<(unsigned)grid, kExBlock, 0, st>>>(a);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_filter(const StoreView &sv, const PredSide &ps_s, const PredSide &ps_o, ValueSrc s, ValueSrc o,
+                  const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st) {
+    FilterOp op;
+    op.s0 = sv.side[0];
+    op.s1 = sv.side[1];
+    op.ps_s = ps_s;
+    op.ps_o = ps_o;
+    op.s = s;
+    op.o = o;
+    op.in = in;
+    op.k = k;
+    op.out = out;
+    // algorithmic bytes: the two tested columns, a row lookup and a probe
+    // sector per row, plus reading and writing the surviving rows (counted at
+    // the input size: an upper bound)
+    KernelTimer t("filter", st, (double)n_in * (8.0 + 8.0 + 32.0 + 8.0 * k), (double)n_in);
+    GS_TRY(run_select(op, n_in, d_count, st, err));
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_cross(const Cols &in, int k, int64_t n_in, const Cols &rel, int r_cols, int64_t m, OutCols out,
+                 cudaStream_t st) {
+    const uint64_t total = (uint64_t)n_in * (uint64_t)m;
+    if (total == 0) return GSMAT_OK;
+    if (total > UINT32_MAX || m > UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "cross product of %llu rows", (unsigned long long)total);
+    KernelTimer t("cross", st, (double)total * 4.0 * (k + r_cols), (double)total);
+    cross_kernel<<<grid_1d((int64_t)total, 256), 256, 0, st>>>(in, k, rel, r_cols, (uint32_t)m, total, out);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_diag(const StoreView &sv, const PredSide &ps0, int32_t *out, int64_t *d_count, int *err, cudaStream_t st) {
+    DiagOp op{sv.side[0].key + ps0.ent_base, sv.side[0].val + ps0.ent_base, out};
+    return run_select(op, ps0.nnz, d_count, st, err);
+}
+
+int launch_const_lookup(const StoreView &sv, const PredSide *d_sides, int n_pred, const int32_t *d_req, int n_req,
+                        int32_t *d_out, cudaStream_t st) {
+    if (n_req <= 0) return GSMAT_OK;
+    const_lookup_kernel<<<(n_req + 127) / 128, 128, 0, st>>>(sv, d_sides, n_pred, d_req, n_req, d_out);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+int launch_pack_rows(const Cols &cols, int nc, int bits, const uint32_t *perm, int64_t n, uint64_t *keys,
+                     cudaStream_t st) {
+    if (n <= 0) return GSMAT_OK;
+    KernelTimer t("pack_rows", st, (double)n * (4.0 * nc + 8.0 + (perm ? 4.0 : 0.0)), (double)n);
+    pack_rows_kernel<<<grid_1d(n, 256), 256, 0, st>>>(cols, nc, bits, perm, n, keys);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_iota(uint32_t *v, int64_t n, cudaStream_t st) {
+    if (n <= 0) return GSMAT_OK;
+    iota_u32_kernel<<<grid_1d(n, 256), 256, 0, st>>>(v, n);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+int launch_gather_rows(const Cols &in, int k, const uint32_t *perm, int64_t n, OutCols out, cudaStream_t st) {
+    if (n <= 0) return GSMAT_OK;
+    KernelTimer t("gather_rows", st, (double)n * (4.0 + 8.0 * k), (double)n);
+    gather_rows_kernel<<<grid_1d(n, 256), 256, 0, st>>>(in, k, perm, n, out);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_interleave(const Cols &in, int k, int64_t n, int32_t *dst, cudaStream_t st) {
+    if (n <= 0 || k <= 0) return GSMAT_OK;
+    interleave_kernel<<<grid_1d(n, 256), 256, 0, st>>>(in, k, n, dst);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+int launch_copy_cols(const Cols &in, int k, int64_t n, OutCols out, cudaStream_t st) {
+    if (n <= 0 || k <= 0) return GSMAT_OK;
+    copy_cols_kernel<<<grid_1d(n, 256), 256, 0, st>>>(in, k, n, out);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,68 @@
+// Join kernels of one SM-based join step (Alg. 3) and their launchers.
+#pragma once
+
+#include "common.cuh"
+
+namespace gs {
+
+constexpr int kMaxCols = 32;
+
+// Column set of a binding table (structure of arrays, int32 columns).
+struct Cols {
+    const int32_t *c[kMaxCols];
+};
+struct OutCols {
+    int32_t *c[kMaxCols];
+};
+
+// A value that comes from a table column or is a constant.
+struct ValueSrc {
+    const int32_t *col;  // null -> constant
+    int32_t constant;
+    __device__ __forceinline__ int32_t at(int64_t i) const { return col ? col[i] : constant; }
+};
+
+// Count + exclusive scan (Alg. 4): for every input row i, N_i = size of the
+// row of x_i on the given side of the predicate, first_i = its first entry;
+// off[i] = sum of N_j for j < i, off[n] = total; *d_total = total.
+int launch_count_scan(const StoreView &sv, int side, const PredSide &ps, const int32_t *x, int64_t n, int64_t *off,
+                      int32_t *first, int64_t *d_total, int *err, cudaStream_t st);
+
+// Gather-expand: output row j of [0, total) = parent row r (off[r] <= j <
+// off[r+1]) with its k columns copied, plus the new column
+// val[first_r + j - off[r]] appended as column k.
+int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t n_in, const int64_t *off,
+                  const int32_t *first, int64_t total, OutCols out, cudaStream_t st);
+
+// Membership filter + compaction: keep row i iff (s_i, o_i) is an entry of
+// the predicate (s_i, o_i from columns or constants); surviving rows' k
+// columns are written in order to `out`; *d_count = survivors.
+int launch_filter(const StoreView &sv, const PredSide &ps_s, const PredSide &ps_o, ValueSrc s, ValueSrc o,
+                  const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st);
+
+// Cartesian product: output row j = (input row j / m, relation row j % m);
+// the relation has r_cols (1 or 2) columns of length m.
+int launch_cross(const Cols &in, int k, int64_t n_in, const Cols &rel, int r_cols, int64_t m, OutCols out,
+                 cudaStream_t st);
+
+// Entries of one predicate (side 0) with key == val, as one column.
+int launch_diag(const StoreView &sv, const PredSide &ps0, int32_t *out, int64_t *d_count, int *err, cudaStream_t st);
+
+// Row ranges of constants: for request i, (first, last) of row x[i] of
+// predicate slot ps[i] on side sd[i]; requests with slot < 0 give (0, 0).
+int launch_const_lookup(const StoreView &sv, const PredSide *d_sides, int n_pred, const int32_t *d_req, int n_req,
+                        int32_t *d_out, cudaStream_t st);
+
+// keys[i] = columns cols[0..nc) of row perm[i] (or row i if perm is null)
+// packed most-significant first with `bits` bits each.
+int launch_pack_rows(const Cols &cols, int nc, int bits, const uint32_t *perm, int64_t n, uint64_t *keys,
+                     cudaStream_t st);
+int launch_iota(uint32_t *v, int64_t n, cudaStream_t st);
+// out[c][i] = in[c][perm[i]] for c < k.
+int launch_gather_rows(const Cols &in, int k, const uint32_t *perm, int64_t n, OutCols out, cudaStream_t st);
+// dst[i * k + c] = in[c][i] (row-major interleave).
+int launch_interleave(const Cols &in, int k, int64_t n, int32_t *dst, cudaStream_t st);
+// out[c][i] = in[c][i] (copy k columns).
+int launch_copy_cols(const Cols &in, int k, int64_t n, OutCols out, cudaStream_t st);
+
+}  // namespace gs

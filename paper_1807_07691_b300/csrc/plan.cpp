@@ -1,0 +1,121 @@
+// Host query planner: Alg. 1 ("Query Plan Generated", Sec. 6.2.2) and the
+// accumulated intermediate-size estimate of Sec. 6.2.1.
+//
+// Alg. 1 as printed resets its scan index on every iteration and removes a
+// pattern in both branches; the prose of Sec. 6.2.1 (steps 1-4) is followed:
+//  1. sort the patterns by their statistic (stable: ties keep input order);
+//  2. take the smallest;
+//  3. take, in sorted order, the first remaining pattern that shares a
+//     variable with the patterns taken so far (constants do not connect);
+//  4. repeat; if no remaining pattern shares a variable (a disconnected
+//     BGP), take the smallest remaining one -- a Cartesian product.
+// The estimate starts from 1 and multiplies, per step, by the key (CROSS,
+// or EXPAND from a constant), by the average row size nnz / nr on the bound
+// side (EXPAND from a variable), or by min(1, nnz / (nr_s * nr_o)) (FILTER);
+// the cost is the sum of the running estimates, the quantity Thm. 1 and
+// Thm. 2 bound.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "plan.h"
+
+namespace gs {
+
+namespace {
+
+uint64_t vars_of(const gsmat_pattern &p) {
+    uint64_t m = 0;
+    if (p.s_var) m |= uint64_t(1) << p.s;
+    if (p.o_var) m |= uint64_t(1) << p.o;
+    return m;
+}
+
+}  // namespace
+
+int step_kind(const gsmat_pattern &p, uint64_t bound) {
+    const bool s_known = !p.s_var || ((bound >> p.s) & 1);
+    const bool o_known = !p.o_var || ((bound >> p.o) & 1);
+    if (s_known && o_known) return GSMAT_STEP_FILTER;
+    if (s_known) return GSMAT_STEP_EXPAND_S;
+    if (o_known) return GSMAT_STEP_EXPAND_O;
+    return GSMAT_STEP_CROSS;
+}
+
+int plan_bgp(const gsmat_pattern *pats, int n, const int64_t *keys, const gsmat_pred_stats *stats, int32_t *order,
+             int32_t *kinds, double *est) {
+    std::vector<int> L(n);
+    for (int i = 0; i < n; ++i) L[i] = i;
+    std::stable_sort(L.begin(), L.end(), [&](int a, int b) { return keys[a] < keys[b]; });
+    uint64_t N = 0;
+    for (int step = 0; step < n; ++step) {
+        size_t pick = 0;
+        if (step > 0) {
+            pick = L.size();
+            for (size_t t = 0; t < L.size(); ++t) {
+                if (vars_of(pats[L[t]]) & N) {
+                    pick = t;
+                    break;
+                }
+            }
+            if (pick == L.size()) pick = 0;
+        }
+        order[step] = L[pick];
+        N |= vars_of(pats[L[pick]]);
+        L.erase(L.begin() + (long)pick);
+    }
+    uint64_t bound = 0;
+    double e = 1.0;
+    for (int step = 0; step < n; ++step) {
+        const int i = order[step];
+        const gsmat_pattern &p = pats[i];
+        const int kind = step_kind(p, bound);
+        const double nnz = (double)stats[i].nnz, nr_s = (double)stats[i].nr_s, nr_o = (double)stats[i].nr_o;
+        double f;
+        if (kind == GSMAT_STEP_CROSS) {
+            f = (double)keys[i];
+        } else if (kind == GSMAT_STEP_FILTER) {
+            f = (nr_s > 0 && nr_o > 0) ? std::min(1.0, nnz / (nr_s * nr_o)) : 0.0;
+        } else if (kind == GSMAT_STEP_EXPAND_S) {
+            f = !p.s_var ? (double)keys[i] : (nr_s > 0 ? nnz / nr_s : 0.0);
+        } else {
+            f = !p.o_var ? (double)keys[i] : (nr_o > 0 ? nnz / nr_o : 0.0);
+        }
+        e = e * f;
+        if (kinds) kinds[step] = kind;
+        if (est) est[step] = e;
+        bound |= vars_of(p);
+    }
+    return GSMAT_OK;
+}
+
+int validate_bgp(const gsmat_pattern *pats, int n_pats, int n_vars) {
+    if (!pats || n_pats < 1 || n_pats > GSMAT_MAX_PATTERNS) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "n_pats = %d (1..%d)", n_pats, GSMAT_MAX_PATTERNS);
+    }
+    if (n_vars < 0 || n_vars > 32) return set_error(GSMAT_ERR_INVALID_ARG, "n_vars = %d (0..32)", n_vars);
+    uint64_t used = 0;
+    for (int i = 0; i < n_pats; ++i) {
+        const gsmat_pattern &p = pats[i];
+        if (p.p_var) return set_error(GSMAT_ERR_UNSUPPORTED, "pattern %d has a variable predicate", i);
+        if (p.p < 0) return set_error(GSMAT_ERR_INVALID_ARG, "pattern %d: negative predicate id", i);
+        const int32_t ends[2] = {p.s, p.o};
+        const uint8_t isv[2] = {p.s_var, p.o_var};
+        for (int e = 0; e < 2; ++e) {
+            if (isv[e]) {
+                if (ends[e] < 0 || ends[e] >= n_vars) {
+                    return set_error(GSMAT_ERR_INVALID_ARG, "pattern %d: variable %d out of range", i, ends[e]);
+                }
+                used |= uint64_t(1) << ends[e];
+            } else if (ends[e] < 0) {
+                return set_error(GSMAT_ERR_INVALID_ARG, "pattern %d: negative constant", i);
+            }
+        }
+    }
+    const uint64_t all = n_vars == 0 ? 0 : (n_vars == 64 ? ~uint64_t(0) : ((uint64_t(1) << n_vars) - 1));
+    if (used != all) return set_error(GSMAT_ERR_INVALID_ARG, "a variable in 0..%d is used by no pattern", n_vars - 1);
+    return GSMAT_OK;
+}
+
+}  // namespace gs

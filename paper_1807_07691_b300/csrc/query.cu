@@ -1,0 +1,445 @@
+// Query executor: Alg. 2 ("Query Execution", Sec. 6.3) over the plan of
+// Alg. 1, one SM-based join (Alg. 3) per step, all on one stream.
+//
+// The running relation starts as the relation with one empty assignment;
+// each plan step joins it with the next pattern's matrix:
+//   FILTER   both ends known      -> membership filter + compaction
+//   EXPAND   one end known        -> count + scan (Alg. 4), gather-expand
+//            (from a constant: a Cartesian product with that row)
+//   CROSS    no end known         -> Cartesian product with M_p (or with its
+//                                    diagonal for ?x p ?x)
+// A step whose input is the one-row, zero-column start relation returns the
+// pattern's relation itself, as a view of the store (no copy).  Results are
+// kept in plan column order, ascending (expansion preserves parent order and
+// every row's entries are sorted), and reordered to variable order at the
+// end by a stable radix sort on the few leading variables that need it.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "join.cuh"
+#include "plan.h"
+#include "query.cuh"
+#include "store.cuh"
+
+namespace gs {
+
+namespace {
+
+struct Tbl {
+    int64_t rows = 0;
+    int ncols = 0;
+    int32_t vars[kMaxCols];
+    const int32_t *col[kMaxCols];
+    DevBuf buf;  // owning storage; empty when the columns are a view of the store
+
+    Cols cols() const {
+        Cols c;
+        for (int i = 0; i < kMaxCols; ++i) c.c[i] = i < ncols ? col[i] : nullptr;
+        return c;
+    }
+    int col_of(int32_t var) const {
+        for (int i = 0; i < ncols; ++i) if (vars[i] == var) return i;
+        return -1;
+    }
+};
+
+// Allocate ncols columns of `rows` rows (each 256-byte aligned).
+int alloc_cols(Tbl &t, int ncols, int64_t rows, cudaStream_t st, OutCols *out) {
+    const size_t stride = round_up((size_t)(rows > 0 ? rows : 1), 64);
+    GS_TRY(t.buf.alloc(sizeof(int32_t) * stride * (size_t)(ncols > 0 ? ncols : 1), st));
+    t.ncols = ncols;
+    t.rows = rows;
+    for (int c = 0; c < kMaxCols; ++c) {
+        int32_t *p = c < ncols ? t.buf.as<int32_t>() + stride * c : nullptr;
+        if (out) out->c[c] = p;
+        if (c < ncols) t.col[c] = p;
+    }
+    return GSMAT_OK;
+}
+
+struct Ctx {
+    const gsmat_store *S;
+    cudaStream_t st;
+    DevBuf qstat;  // [0] count / total, [1] error word (int)
+    int64_t *h = nullptr;
+
+    int64_t *d_count() { return qstat.as<int64_t>(); }
+    int *d_err() { return reinterpret_cast<int *>(qstat.as<int64_t>() + 1); }
+
+    // Read the count word and the error word; synchronises the stream.
+    int read_count(int64_t *count) {
+        GS_CUDA(cudaMemcpyAsync(h, qstat.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+        if (*reinterpret_cast<int *>(h + 1)) return set_error(GSMAT_ERR_DEVICE_CHECK, "a bounded wait expired");
+        *count = h[0];
+        return GSMAT_OK;
+    }
+};
+
+// Stable reorder of rows by the first m variables (variable order), then
+// columns in variable order.  Input rows ascend in plan column order.
+int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
+    const int V = t.ncols;
+    int32_t colof[kMaxCols];
+    for (int v = 0; v < V; ++v) colof[v] = t.col_of(v);
+    // smallest m: dropping variables 0..m-1 from the column order leaves
+    // m, m+1, ..., V-1 in order (stable sort by a key over an input sorted
+    // by S yields order (key, S))
+    int m = V;
+    for (int cand = 0; cand <= V; ++cand) {
+        int want = cand;
+        bool ok = true;
+        for (int c = 0; c < V && ok; ++c) {
+            if (t.vars[c] < cand) continue;
+            if (t.vars[c] != want) ok = false;
+            want++;
+        }
+        if (ok) {
+            m = cand;
+            break;
+        }
+    }
+    out.rows = t.rows;
+    out.ncols = V;
+    if (t.rows <= 1 || m == 0) {
+        // only the column order changes
+        for (int v = 0; v < V; ++v) {
+            out.vars[v] = v;
+            out.col[v] = t.col[colof[v]];
+        }
+        out.buf = std::move(t.buf);
+        return GSMAT_OK;
+    }
+    const int64_t n = t.rows;
+    const int bits = std::max(1, bits_for((uint64_t)std::max(cx.S->max_entity, 0)));
+    const int per_key = 64 / bits;
+    DevBuf keys, perm;
+    GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, cx.st));
+    GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)n, cx.st));
+    bool first = true;
+    for (int e = m; e > 0;) {
+        const int b = std::max(0, e - per_key);
+        Cols kc;
+        for (int v = b; v < e; ++v) kc.c[v - b] = t.col[colof[v]];
+        const int nc = e - b;
+        if (first) {
+            GS_TRY(launch_iota(perm.as<uint32_t>(), n, cx.st));
+            GS_TRY(launch_pack_rows(kc, nc, bits, nullptr, n, keys.as<uint64_t>(), cx.st));
+            first = false;
+        } else {
+            GS_TRY(launch_pack_rows(kc, nc, bits, perm.as<uint32_t>(), n, keys.as<uint64_t>(), cx.st));
+        }
+        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, nc * bits, cx.st));
+        e = b;
+    }
+    keys.release();
+    OutCols oc;
+    GS_TRY(alloc_cols(out, V, n, cx.st, &oc));
+    Cols in;
+    for (int v = 0; v < V; ++v) {
+        in.c[v] = t.col[colof[v]];
+        out.vars[v] = v;
+    }
+    GS_TRY(launch_gather_rows(in, V, perm.as<uint32_t>(), n, oc, cx.st));
+    return GSMAT_OK;
+}
+
+int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
+        gsmat_table *T) {
+    GS_TRY(validate_bgp(pats, n_pats, n_vars));
+    if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY)) return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    Ctx cx;
+    cx.S = S;
+    cx.st = st;
+    cx.h = pinned_scratch(4 + 4 * GSMAT_MAX_PATTERNS);
+    if (!cx.h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    GS_TRY(cx.qstat.alloc(4 * sizeof(int64_t), st));
+    GS_CUDA(cudaMemsetAsync(cx.qstat.p, 0, 4 * sizeof(int64_t), st));
+
+    // predicate slots, statistics and constant rows
+    std::vector<int32_t> slot(n_pats);
+    std::vector<gsmat_pred_stats> stats(n_pats);
+    std::vector<int64_t> keys(n_pats);
+    std::vector<int> req_s(n_pats, -1), req_o(n_pats, -1);
+    std::vector<int32_t> req;
+    bool absent = false;
+    for (int i = 0; i < n_pats; ++i) {
+        slot[i] = S->slot_of(pats[i].p);
+        memset(&stats[i], 0, sizeof(stats[i]));
+        stats[i].pred_id = pats[i].p;
+        if (slot[i] < 0) {
+            absent = true;
+            continue;
+        }
+        stats[i].nnz = S->side[0][slot[i]].nnz;
+        stats[i].nr_s = S->side[0][slot[i]].nrows;
+        stats[i].nr_o = S->side[1][slot[i]].nrows;
+        if (!pats[i].s_var) {
+            req_s[i] = (int)req.size() / 3;
+            req.insert(req.end(), {slot[i], 0, pats[i].s});
+        }
+        if (!pats[i].o_var) {
+            req_o[i] = (int)req.size() / 3;
+            req.insert(req.end(), {slot[i], 1, pats[i].o});
+        }
+    }
+    const int n_req = (int)req.size() / 3;
+    std::vector<int32_t> rng(2 * (size_t)n_req);
+    if (n_req > 0 && !absent) {
+        DevBuf d_req;
+        GS_TRY(d_req.alloc(sizeof(int32_t) * (req.size() + rng.size()), st));
+        int32_t *hreq = reinterpret_cast<int32_t *>(cx.h + 4);
+        memcpy(hreq, req.data(), sizeof(int32_t) * req.size());
+        GS_CUDA(cudaMemcpyAsync(d_req.p, hreq, sizeof(int32_t) * req.size(), cudaMemcpyHostToDevice, st));
+        int32_t *d_out = d_req.as<int32_t>() + req.size();
+        GS_TRY(launch_const_lookup(S->view, S->pred_side_dev.as<PredSide>(), S->n_pred, d_req.as<int32_t>(), n_req,
+                                   d_out, st));
+        GS_CUDA(cudaMemcpyAsync(hreq, d_out, sizeof(int32_t) * rng.size(), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+        memcpy(rng.data(), hreq, sizeof(int32_t) * rng.size());
+    }
+    auto row_len = [&](int r) -> int64_t { return r < 0 ? 0 : (int64_t)rng[2 * r + 1] - rng[2 * r]; };
+    for (int i = 0; i < n_pats; ++i) {
+        if (slot[i] < 0) {
+            keys[i] = 0;
+        } else if (!pats[i].s_var && !pats[i].o_var) {
+            keys[i] = std::min(row_len(req_s[i]), row_len(req_o[i]));
+        } else if (!pats[i].s_var) {
+            keys[i] = row_len(req_s[i]);
+        } else if (!pats[i].o_var) {
+            keys[i] = row_len(req_o[i]);
+        } else {
+            keys[i] = stats[i].nnz;
+        }
+    }
+    gsmat_query_stats &qs = T->stats;
+    memset(&qs, 0, sizeof(qs));
+    qs.n_steps = n_pats;
+    GS_TRY(plan_bgp(pats, n_pats, keys.data(), stats.data(), qs.order, qs.kind, qs.est_rows));
+    for (int s = 0; s < n_pats; ++s) {
+        qs.est_cost += qs.est_rows[s];
+        qs.rows[s] = -1;
+    }
+    // variables in the order the plan binds them
+    std::vector<int32_t> plan_vars;
+    {
+        uint64_t seen = 0;
+        for (int s = 0; s < n_pats; ++s) {
+            const gsmat_pattern &p = pats[qs.order[s]];
+            if (p.s_var && !((seen >> p.s) & 1)) { plan_vars.push_back(p.s); seen |= uint64_t(1) << p.s; }
+            if (p.o_var && !((seen >> p.o) & 1)) { plan_vars.push_back(p.o); seen |= uint64_t(1) << p.o; }
+        }
+    }
+
+    Tbl cur;
+    cur.rows = absent ? 0 : 1;  // one empty assignment
+    cur.ncols = 0;
+    const bool count_only = (flags & GSMAT_COUNT_ONLY) != 0;
+    for (int step = 0; step < n_pats && cur.rows > 0; ++step) {
+        const gsmat_pattern &p = pats[qs.order[step]];
+        const int kind = qs.kind[step];
+        const PredSide &ps0 = S->side[0][slot[qs.order[step]]];
+        const PredSide &ps1 = S->side[1][slot[qs.order[step]]];
+        const bool last = step == n_pats - 1;
+        const bool unit = cur.rows == 1 && cur.ncols == 0;
+        Tbl nxt;
+        if (kind == GSMAT_STEP_FILTER) {
+            ValueSrc vs{p.s_var ? cur.col[cur.col_of(p.s)] : nullptr, p.s_var ? 0 : p.s};
+            ValueSrc vo{p.o_var ? cur.col[cur.col_of(p.o)] : nullptr, p.o_var ? 0 : p.o};
+            OutCols oc;
+            const int keep = (count_only && last) ? 0 : cur.ncols;
+            GS_TRY(alloc_cols(nxt, cur.ncols, cur.rows, st, &oc));
+            GS_TRY(launch_filter(S->view, ps0, ps1, vs, vo, cur.cols(), keep, cur.rows, oc, cx.d_count(), cx.d_err(), st));
+            int64_t cnt;
+            GS_TRY(cx.read_count(&cnt));
+            nxt.rows = cnt;
+            for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+        } else if (kind == GSMAT_STEP_EXPAND_S || kind == GSMAT_STEP_EXPAND_O) {
+            const int side = kind == GSMAT_STEP_EXPAND_S ? 0 : 1;
+            const PredSide &ps = side == 0 ? ps0 : ps1;
+            const bool from_var = side == 0 ? p.s_var : p.o_var;
+            const int32_t known = side == 0 ? p.s : p.o;
+            const int32_t newv = side == 0 ? p.o : p.s;
+            if (!from_var) {
+                // a constant's row: Cartesian product with it
+                const int r = side == 0 ? req_s[qs.order[step]] : req_o[qs.order[step]];
+                const int64_t first = rng[2 * r], m = row_len(r);
+                Cols rel;
+                rel.c[0] = S->view.side[side].val + first;
+                if (unit) {
+                    nxt.rows = m;
+                    nxt.ncols = 1;
+                    nxt.col[0] = rel.c[0];
+                } else {
+                    const int64_t total = cur.rows * m;
+                    if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "step %d: %lld rows", step, (long long)total);
+                    if (count_only && last) {
+                        nxt.rows = total;
+                        nxt.ncols = cur.ncols + 1;
+                    } else {
+                        OutCols oc;
+                        GS_TRY(alloc_cols(nxt, cur.ncols + 1, total, st, &oc));
+                        GS_TRY(launch_cross(cur.cols(), cur.ncols, cur.rows, rel, 1, m, oc, st));
+                    }
+                }
+                for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+                nxt.vars[cur.ncols] = newv;
+            } else {
+                const int xc = cur.col_of(known);
+                DevBuf off, fst;
+                GS_TRY(off.alloc(sizeof(int64_t) * (size_t)(cur.rows + 1), st));
+                GS_TRY(fst.alloc(sizeof(int32_t) * (size_t)cur.rows, st));
+                GS_TRY(launch_count_scan(S->view, side, ps, cur.col[xc], cur.rows, off.as<int64_t>(), fst.as<int32_t>(),
+                                         cx.d_count(), cx.d_err(), st));
+                int64_t total;
+                GS_TRY(cx.read_count(&total));
+                if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "step %d: %lld rows", step, (long long)total);
+                if (count_only && last) {
+                    nxt.rows = total;
+                    nxt.ncols = cur.ncols + 1;
+                } else {
+                    OutCols oc;
+                    GS_TRY(alloc_cols(nxt, cur.ncols + 1, total, st, &oc));
+                    GS_TRY(launch_expand(S->view, side, cur.cols(), cur.ncols, cur.rows, off.as<int64_t>(),
+                                         fst.as<int32_t>(), total, oc, st));
+                }
+                for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+                nxt.vars[cur.ncols] = newv;
+            }
+        } else {  // CROSS
+            Cols rel;
+            int rc;
+            int64_t m;
+            DevBuf diag;
+            int32_t rv[2];
+            if (p.s == p.o) {  // ?x p ?x
+                GS_TRY(diag.alloc(sizeof(int32_t) * (size_t)(ps0.nnz > 0 ? ps0.nnz : 1), st));
+                GS_TRY(launch_diag(S->view, ps0, diag.as<int32_t>(), cx.d_count(), cx.d_err(), st));
+                GS_TRY(cx.read_count(&m));
+                rel.c[0] = diag.as<int32_t>();
+                rc = 1;
+                rv[0] = p.s;
+            } else {
+                rel.c[0] = S->view.side[0].key + ps0.ent_base;
+                rel.c[1] = S->view.side[0].val + ps0.ent_base;
+                m = ps0.nnz;
+                rc = 2;
+                rv[0] = p.s;
+                rv[1] = p.o;
+            }
+            if (unit) {
+                nxt.rows = m;
+                nxt.ncols = rc;
+                for (int c = 0; c < rc; ++c) nxt.col[c] = rel.c[c];
+                nxt.buf = std::move(diag);  // owns the diagonal when there is one
+            } else {
+                const int64_t total = cur.rows * m;
+                if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "step %d: %lld rows", step, (long long)total);
+                if (count_only && last) {
+                    nxt.rows = total;
+                    nxt.ncols = cur.ncols + rc;
+                } else {
+                    OutCols oc;
+                    GS_TRY(alloc_cols(nxt, cur.ncols + rc, total, st, &oc));
+                    GS_TRY(launch_cross(cur.cols(), cur.ncols, cur.rows, rel, rc, m, oc, st));
+                }
+            }
+            for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+            for (int c = 0; c < rc; ++c) nxt.vars[cur.ncols + c] = rv[c];
+        }
+        cur = std::move(nxt);
+        qs.rows[step] = cur.rows;
+    }
+
+    // result
+    const int64_t rows = cur.rows;
+    qs.result_rows = rows;
+    if (count_only) {
+        T->rows = rows;
+        T->ncols = 0;
+        return GSMAT_OK;
+    }
+    if (rows == 0 || cur.ncols != n_vars) {
+        // empty result (possibly before every variable was bound)
+        T->rows = 0;
+        T->ncols = n_vars;
+        for (int c = 0; c < n_vars; ++c) {
+            T->vars[c] = (flags & GSMAT_PLAN_ORDER) ? plan_vars[c] : c;
+            T->col[c] = nullptr;
+        }
+        return GSMAT_OK;
+    }
+    Tbl fin;
+    if (flags & GSMAT_PLAN_ORDER) {
+        fin.rows = cur.rows;
+        fin.ncols = cur.ncols;
+        for (int c = 0; c < cur.ncols; ++c) {
+            fin.vars[c] = cur.vars[c];
+            fin.col[c] = cur.col[c];
+        }
+        fin.buf = std::move(cur.buf);
+    } else {
+        GS_TRY(canonical_order(cx, cur, fin));
+    }
+    // the result owns its columns (a view of the store is copied)
+    if (!fin.buf.p && fin.ncols > 0) {
+        Tbl own;
+        OutCols oc;
+        GS_TRY(alloc_cols(own, fin.ncols, fin.rows, st, &oc));
+        GS_TRY(launch_copy_cols(fin.cols(), fin.ncols, fin.rows, oc, st));
+        for (int c = 0; c < fin.ncols; ++c) own.vars[c] = fin.vars[c];
+        fin = std::move(own);
+    }
+    T->rows = fin.rows;
+    T->ncols = fin.ncols;
+    for (int c = 0; c < fin.ncols; ++c) {
+        T->vars[c] = fin.vars[c];
+        T->col[c] = fin.col[c];
+    }
+    T->storage = std::move(fin.buf);
+    return GSMAT_OK;
+}
+
+}  // namespace
+
+int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
+              gsmat_table **out) {
+    if (!S || !out) return set_error(GSMAT_ERR_INVALID_ARG, "store or out is NULL");
+    *out = nullptr;
+    gsmat_table *T = new gsmat_table();
+    int rc = run(S, pats, n_pats, n_vars, flags, st, T);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == GSMAT_OK && e != cudaSuccess) rc = set_error(GSMAT_ERR_CUDA, "query: %s", cudaGetErrorString(e));
+    profile_flush();
+    if (rc != GSMAT_OK) {
+        delete T;
+        return rc;
+    }
+    T->storage.st = nullptr;  // freed on the legacy stream later
+    *out = T;
+    return GSMAT_OK;
+}
+
+int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st) {
+    if (!T || (!dst && T->rows > 0 && T->ncols > 0)) return set_error(GSMAT_ERR_INVALID_ARG, "table or dst is NULL");
+    const int64_t n = T->rows;
+    const int k = T->ncols;
+    if (n == 0 || k == 0) return GSMAT_OK;
+    Cols in;
+    for (int c = 0; c < kMaxCols; ++c) in.c[c] = c < k ? T->col[c] : nullptr;
+    if (dst_on_device) {
+        GS_TRY(launch_interleave(in, k, n, dst, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+        return GSMAT_OK;
+    }
+    DevBuf tmp;
+    GS_TRY(tmp.alloc(sizeof(int32_t) * (size_t)n * k, st));
+    GS_TRY(launch_interleave(in, k, n, tmp.as<int32_t>(), st));
+    GS_CUDA(cudaMemcpyAsync(dst, tmp.p, sizeof(int32_t) * (size_t)n * k, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GSMAT_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,21 @@
+// Result tables and the query entry points shared with the C ABI layer.
+#pragma once
+
+#include "common.cuh"
+
+struct gsmat_table {
+    int64_t rows = 0;
+    int32_t ncols = 0;
+    int32_t vars[32] = {0};
+    const int32_t *col[32] = {nullptr};
+    gs::DevBuf storage;  // owns the columns
+    gsmat_query_stats stats{};
+};
+
+namespace gs {
+
+int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
+              gsmat_table **out);
+int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st);
+
+}  // namespace gs

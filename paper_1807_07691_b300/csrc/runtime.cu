@@ -1,0 +1,230 @@
+// Process-wide runtime of libgsmat: error records, the allocator hook,
+// pinned host scratch and the kernel-timing registry.
+#include <stdarg.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// errors
+
+static thread_local std::string t_last_error;
+
+int set_error(int status, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return status;
+}
+
+void clear_error() { t_last_error.clear(); }
+
+const char *last_error() { return t_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// allocator hook
+
+static std::mutex g_alloc_mu;
+static gsmat_alloc_fn g_alloc = nullptr;
+static gsmat_free_fn g_free = nullptr;
+static void *g_alloc_ctx = nullptr;
+static bool g_pool_configured[64] = {false};
+
+static void configure_default_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    if (g_pool_configured[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        // keep freed blocks in the pool instead of returning them at every sync
+        uint64_t threshold = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+    }
+    g_pool_configured[dev] = true;
+}
+
+void *dev_alloc_raw(size_t bytes, cudaStream_t st) {
+    gsmat_alloc_fn a;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        ctx = g_alloc_ctx;
+        if (!a) configure_default_pool();
+    }
+    // 256-byte alignment is guaranteed by both cudaMallocAsync and the
+    // documented contract of the hook.
+    if (a) return a(bytes, ctx, (gsmat_stream_t)st);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free_raw(void *p, cudaStream_t st) {
+    if (!p) return;
+    gsmat_free_fn f;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_free;
+        ctx = g_alloc_ctx;
+    }
+    if (f) {
+        f(p, ctx, (gsmat_stream_t)st);
+        return;
+    }
+    cudaFreeAsync(p, st);
+}
+
+int set_allocator(gsmat_alloc_fn a, gsmat_free_fn f, void *ctx) {
+    if ((a == nullptr) != (f == nullptr)) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "alloc and free must both be set or both be NULL");
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = a;
+    g_free = f;
+    g_alloc_ctx = a ? ctx : nullptr;
+    return GSMAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pinned host scratch
+
+int64_t *pinned_scratch(int n_words) {
+    struct Holder {
+        int64_t *p = nullptr;
+        int cap = 0;
+        ~Holder() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    static thread_local Holder h;
+    if (h.cap < n_words) {
+        if (h.p) cudaFreeHost(h.p);
+        h.p = nullptr;
+        h.cap = 0;
+        int cap = n_words < 64 ? 64 : n_words;
+        if (cudaMallocHost((void **)&h.p, sizeof(int64_t) * (size_t)cap) != cudaSuccess) {
+            cudaGetLastError();
+            h.p = nullptr;
+            return nullptr;
+        }
+        h.cap = cap;
+    }
+    return h.p;
+}
+
+// ---------------------------------------------------------------------------
+// kernel timing
+
+struct ProfAgg {
+    int64_t launches = 0;
+    double ms = 0, bytes = 0, items = 0;
+};
+
+static std::mutex g_prof_mu;
+static std::map<std::string, ProfAgg> g_prof;
+static volatile bool g_prof_on = false;
+
+struct PendingTimer {
+    const char *name;
+    cudaEvent_t a, b;
+    double bytes, items;
+};
+static thread_local std::vector<PendingTimer> t_pending;
+static thread_local std::vector<cudaEvent_t> t_event_pool;
+
+static cudaEvent_t get_event() {
+    if (!t_event_pool.empty()) {
+        cudaEvent_t e = t_event_pool.back();
+        t_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+bool profile_on() { return g_prof_on; }
+
+KernelTimer::KernelTimer(const char *n, cudaStream_t s, double algo_bytes, double n_items)
+    : name(n), st(s), bytes(algo_bytes), items(n_items) {
+    if (!g_prof_on) return;
+    a = get_event();
+    b = get_event();
+    if (!a || !b) {
+        a = b = nullptr;
+        return;
+    }
+    cudaEventRecord(a, st);
+}
+
+void KernelTimer::stop() {
+    if (!a) return;
+    cudaEventRecord(b, st);
+    t_pending.push_back({name, a, b, bytes, items});
+    a = b = nullptr;
+}
+
+void profile_flush() {
+    if (t_pending.empty()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &p : t_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &g = g_prof[p.name];
+            g.launches++;
+            g.ms += ms;
+            g.bytes += p.bytes;
+            g.items += p.items;
+        } else {
+            cudaGetLastError();
+        }
+        t_event_pool.push_back(p.a);
+        t_event_pool.push_back(p.b);
+    }
+    t_pending.clear();
+}
+
+int profile_enable(int on) {
+    g_prof_on = on != 0;
+    return GSMAT_OK;
+}
+
+int profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset) {
+    profile_flush();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int32_t n = 0;
+    for (auto &kv : g_prof) {
+        if (out && n < cap) {
+            gsmat_kernel_profile &o = out[n];
+            memset(&o, 0, sizeof(o));
+            strncpy(o.name, kv.first.c_str(), sizeof(o.name) - 1);
+            o.launches = kv.second.launches;
+            o.total_ms = kv.second.ms;
+            o.algo_bytes = kv.second.bytes;
+            o.items = kv.second.items;
+        }
+        n++;
+    }
+    if (n_out) *n_out = n;
+    if (reset) g_prof.clear();
+    return GSMAT_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,87 @@
+// Single-pass exclusive prefix sum (decoupled look-back) and a generic
+// stable selection of int32 values.  The scan is the offset computation of
+// the pre-allocation step of the GPU join (Sec. 7.2.2, Alg. 4: P_i =
+// P_{i-1} + N_{i-1}), done on the device in int64.
+#include "common.cuh"
+#include "select.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kScanBlock = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+// Shared-memory index with one padding word per 32, so that a thread
+// reading its kScanItems consecutive values hits distinct banks.
+__device__ __forceinline__ int padded(int i) { return i + (i >> 5); }
+
+__global__ void __launch_bounds__(kScanBlock) scan_i32_kernel(const int32_t *__restrict__ in, int64_t *__restrict__ out,
+                                                              int64_t n, LookbackScratch ls) {
+    __shared__ int tile_sm;
+    __shared__ int64_t scan_sm[kScanBlock / 32 + 1];
+    __shared__ int64_t prefix_sm;
+    __shared__ int32_t stage[kScanTile + kScanTile / 32];
+    const int tile = acquire_tile_id(ls, &tile_sm);
+    const int64_t t0 = (int64_t)tile * kScanTile;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int idx = j * kScanBlock + threadIdx.x;
+        const int64_t i = t0 + idx;
+        stage[padded(idx)] = i < n ? __ldg(in + i) : 0;
+    }
+    __syncthreads();
+    int32_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        v[j] = stage[padded(threadIdx.x * kScanItems + j)];
+        s += v[j];
+    }
+    int64_t tot;
+    const int64_t ex = block_exclusive_sum<kScanBlock>(s, scan_sm, &tot);
+    const int64_t pre = tile_lookback(ls, tile, tot, &prefix_sm);
+    int64_t run = pre + ex;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int64_t i = t0 + threadIdx.x * kScanItems + j;
+        if (i < n) out[i] = run;
+        run += v[j];
+    }
+    if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) out[n] = pre + tot;
+}
+
+struct SelectI32Op {
+    const int32_t *in;
+    const uint8_t *flags;
+    int32_t *out;
+    __device__ bool flag(int64_t i) const { return flags[i] != 0; }
+    __device__ void emit(int64_t i, int64_t j) const { out[j] = in[i]; }
+};
+
+}  // namespace
+
+int exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st, int *err_word) {
+    if (n < 0 || (n > 0 && !in) || !out) return set_error(GSMAT_ERR_INVALID_ARG, "scan: bad arguments");
+    if (n == 0) {
+        GS_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        return GSMAT_OK;
+    }
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > INT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "scan over %lld items", (long long)n);
+    LookbackBuf lb;
+    GS_TRY(lb.make(ntiles, st, err_word));
+    KernelTimer t("scan_i32", st, (double)n * 12.0, (double)n);
+    scan_i32_kernel<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, out, n, lb.view);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int select_flagged_i32(const int32_t *in, const uint8_t *flags, int32_t *out, int64_t n, int64_t *d_count,
+                       cudaStream_t st, int *err_word) {
+    SelectI32Op op{in, flags, out};
+    return run_select(op, n, d_count, st, err_word);
+}
+
+}  // namespace gs

@@ -1,0 +1,484 @@
+// Device storage builder (Sec. 5): from an int32 (s, p, o) triple multiset
+// to the per-predicate sparse matrices M_h, stored on both sides.
+//
+// Steps (Sec. 5.1 lists the paper's three: encode, build the cube, store
+// the cube per predicate with statistics; ids arrive already encoded):
+//  1. validate ids and find their ranges;
+//  2. the distinct predicates (radix sort + unique) -> predicate slots and
+//     the predicate hash index (host and device copies);
+//  3. sort the triples by (slot, s, o), drop repeats (a dataset is a set,
+//     Sec. 3.1) -> side 0 entries;
+//  4. sort the unique triples by (slot, o, s) -> side 1 entries;
+//  5. per side: non-zero rows (id, first entry) = the auxiliary arrays Row /
+//     Rpos of Sec. 6.3, per predicate its first entry, nnz (the statistic m)
+//     and first row; dense row pointers for predicates with many entries.
+#include <string.h>
+
+#include <algorithm>
+
+#include "select.cuh"
+#include "store.cuh"
+
+namespace gs {
+
+uint32_t pred_hash(int32_t p) { return (uint32_t)p * 2654435761u; }
+
+namespace {
+
+constexpr int kThreads = 256;
+
+unsigned grid_for(int64_t n) { return grid_1d(n, kThreads); }
+
+__global__ void init_ranges_kernel(int *r) {
+    r[0] = -1;         // max subject/object
+    r[1] = -1;         // max predicate
+    r[2] = INT32_MAX;  // min over all ids
+}
+
+__global__ void ranges_kernel(const int32_t *__restrict__ tri, int64_t n, int *r) {
+    int mx_so = -1, mx_p = -1, mn = INT32_MAX;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int s = tri[3 * i], p = tri[3 * i + 1], o = tri[3 * i + 2];
+        mx_so = max(mx_so, max(s, o));
+        mx_p = max(mx_p, p);
+        mn = min(mn, min(s, min(p, o)));
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        mx_so = max(mx_so, __shfl_xor_sync(0xffffffffu, mx_so, d));
+        mx_p = max(mx_p, __shfl_xor_sync(0xffffffffu, mx_p, d));
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&r[0], mx_so);
+        atomicMax(&r[1], mx_p);
+        atomicMin(&r[2], mn);
+    }
+}
+
+__global__ void extract_pred_kernel(const int32_t *__restrict__ tri, int64_t n, uint32_t *__restrict__ p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        p[i] = (uint32_t)tri[3 * i + 1];
+    }
+}
+
+struct DistinctU32Op {
+    const uint32_t *a;
+    int32_t *out;
+    __device__ bool flag(int64_t i) const { return i == 0 || a[i] != a[i - 1]; }
+    __device__ void emit(int64_t i, int64_t j) const { out[j] = (int32_t)a[i]; }
+};
+
+__device__ __forceinline__ int32_t hash_lookup(const int32_t *keys, const int32_t *vals, uint32_t mask, int32_t p) {
+    uint32_t h = ((uint32_t)p * 2654435761u) & mask;
+    while (true) {
+        const int32_t k = keys[h];
+        if (k == p) return vals[h];
+        if (k < 0) return -1;
+        h = (h + 1) & mask;
+    }
+}
+
+// Split the triples into s, o and predicate-slot columns.
+__global__ void split_kernel(const int32_t *__restrict__ tri, int64_t n, const int32_t *__restrict__ hkeys,
+                             const int32_t *__restrict__ hvals, uint32_t hmask, int32_t *__restrict__ s,
+                             int32_t *__restrict__ o, int32_t *__restrict__ slot) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        s[i] = tri[3 * i];
+        o[i] = tri[3 * i + 2];
+        slot[i] = hash_lookup(hkeys, hvals, hmask, tri[3 * i + 1]);
+    }
+}
+
+// key = slot << (2 bits) | a << bits | b
+__global__ void pack_kernel(const int32_t *__restrict__ a, const int32_t *__restrict__ b, const int32_t *__restrict__ c,
+                            int64_t n, int bits, uint64_t *__restrict__ keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        keys[i] = ((uint64_t)(uint32_t)c[i] << (2 * bits)) | ((uint64_t)(uint32_t)a[i] << bits) | (uint64_t)(uint32_t)b[i];
+    }
+}
+
+__global__ void unpack_kernel(const uint64_t *__restrict__ keys, int64_t n, int bits, int32_t *__restrict__ a,
+                              int32_t *__restrict__ b, int32_t *__restrict__ c) {
+    const uint64_t m = (bits >= 32) ? 0xffffffffull : ((1ull << bits) - 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        b[i] = (int32_t)(k & m);
+        a[i] = (int32_t)((k >> bits) & m);
+        c[i] = (int32_t)(k >> (2 * bits));
+    }
+}
+
+__global__ void iota_kernel(uint32_t *v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        v[i] = (uint32_t)i;
+    }
+}
+
+// keys[i] = x[perm[i]] (widened), or hi/lo packing of two columns.
+__global__ void gather_key_kernel(const int32_t *__restrict__ hi, const int32_t *__restrict__ lo, int lo_bits,
+                                  const uint32_t *__restrict__ perm, int64_t n, uint64_t *__restrict__ keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = perm ? perm[i] : (uint32_t)i;
+        uint64_t k = (uint64_t)(uint32_t)lo[r];
+        if (hi) k |= (uint64_t)(uint32_t)hi[r] << lo_bits;
+        keys[i] = k;
+    }
+}
+
+__global__ void gather3_kernel(const int32_t *__restrict__ a, const int32_t *__restrict__ b, const int32_t *__restrict__ c,
+                               const uint32_t *__restrict__ perm, int64_t n, int32_t *__restrict__ oa,
+                               int32_t *__restrict__ ob, int32_t *__restrict__ oc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = perm[i];
+        oa[i] = a[r];
+        ob[i] = b[r];
+        oc[i] = c[r];
+    }
+}
+
+// Drop adjacent repeats of sorted (c, a, b) rows.
+struct DedupeOp {
+    const int32_t *a, *b, *c;
+    int32_t *oa, *ob, *oc;
+    __device__ bool flag(int64_t i) const {
+        return i == 0 || a[i] != a[i - 1] || b[i] != b[i - 1] || c[i] != c[i - 1];
+    }
+    __device__ void emit(int64_t i, int64_t j) const {
+        oa[j] = a[i];
+        ob[j] = b[i];
+        oc[j] = c[i];
+    }
+};
+
+// Non-zero rows: the first entry of every (slot, key) run.
+struct RowStartOp {
+    const int32_t *key, *slot;
+    int32_t *rowid, *rowoff, *rowslot;
+    __device__ bool flag(int64_t i) const { return i == 0 || key[i] != key[i - 1] || slot[i] != slot[i - 1]; }
+    __device__ void emit(int64_t i, int64_t j) const {
+        rowid[j] = key[i];
+        rowoff[j] = (int32_t)i;
+        rowslot[j] = slot[i];
+    }
+};
+
+__global__ void pred_bounds_kernel(const int32_t *__restrict__ rowslot, const int32_t *__restrict__ rowoff, int64_t R,
+                                   int32_t *__restrict__ ent_base, int32_t *__restrict__ row_base) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < R; j += (int64_t)gridDim.x * blockDim.x) {
+        if (j == 0 || rowslot[j] != rowslot[j - 1]) {
+            ent_base[rowslot[j]] = rowoff[j];
+            row_base[rowslot[j]] = (int32_t)j;
+        }
+    }
+}
+
+// dense[x] = first entry of row x (or of the next non-empty row) for
+// x in [0, max_entity + 1].
+__global__ void dense_fill_kernel(const int32_t *__restrict__ rowid, const int32_t *__restrict__ rowoff, PredSide ps,
+                                  int32_t max_entity, int32_t *__restrict__ dense) {
+    const int64_t len = (int64_t)max_entity + 2;
+    const int32_t *ids = rowid + ps.row_base;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < len; x += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = ps.nrows;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ids[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        dense[x] = (lo < ps.nrows) ? rowoff[ps.row_base + lo] : ps.ent_base + ps.nnz;
+    }
+}
+
+// Sort rows (c, a, b) lexicographically; results into oa/ob/oc.
+int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, int id_bits, int slot_bits,
+               int32_t *oa, int32_t *ob, int32_t *oc, cudaStream_t st) {
+    if (n == 0) return GSMAT_OK;
+    const unsigned g = grid_for(n);
+    if (slot_bits + 2 * id_bits <= 64) {
+        DevBuf keys;
+        GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, st));
+        pack_kernel<<<g, kThreads, 0, st>>>(a, b, c, n, id_bits, keys.as<uint64_t>());
+        GS_LAUNCH_CHECK();
+        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, 0, slot_bits + 2 * id_bits, st));
+        unpack_kernel<<<g, kThreads, 0, st>>>(keys.as<uint64_t>(), n, id_bits, oa, ob, oc);
+        GS_LAUNCH_CHECK();
+        return GSMAT_OK;
+    }
+    // Wide ids: two stable passes, least significant field first.
+    DevBuf keys, perm;
+    GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, st));
+    GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)n, st));
+    iota_kernel<<<g, kThreads, 0, st>>>(perm.as<uint32_t>(), n);
+    gather_key_kernel<<<g, kThreads, 0, st>>>(nullptr, b, 0, nullptr, n, keys.as<uint64_t>());
+    GS_LAUNCH_CHECK();
+    GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, id_bits, st));
+    gather_key_kernel<<<g, kThreads, 0, st>>>(c, a, id_bits, perm.as<uint32_t>(), n, keys.as<uint64_t>());
+    GS_LAUNCH_CHECK();
+    GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, slot_bits + id_bits, st));
+    gather3_kernel<<<g, kThreads, 0, st>>>(a, b, c, perm.as<uint32_t>(), n, oa, ob, oc);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+// Build one side from entries sorted by (slot, key, val).
+int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t *slot, int64_t n, int *err,
+               cudaStream_t st) {
+    const int P = S->n_pred;
+    DevBuf rid, roff, rslot, cnt, bases;
+    GS_TRY(rid.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(roff.alloc(sizeof(int32_t) * (size_t)(n + 1), st));
+    GS_TRY(rslot.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(cnt.alloc(sizeof(int64_t), st));
+    RowStartOp op{key.as<int32_t>(), slot, rid.as<int32_t>(), roff.as<int32_t>(), rslot.as<int32_t>()};
+    GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
+    int64_t *h = pinned_scratch(4);
+    if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    const int64_t R = h[0];
+    // exact-size auxiliary arrays, rowoff with its sentinel
+    GS_TRY(S->rowid[side].alloc(sizeof(int32_t) * (size_t)R, st));
+    GS_TRY(S->rowoff[side].alloc(sizeof(int32_t) * (size_t)(R + 1), st));
+    if (R > 0) {
+        GS_CUDA(cudaMemcpyAsync(S->rowid[side].p, rid.p, sizeof(int32_t) * (size_t)R, cudaMemcpyDeviceToDevice, st));
+        GS_CUDA(cudaMemcpyAsync(S->rowoff[side].p, roff.p, sizeof(int32_t) * (size_t)R, cudaMemcpyDeviceToDevice, st));
+    }
+    const int32_t sentinel = (int32_t)n;
+    GS_CUDA(cudaMemcpyAsync(S->rowoff[side].as<int32_t>() + R, &sentinel, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // per predicate: first entry and first row
+    GS_TRY(bases.alloc(sizeof(int32_t) * 2 * (size_t)(P + 1), st));
+    int32_t *ent_base = bases.as<int32_t>(), *row_base = ent_base + (P + 1);
+    if (R > 0) {
+        pred_bounds_kernel<<<grid_for(R), kThreads, 0, st>>>(rslot.as<int32_t>(), roff.as<int32_t>(), R, ent_base,
+                                                             row_base);
+        GS_LAUNCH_CHECK();
+    }
+    std::vector<int32_t> hb(2 * (size_t)(P + 1));
+    GS_CUDA(cudaMemcpyAsync(hb.data(), bases.p, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    hb[P] = (int32_t)n;
+    hb[(P + 1) + P] = (int32_t)R;
+    S->side[side].resize(P);
+    for (int p = 0; p < P; ++p) {
+        PredSide &ps = S->side[side][p];
+        ps.ent_base = hb[p];
+        ps.nnz = hb[p + 1] - hb[p];
+        ps.row_base = hb[(P + 1) + p];
+        ps.nrows = hb[(P + 1) + p + 1] - hb[(P + 1) + p];
+        ps.dense_base = -1;
+    }
+    // dense row pointers where the array costs at most 4x the entries
+    const int64_t len = (int64_t)S->max_entity + 2;
+    int64_t total = 0;
+    for (int p = 0; p < P; ++p) {
+        PredSide &ps = S->side[side][p];
+        if (S->max_entity >= 0 && len <= 4 * (int64_t)ps.nnz) {
+            ps.dense_base = total;
+            total += len;
+        }
+    }
+    S->n_dense[side] = 0;
+    if (total > 0) {
+        GS_TRY(S->dense[side].alloc(sizeof(int32_t) * (size_t)total, st));
+        for (int p = 0; p < P; ++p) {
+            const PredSide &ps = S->side[side][p];
+            if (ps.dense_base < 0) continue;
+            S->n_dense[side]++;
+            dense_fill_kernel<<<grid_for(len), kThreads, 0, st>>>(S->rowid[side].as<int32_t>(),
+                                                                  S->rowoff[side].as<int32_t>(), ps, S->max_entity,
+                                                                  S->dense[side].as<int32_t>() + ps.dense_base);
+            GS_LAUNCH_CHECK();
+        }
+    }
+    S->key[side] = std::move(key);
+    S->val[side] = std::move(val);
+    return GSMAT_OK;
+}
+
+int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st, gsmat_store *S) {
+    S->n_input = n;
+    DevBuf d_tri_own, ranges, err;
+    const int32_t *tri = triples;
+    GS_TRY(err.alloc(sizeof(int), st));
+    GS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    if (n > 0 && !on_device) {
+        GS_TRY(d_tri_own.alloc(sizeof(int32_t) * 3 * (size_t)n, st));
+        GS_CUDA(cudaMemcpyAsync(d_tri_own.p, triples, sizeof(int32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, st));
+        tri = d_tri_own.as<int32_t>();
+    }
+    KernelTimer t_all("store_build", st, (double)n * 12.0, (double)n);
+    int64_t *h = pinned_scratch(8);
+    if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    // 1. ranges
+    GS_TRY(ranges.alloc(sizeof(int) * 4, st));
+    init_ranges_kernel<<<1, 1, 0, st>>>(ranges.as<int>());
+    if (n > 0) ranges_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, ranges.as<int>());
+    GS_LAUNCH_CHECK();
+    GS_CUDA(cudaMemcpyAsync(h, ranges.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    const int *hr = reinterpret_cast<const int *>(h);
+    if (n > 0 && hr[2] < 0) return set_error(GSMAT_ERR_INVALID_ARG, "negative id in triples (min %d)", hr[2]);
+    S->max_entity = n > 0 ? hr[0] : -1;
+    S->max_pred = n > 0 ? hr[1] : -1;
+    if (n == 0) {
+        for (int s = 0; s < 2; ++s) {
+            GS_TRY(S->rowoff[s].alloc(sizeof(int32_t), st));
+            GS_CUDA(cudaMemsetAsync(S->rowoff[s].p, 0, sizeof(int32_t), st));
+        }
+        S->hash_mask = 15;
+        S->hash_keys.assign(16, -1);
+        S->hash_vals.assign(16, -1);
+        return GSMAT_OK;
+    }
+    // 2. distinct predicates -> slots, hash index
+    {
+        DevBuf pcol, pdist, cnt;
+        GS_TRY(pcol.alloc(sizeof(uint32_t) * (size_t)n, st));
+        GS_TRY(pdist.alloc(sizeof(int32_t) * (size_t)n, st));
+        GS_TRY(cnt.alloc(sizeof(int64_t), st));
+        extract_pred_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, pcol.as<uint32_t>());
+        GS_LAUNCH_CHECK();
+        GS_TRY(radix_sort_u32(pcol.as<uint32_t>(), nullptr, n, 0, bits_for((uint64_t)S->max_pred), st));
+        DistinctU32Op op{pcol.as<uint32_t>(), pdist.as<int32_t>()};
+        GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err.as<int>()));
+        GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+        const int64_t P = h[0];
+        if (P <= 0 || P > INT32_MAX / 4) return set_error(GSMAT_ERR_CAPACITY, "%lld distinct predicates", (long long)P);
+        S->n_pred = (int32_t)P;
+        S->pred_ids.resize((size_t)P);
+        GS_CUDA(cudaMemcpyAsync(S->pred_ids.data(), pdist.p, sizeof(int32_t) * (size_t)P, cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+    }
+    {
+        uint32_t cap = 16;
+        while (cap < 2u * (uint32_t)S->n_pred) cap <<= 1;
+        S->hash_mask = cap - 1;
+        S->hash_keys.assign(cap, -1);
+        S->hash_vals.assign(cap, -1);
+        for (int32_t i = 0; i < S->n_pred; ++i) {
+            uint32_t hh = pred_hash(S->pred_ids[i]) & S->hash_mask;
+            while (S->hash_keys[hh] >= 0) hh = (hh + 1) & S->hash_mask;
+            S->hash_keys[hh] = S->pred_ids[i];
+            S->hash_vals[hh] = i;
+        }
+        GS_TRY(S->hash_dev.alloc(sizeof(int32_t) * 2 * cap, st));
+        GS_CUDA(cudaMemcpyAsync(S->hash_dev.p, S->hash_keys.data(), sizeof(int32_t) * cap, cudaMemcpyHostToDevice, st));
+        GS_CUDA(cudaMemcpyAsync(S->hash_dev.as<int32_t>() + cap, S->hash_vals.data(), sizeof(int32_t) * cap,
+                                cudaMemcpyHostToDevice, st));
+    }
+    const int id_bits = std::max(1, bits_for((uint64_t)S->max_entity));
+    const int slot_bits = bits_for((uint64_t)(S->n_pred - 1));
+    // 3. side 0: sort by (slot, s, o) and drop repeats
+    DevBuf s_raw, o_raw, slot_raw, s_sorted, o_sorted, slot_sorted, cnt;
+    GS_TRY(s_raw.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(o_raw.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(slot_raw.alloc(sizeof(int32_t) * (size_t)n, st));
+    {
+        const uint32_t cap = S->hash_mask + 1;
+        split_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, S->hash_dev.as<int32_t>(), S->hash_dev.as<int32_t>() + cap,
+                                                       S->hash_mask, s_raw.as<int32_t>(), o_raw.as<int32_t>(),
+                                                       slot_raw.as<int32_t>());
+        GS_LAUNCH_CHECK();
+    }
+    d_tri_own.release();
+    GS_TRY(s_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(o_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(slot_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(sort_rows3(s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>(), n, id_bits, slot_bits,
+                      s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(), st));
+    // dedupe into the raw buffers (reused)
+    GS_TRY(cnt.alloc(sizeof(int64_t), st));
+    {
+        DedupeOp op{s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(),
+                    s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>()};
+        GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err.as<int>()));
+        GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GS_CUDA(cudaStreamSynchronize(st));
+    }
+    const int64_t nu = h[0];
+    S->n_unique = nu;
+    // side 0 arrays: key = s, val = o (exact size)
+    DevBuf key0, val0, slot0;
+    GS_TRY(key0.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(val0.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(slot0.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_CUDA(cudaMemcpyAsync(key0.p, s_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(val0.p, o_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(slot0.p, slot_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
+    s_raw.release(); o_raw.release(); slot_raw.release();
+    // 4. side 1: sort the unique triples by (slot, o, s)
+    DevBuf key1, val1, slot1;
+    GS_TRY(key1.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(sort_rows3(val0.as<int32_t>(), key0.as<int32_t>(), slot0.as<int32_t>(), nu, id_bits, slot_bits,
+                      key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st));
+    s_sorted.release(); o_sorted.release(); slot_sorted.release();
+    // 5. rows, predicate bounds, dense row pointers
+    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err.as<int>(), st));
+    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err.as<int>(), st));
+    // device copy of the per-predicate tables
+    {
+        const size_t P = (size_t)S->n_pred;
+        GS_TRY(S->pred_side_dev.alloc(sizeof(PredSide) * 2 * P, st));
+        GS_CUDA(cudaMemcpyAsync(S->pred_side_dev.p, S->side[0].data(), sizeof(PredSide) * P, cudaMemcpyHostToDevice, st));
+        GS_CUDA(cudaMemcpyAsync(S->pred_side_dev.as<PredSide>() + P, S->side[1].data(), sizeof(PredSide) * P,
+                                cudaMemcpyHostToDevice, st));
+    }
+    t_all.stop();
+    GS_CUDA(cudaMemcpyAsync(h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (*reinterpret_cast<int *>(h)) return set_error(GSMAT_ERR_DEVICE_CHECK, "store build: a bounded wait expired");
+    return GSMAT_OK;
+}
+
+}  // namespace
+
+int store_build(const int32_t *triples, int64_t n, int on_device, cudaStream_t st, gsmat_store **out) {
+    if (!out) return set_error(GSMAT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > (int64_t)INT32_MAX) return set_error(GSMAT_ERR_INVALID_ARG, "n = %lld out of range", (long long)n);
+    if (n > 0 && !triples) return set_error(GSMAT_ERR_INVALID_ARG, "triples is NULL");
+    gsmat_store *S = new gsmat_store();
+    cudaGetDevice(&S->device);
+    int rc = build_impl(triples, n, on_device, st, S);
+    if (rc == GSMAT_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = set_error(GSMAT_ERR_CUDA, "store build: %s", cudaGetErrorString(e));
+    }
+    if (rc != GSMAT_OK) {
+        cudaStreamSynchronize(st);
+        delete S;
+        return rc;
+    }
+    // From here on the buffers are freed on the legacy stream (the load
+    // stream may be gone by then).
+    for (int s = 0; s < 2; ++s) {
+        S->key[s].st = S->val[s].st = S->rowid[s].st = S->rowoff[s].st = S->dense[s].st = nullptr;
+        S->view.side[s].key = S->key[s].as<int32_t>();
+        S->view.side[s].val = S->val[s].as<int32_t>();
+        S->view.side[s].rowid = S->rowid[s].as<int32_t>();
+        S->view.side[s].rowoff = S->rowoff[s].as<int32_t>();
+        S->view.side[s].dense = S->dense[s].as<int32_t>();
+        S->view.side[s].max_entity = S->max_entity;
+    }
+    S->pred_side_dev.st = nullptr;
+    S->hash_dev.st = nullptr;
+    profile_flush();
+    *out = S;
+    return GSMAT_OK;
+}
+
+}  // namespace gs
+
+int32_t gsmat_store::slot_of(int32_t pred_id) const {
+    if (pred_id < 0 || hash_keys.empty()) return -1;
+    uint32_t h = gs::pred_hash(pred_id) & hash_mask;
+    while (true) {
+        const int32_t k = hash_keys[h];
+        if (k == pred_id) return hash_vals[h];
+        if (k < 0) return -1;
+        h = (h + 1) & hash_mask;
+    }
+}

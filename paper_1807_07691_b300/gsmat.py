@@ -1,0 +1,386 @@
+"""ctypes binding of libgsmat (include/gsmat.h): argument marshalling only.
+
+Every step of loading and querying runs in the library's CUDA kernels; this
+module converts Python/numpy/torch arguments to the C ABI and back.  If the
+shared library is missing the import fails loudly -- there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgsmat.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "gsmat.h")
+
+OK = 0
+ERR_INVALID_ARG = 1
+ERR_UNSUPPORTED = 2
+ERR_OOM = 3
+ERR_CAPACITY = 4
+ERR_CUDA = 5
+ERR_DEVICE_CHECK = 6
+
+SORTED = 0
+PLAN_ORDER = 1
+COUNT_ONLY = 2
+
+STEP_CROSS, STEP_EXPAND_S, STEP_EXPAND_O, STEP_FILTER = 0, 1, 2, 3
+MAX_PATTERNS = 64
+
+
+class GsmatError(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        self.code = code
+        self.detail = detail
+        super().__init__(f"gsmat error {code} ({_strerror(code)}): {detail}")
+
+
+class Pattern(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("p", ctypes.c_int32), ("o", ctypes.c_int32),
+                ("s_var", ctypes.c_uint8), ("p_var", ctypes.c_uint8), ("o_var", ctypes.c_uint8),
+                ("_pad", ctypes.c_uint8)]
+
+
+class StoreInfo(ctypes.Structure):
+    _fields_ = [("n_input", ctypes.c_int64), ("n_unique", ctypes.c_int64), ("n_predicates", ctypes.c_int32),
+                ("max_entity", ctypes.c_int32), ("max_predicate", ctypes.c_int32),
+                ("n_dense_rows_s", ctypes.c_int32), ("n_dense_rows_o", ctypes.c_int32),
+                ("_reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+class PredStats(ctypes.Structure):
+    _fields_ = [("pred_id", ctypes.c_int32), ("nnz", ctypes.c_int32), ("nr_s", ctypes.c_int32),
+                ("nr_o", ctypes.c_int32)]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int32), ("order", ctypes.c_int32 * MAX_PATTERNS),
+                ("kind", ctypes.c_int32 * MAX_PATTERNS), ("est_rows", ctypes.c_double * MAX_PATTERNS),
+                ("rows", ctypes.c_int64 * MAX_PATTERNS), ("est_cost", ctypes.c_double),
+                ("result_rows", ctypes.c_int64)]
+
+
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("algo_bytes", ctypes.c_double), ("items", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgsmat.so is not built ({LIB_PATH}); run python -m paper_1807_07691_b300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    c_int = ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "gsmat_strerror": ([c_int], ctypes.c_char_p),
+        "gsmat_last_error": ([], ctypes.c_char_p),
+        "gsmat_version": ([], c_int),
+        "gsmat_set_allocator": ([vp, vp, vp], c_int),
+        "gsmat_load": ([vp, i64, c_int, vp, P(vp)], c_int),
+        "gsmat_store_info": ([vp, P(StoreInfo)], c_int),
+        "gsmat_store_pred_stats": ([vp, vp, i32, P(i32)], c_int),
+        "gsmat_store_export": ([vp, i32, c_int, vp, vp, vp, vp], c_int),
+        "gsmat_store_pred_index": ([vp, i32], i32),
+        "gsmat_store_free": ([vp], None),
+        "gsmat_query": ([vp, vp, c_int, c_int, u32, vp, P(vp)], c_int),
+        "gsmat_table_info": ([vp, P(i64), P(i32), vp], c_int),
+        "gsmat_table_column": ([vp, i32, P(vp)], c_int),
+        "gsmat_table_copy": ([vp, vp, c_int, vp], c_int),
+        "gsmat_table_stats": ([vp, P(QueryStats)], c_int),
+        "gsmat_table_free": ([vp], None),
+        "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
+        "gsmat_radix_sort_u64": ([vp, vp, i64, c_int, c_int, vp], c_int),
+        "gsmat_exclusive_scan_i32": ([vp, vp, i64, vp], c_int),
+        "gsmat_profile_enable": ([c_int], c_int),
+        "gsmat_profile_read": ([vp, i32, P(i32), c_int], c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/gsmat.h."""
+    with open(HEADER_PATH) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"GSMAT_API\s+[\w\s\*]+?\b(gsmat_\w+)\s*\(", text)))
+
+
+def _strerror(code: int) -> str:
+    return _lib.gsmat_strerror(code).decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise GsmatError(rc, _lib.gsmat_last_error().decode())
+
+
+def _stream_ptr(stream):
+    """A cudaStream_t from None (torch's current stream if CUDA is up, else
+    the legacy default stream), an int, or a torch.cuda.Stream."""
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _patterns(bgp):
+    """(ctypes array of Pattern, n, n_vars) from a BGP-like object, an (n, 6)
+    array (s, p, o, s_var, p_var, o_var) or a list of (s, p, o, s_var,
+    o_var) tuples."""
+    n_vars = getattr(bgp, "n_vars", None)
+    if hasattr(bgp, "as_array"):
+        arr = bgp.as_array()
+    else:
+        arr = np.asarray(bgp, dtype=np.int64)
+        if arr.ndim == 2 and arr.shape[1] == 5:
+            arr = np.stack([arr[:, 0], arr[:, 1], arr[:, 2], arr[:, 3], np.zeros(len(arr), np.int64), arr[:, 4]], 1)
+    arr = arr.reshape(-1, 6)
+    pats = (Pattern * max(1, arr.shape[0]))()
+    for i, (s, p, o, sv, pv, ov) in enumerate(arr.tolist()):
+        pats[i] = Pattern(int(s), int(p), int(o), int(sv), int(pv), int(ov), 0)
+    return pats, arr.shape[0], n_vars
+
+
+# ----------------------------------------------------------------------------
+
+
+class Table:
+    """A device-resident binding table (columns are int32 device arrays)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.gsmat_table_free(h)
+        self._h = None
+
+    @property
+    def shape(self):
+        rows, cols = ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.gsmat_table_info(self._h, ctypes.byref(rows), ctypes.byref(cols), None))
+        return int(rows.value), int(cols.value)
+
+    @property
+    def rows(self) -> int:
+        return self.shape[0]
+
+    @property
+    def col_vars(self) -> list:
+        rows, cols = self.shape
+        buf = (ctypes.c_int32 * max(1, cols))()
+        _check(_lib.gsmat_table_info(self._h, None, None, buf))
+        return [int(buf[i]) for i in range(cols)]
+
+    def column_ptr(self, c: int) -> int:
+        p = ctypes.c_void_p()
+        _check(_lib.gsmat_table_column(self._h, c, ctypes.byref(p)))
+        return p.value or 0
+
+    def to_numpy(self, stream=None) -> np.ndarray:
+        rows, cols = self.shape
+        out = np.empty((rows, cols), dtype=np.int32)
+        if rows and cols:
+            _check(_lib.gsmat_table_copy(self._h, out.ctypes.data, 0, _stream_ptr(stream)))
+        return out
+
+    def to_torch(self, stream=None):
+        """Row-major (rows, cols) int32 CUDA tensor (a copy)."""
+        import torch
+
+        rows, cols = self.shape
+        out = torch.empty((rows, cols), dtype=torch.int32, device="cuda")
+        if rows and cols:
+            _check(_lib.gsmat_table_copy(self._h, ctypes.c_void_p(out.data_ptr()), 1, _stream_ptr(stream)))
+        return out
+
+    def stats(self) -> dict:
+        s = QueryStats()
+        _check(_lib.gsmat_table_stats(self._h, ctypes.byref(s)))
+        n = s.n_steps
+        return {
+            "order": [s.order[i] for i in range(n)],
+            "kind": [s.kind[i] for i in range(n)],
+            "est_rows": [s.est_rows[i] for i in range(n)],
+            "rows": [int(s.rows[i]) for i in range(n)],
+            "est_cost": s.est_cost,
+            "result_rows": int(s.result_rows),
+        }
+
+
+class Store:
+    """The device-resident SM store built by gsmat_load."""
+
+    def __init__(self, triples, stream=None):
+        h = ctypes.c_void_p()
+        on_device = 0
+        keep = None
+        if hasattr(triples, "data_ptr"):  # torch tensor
+            import torch
+
+            t = triples
+            if t.dtype != torch.int32 or t.dim() != 2 or t.shape[1] != 3 or not t.is_contiguous():
+                raise ValueError("triples must be a contiguous (n, 3) int32 tensor")
+            ptr, n = t.data_ptr(), t.shape[0]
+            on_device = 1 if t.is_cuda else 0
+            keep = t
+        else:
+            arr = np.ascontiguousarray(np.asarray(triples, dtype=np.int32).reshape(-1, 3))
+            ptr, n = arr.ctypes.data, arr.shape[0]
+            keep = arr
+        _check(_lib.gsmat_load(ctypes.c_void_p(ptr), n, on_device, _stream_ptr(stream), ctypes.byref(h)))
+        del keep
+        self._h = h
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.gsmat_store_free(h)
+        self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = StoreInfo()
+        _check(_lib.gsmat_store_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in StoreInfo._fields_ if not f.startswith("_")}
+
+    def pred_stats(self) -> list:
+        n = self.info()["n_predicates"]
+        buf = (PredStats * max(1, n))()
+        got = ctypes.c_int32()
+        _check(_lib.gsmat_store_pred_stats(self._h, buf, n, ctypes.byref(got)))
+        return [{"pred_id": b.pred_id, "nnz": b.nnz, "nr_s": b.nr_s, "nr_o": b.nr_o} for b in buf[: got.value]]
+
+    def pred_index(self, pred_id: int) -> int:
+        return int(_lib.gsmat_store_pred_index(self._h, int(pred_id)))
+
+    def export(self, pred_id: int, side: int, stream=None):
+        """(row_ids, row_ptr, entries) of one predicate on one side (host)."""
+        st = {s["pred_id"]: s for s in self.pred_stats()}[int(pred_id)]
+        nr = st["nr_s"] if side == 0 else st["nr_o"]
+        rid = np.empty(max(1, nr), np.int32)
+        ptr = np.empty(nr + 1, np.int64)
+        ent = np.empty(max(1, st["nnz"]), np.int32)
+        _check(_lib.gsmat_store_export(self._h, int(pred_id), int(side), rid.ctypes.data, ptr.ctypes.data,
+                                       ent.ctypes.data, _stream_ptr(stream)))
+        return rid[:nr], ptr, ent[: st["nnz"]]
+
+    def query(self, bgp, n_vars=None, flags: int = SORTED, stream=None) -> Table:
+        pats, n, nv = _patterns(bgp)
+        if n_vars is None:
+            n_vars = nv
+        if n_vars is None:
+            raise ValueError("n_vars is required")
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_query(self._h, pats, n, int(n_vars), flags, _stream_ptr(stream), ctypes.byref(h)))
+        return Table(h)
+
+
+# ----------------------------------------------------------------------------
+
+
+def plan(bgp, keys, stats, n_vars=None):
+    """Host planner (Alg. 1): (order, kinds, est) for given per-pattern keys
+    and predicate statistics (list of dicts with nnz, nr_s, nr_o)."""
+    pats, n, nv = _patterns(bgp)
+    n_vars = nv if n_vars is None else n_vars
+    k = np.ascontiguousarray(np.asarray(keys, dtype=np.int64))
+    st = (PredStats * n)()
+    for i, s in enumerate(stats):
+        st[i] = PredStats(int(s.get("pred_id", 0)), int(s["nnz"]), int(s["nr_s"]), int(s["nr_o"]))
+    order = np.zeros(n, np.int32)
+    kinds = np.zeros(n, np.int32)
+    est = np.zeros(n, np.float64)
+    _check(_lib.gsmat_plan(pats, n, int(n_vars), k.ctypes.data, st, order.ctypes.data, kinds.ctypes.data,
+                           est.ctypes.data))
+    return order.tolist(), kinds.tolist(), est.tolist()
+
+
+def radix_sort_u64(keys, vals=None, begin_bit: int = 0, end_bit: int = 64, stream=None):
+    """Sort a CUDA uint64/int64 tensor in place (optional int32/uint32 payload)."""
+    _check(_lib.gsmat_radix_sort_u64(ctypes.c_void_p(keys.data_ptr()),
+                                     ctypes.c_void_p(vals.data_ptr()) if vals is not None else None,
+                                     keys.numel(), begin_bit, end_bit, _stream_ptr(stream)))
+
+
+def exclusive_scan_i32(src, dst, stream=None):
+    """dst[0..n] (int64 CUDA tensor) = exclusive prefix sums of src (int32)."""
+    _check(_lib.gsmat_exclusive_scan_i32(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                         src.numel(), _stream_ptr(stream)))
+
+
+def profile_enable(on: bool = True):
+    _check(_lib.gsmat_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = False) -> dict:
+    n = ctypes.c_int32()
+    _check(_lib.gsmat_profile_read(None, 0, ctypes.byref(n), 0))
+    buf = (KernelProfile * max(1, n.value))()
+    _check(_lib.gsmat_profile_read(buf, n.value, ctypes.byref(n), 1 if reset else 0))
+    return {b.name.decode(): {"launches": b.launches, "total_ms": b.total_ms, "algo_bytes": b.algo_bytes,
+                              "items": b.items} for b in buf[: n.value]}
+
+
+# torch caching allocator as the device allocation hook -----------------------
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_hooks = []
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching
+    allocator (enable=False restores cudaMallocAsync)."""
+    if not enable:
+        _check(_lib.gsmat_set_allocator(None, None, None))
+        _hooks.clear()
+        return
+    import torch
+
+    def _alloc(nbytes, ctx, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_T(_alloc), _FREE_T(_free)
+    _hooks[:] = [a, f]
+    _check(_lib.gsmat_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None))

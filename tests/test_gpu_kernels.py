@@ -1,0 +1,70 @@
+"""Radix sort and scan primitives through the C ABI against numpy (GPU)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    torch.cuda.init()
+    import paper_1807_07691_b300 as g
+
+    return g, torch
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 100, 3071, 3072, 3073, 100_000, 1_234_567])
+@pytest.mark.parametrize("bits", [(0, 64), (0, 20), (8, 40)])
+def test_radix_sort_pairs_stable(env, n, bits):
+    g, torch = env
+    rng = np.random.default_rng(n + bits[1])
+    keys = rng.integers(0, 2**63, size=n, dtype=np.int64).view(np.uint64)
+    if n > 10:
+        keys[: n // 3] = keys[0]  # many equal keys: stability matters
+    vals = np.arange(n, dtype=np.uint32)
+    dk = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    dv = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    g.radix_sort_u64(dk, dv, bits[0], bits[1])
+    torch.cuda.synchronize()
+    b0, b1 = bits
+    mask = np.uint64((1 << (b1 - b0)) - 1) if b1 - b0 < 64 else np.uint64(2**64 - 1)
+    digit = (keys >> np.uint64(b0)) & mask
+    order = np.argsort(digit, kind="stable")
+    assert np.array_equal(dk.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(dv.cpu().numpy().view(np.uint32), vals[order])
+
+
+def test_radix_sort_keys_only(env):
+    g, torch = env
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 2**40, size=500_001, dtype=np.int64)
+    dk = torch.from_numpy(keys.copy()).cuda()
+    g.radix_sort_u64(dk, None, 0, 40)
+    assert np.array_equal(dk.cpu().numpy(), np.sort(keys))
+
+
+@pytest.mark.parametrize("n", [0, 1, 5, 2047, 2048, 2049, 1_000_003])
+def test_exclusive_scan(env, n):
+    g, torch = env
+    rng = np.random.default_rng(n)
+    x = rng.integers(0, 1000, size=n).astype(np.int32)
+    dx = torch.from_numpy(x).cuda()
+    out = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    g.exclusive_scan_i32(dx, out)
+    want = np.concatenate([[0], np.cumsum(x, dtype=np.int64)])
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+def test_scan_total_beyond_int32(env):
+    g, torch = env
+    n = 3_000_000
+    x = np.full(n, 2**30, dtype=np.int32)
+    x[::7] = 5
+    out = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    g.exclusive_scan_i32(torch.from_numpy(x).cuda(), out)
+    want = np.concatenate([[0], np.cumsum(x, dtype=np.int64)])
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert want[-1] > 2**31

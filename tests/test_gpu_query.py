@@ -1,0 +1,155 @@
+"""BGP evaluation on the GPU against the oracle, bit-exact (GPU)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import golden, is_sorted_unique, random_bgp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+
+    torch.cuda.init()
+    import paper_1807_07691_b300 as g
+
+    return g
+
+
+@pytest.fixture(scope="module")
+def tiny(gs):
+    t = synth.make_graph("tiny")
+    return t, oracle.OracleIndex(t), gs.Store(t), synth.make_queries("tiny", t)
+
+
+def test_dg_example(gs):
+    g = golden("dg_example.json")
+    S = gs.Store(np.array(g["cube_spo"], dtype=np.int32))
+    T = S.query(g["query"], 4)
+    assert T.to_numpy().tolist() == g["answer_xyzw"]
+    st = T.stats()
+    assert st["order"] == g["plan_order"]
+    assert st["rows"] == g["plan_step_rows"]
+    # paper's column order (X, W, Z, Y) = plan order
+    P = S.query(g["query"], 4, flags=gs.PLAN_ORDER)
+    assert P.col_vars == [0, 3, 2, 1]
+    assert P.to_numpy().tolist() == [g["answer_XWZY"]]
+
+
+def test_tiny_workload_bit_exact(gs, tiny):
+    t, ix, S, qs = tiny
+    for q in qs:
+        want = ix.query(q)
+        got = S.query(q).to_numpy()
+        assert got.shape == want.shape, q.name
+        assert np.array_equal(got, want), q.name
+
+
+def test_tiny_workload_any_pattern_order(gs, tiny):
+    t, ix, S, qs = tiny
+    rng = np.random.default_rng(11)
+    for q in qs:
+        want = ix.query(q)
+        for _ in range(2):
+            got = S.query(q.permuted(rng.permutation(len(q.patterns)))).to_numpy()
+            assert np.array_equal(got, want), q.name
+
+
+def test_tiny_plan_order_and_count_only(gs, tiny):
+    t, ix, S, qs = tiny
+    for q in qs:
+        want = ix.query(q)
+        P = S.query(q, flags=gs.PLAN_ORDER)
+        cv = P.col_vars
+        got = P.to_numpy()
+        assert is_sorted_unique(got)
+        ref = want[:, cv]
+        ref = ref[np.lexsort(ref.T[::-1])] if len(ref) else ref
+        assert np.array_equal(got, ref), q.name
+        C = S.query(q, flags=gs.COUNT_ONLY)
+        assert C.shape == (want.shape[0], 0)
+
+
+def test_tiny_rerun_is_identical(gs, tiny):
+    t, ix, S, qs = tiny
+    for q in qs[:4]:
+        a = S.query(q).to_numpy()
+        b = S.query(q).to_numpy()
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_bgps_small_graphs(gs, seed):
+    rng = np.random.default_rng(1000 + seed)
+    t = synth.small_random_graph(int(rng.integers(3, 12)), 3, int(rng.integers(1, 80)), seed=seed,
+                                 pred_ids=np.array([3, 77, 123456]))
+    pats, V = random_bgp(rng, t, n_vars_max=5, n_pats_max=6)
+    want = oracle.oracle_query(t, pats, V)
+    S = gs.Store(t)
+    got = S.query(pats, V).to_numpy()
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)
+
+
+def test_edge_cases(gs):
+    t = np.array([(1, 7, 2), (2, 7, 3), (3, 7, 3), (2, 8, 1)], dtype=np.int32)
+    ix = oracle.OracleIndex(t)
+    S = gs.Store(t)
+    cases = [
+        ([(0, 7, 0, 1, 1)], 1),                        # ?x p ?x
+        ([(1, 7, 2, 0, 0), (0, 7, 1, 1, 1)], 2),       # constant pattern present
+        ([(1, 7, 3, 0, 0), (0, 7, 1, 1, 1)], 2),       # constant pattern absent
+        ([(0, 99, 1, 1, 1)], 2),                       # absent predicate
+        ([(0, 7, 1, 1, 1), (2, 8, 3, 1, 1)], 4),       # Cartesian product
+        ([(1, 7, 2, 0, 0)], 0),                        # no variables
+        ([(1, 7, 9, 0, 0)], 0),
+        ([(0, 7, 1, 1, 1), (0, 7, 1, 1, 1)], 2),       # duplicate pattern
+        ([(0, 7, 1, 1, 1), (1, 7, 1, 1, 1)], 2),       # repeated var after binding
+        ([(2, 7, 0, 0, 1), (0, 7, 1, 1, 1)], 2),       # constant subject
+        ([(0, 7, 3, 1, 0)], 1),                        # constant object
+        ([(5000, 7, 0, 0, 1)], 1),                     # constant absent from the store
+    ]
+    for pats, V in cases:
+        want = ix.query(pats, V)
+        got = S.query(pats, V).to_numpy()
+        assert got.shape == want.shape, pats
+        assert np.array_equal(got, want), pats
+    with pytest.raises(gs.GsmatError) as e:
+        S.query(np.array([[0, 0, 1, 1, 1, 1]]), 2)
+    assert e.value.code == 2
+    with pytest.raises(gs.GsmatError) as e:
+        S.query([(0, 7, 1, 1, 1)], 3)
+    assert e.value.code == 1
+
+
+def test_empty_store_query(gs):
+    S = gs.Store(np.zeros((0, 3), np.int32))
+    T = S.query([(0, 7, 1, 1, 1)], 2)
+    assert T.shape == (0, 2)
+
+
+def test_query_on_torch_stream(gs, tiny):
+    import torch
+
+    t, ix, S, qs = tiny
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        got = S.query(qs[0], stream=s).to_torch(stream=s)
+    s.synchronize()
+    assert np.array_equal(got.cpu().numpy(), ix.query(qs[0]))
+
+
+def test_torch_allocator_hook(gs, tiny):
+    t, ix, S, qs = tiny
+    gs.use_torch_allocator(True)
+    try:
+        S2 = gs.Store(t)
+        for q in qs[:3]:
+            assert np.array_equal(S2.query(q).to_numpy(), ix.query(q))
+        del S2
+    finally:
+        gs.use_torch_allocator(False)
