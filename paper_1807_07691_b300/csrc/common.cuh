@@ -326,6 +326,9 @@ int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
 // set if a bounded wait expired (may be null).
 int exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st, int *err_word);
 
+// In-place exclusive scan of uint32 values whose total fits in 32 bits.
+int exclusive_scan_u32_inplace(uint32_t *data, int64_t n, cudaStream_t st);
+
 // Stable selection: out[j] = in[i] for the i with flags[i] != 0, in order;
 // *d_count (device int64) receives the number selected.
 int select_flagged_i32(const int32_t *in, const uint8_t *flags, int32_t *out, int64_t n, int64_t *d_count,

@@ -68,12 +68,38 @@ __global__ void __launch_bounds__(kCsBlock) count_scan_kernel(SideView sv, PredS
 
 // ---------------------------------------------------------------------------
 // expand
+//
+// Load balance: the merge of the row-end sequence off[1..n] with the output
+// slots 0..total-1 is cut into pieces of kExItems items (rows + slots), so a
+// CTA never sees more than kExItems parent rows, however many input rows
+// have no match.  A partition kernel finds every cut by a merge-path search;
+// the expand kernel stages its piece of the offsets in shared memory and
+// finds each slot's parent by a shared-memory binary search.
 
 constexpr int kExBlock = 256;
-constexpr int kExVec = 4;
-constexpr int kExIter = 4;
-constexpr int kExSlots = kExBlock * kExVec * kExIter;  // output rows per CTA
-constexpr int kExSmemRows = kExSlots + 2;
+constexpr int kExItems = 2048;  // rows + slots per CTA
+
+// Number of rows whose end off[r + 1] precedes output slot diag - a in the
+// merge, for the first `diag` merged items (rows win ties).
+__device__ __forceinline__ int64_t merge_path(const int64_t *__restrict__ off, int64_t n_rows, int64_t total,
+                                              int64_t diag) {
+    int64_t lo = diag - total > 0 ? diag - total : 0;
+    int64_t hi = diag < n_rows ? diag : n_rows;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid + 1) <= diag - 1 - mid) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void expand_partition_kernel(const int64_t *__restrict__ off, int64_t n_rows, int64_t total, int64_t n_parts,
+                                        int64_t *__restrict__ cuts) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p > n_parts) return;
+    int64_t diag = p * kExItems;
+    if (diag > n_rows + total) diag = n_rows + total;
+    cuts[p] = merge_path(off, n_rows, total, diag);
+}
 
 struct ExpandArgs {
     const int32_t *val;  // the side's entry array
@@ -83,91 +109,37 @@ struct ExpandArgs {
     const int64_t *off;
     const int32_t *first;
     int64_t total;
+    const int64_t *cuts;
     OutCols out;
 };
 
-// Largest r in [lo, hi] with off[r] <= j (off[lo] <= j is required).
-__device__ __forceinline__ int64_t parent_global(const int64_t *__restrict__ off, int64_t lo, int64_t hi, int64_t j) {
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (__ldg(off + mid) <= j) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(kExBlock) expand_kernel(ExpandArgs a) {
-    __shared__ int64_t soff[kExSmemRows];
-    __shared__ int64_t range_sm[2];
-    const int64_t j0 = (int64_t)blockIdx.x * kExSlots;
-    const int64_t j1 = (j0 + kExSlots < a.total) ? j0 + kExSlots : a.total;
-    if (threadIdx.x == 0) {
-        const int64_t lo = parent_global(a.off, 0, a.n_in - 1, j0);
-        range_sm[0] = lo;
-        range_sm[1] = parent_global(a.off, lo, a.n_in - 1, j1 - 1);
-    }
-    __syncthreads();
-    const int64_t r_lo = range_sm[0];
-    const int64_t nr = range_sm[1] - r_lo + 1;  // parent rows of this slab
-    const bool staged = nr + 1 <= kExSmemRows;
-    if (staged) {
-        for (int i = threadIdx.x; i <= nr; i += kExBlock) soff[i] = __ldg(a.off + r_lo + i);
-    }
+    __shared__ int64_t soff[kExItems + 2];
+    __shared__ int32_t sfirst[kExItems + 1];
+    const int64_t d0 = (int64_t)blockIdx.x * kExItems;
+    const int64_t d1 = d0 + kExItems < a.n_in + a.total ? d0 + kExItems : a.n_in + a.total;
+    const int64_t r0 = __ldg(a.cuts + blockIdx.x);
+    const int64_t r1 = __ldg(a.cuts + blockIdx.x + 1);
+    const int64_t j0 = d0 - r0, j1 = d1 - r1;  // output slots [j0, j1)
+    if (j1 <= j0) return;
+    // parents of the slots lie in [r0, r_last]
+    const int64_t r_last = r1 < a.n_in ? r1 : a.n_in - 1;
+    const int nr = (int)(r_last - r0 + 1);
+    for (int i = threadIdx.x; i <= nr; i += kExBlock) soff[i] = __ldg(a.off + r0 + i);
+    for (int i = threadIdx.x; i < nr; i += kExBlock) sfirst[i] = __ldg(a.first + r0 + i);
     __syncthreads();
     const int k = a.k;
-#pragma unroll 1
-    for (int it = 0; it < kExIter; ++it) {
-        const int64_t jb = j0 + (int64_t)it * (kExBlock * kExVec) + (int64_t)threadIdx.x * kExVec;
-        if (jb >= j1) break;
-        // parent of the first slot
-        int64_t r;
-        if (staged) {
-            int lo = 0, hi = (int)nr - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (soff[mid] <= jb) lo = mid; else hi = mid - 1;
-            }
-            r = r_lo + lo;
-        } else {
-            r = parent_global(a.off, r_lo, r_lo + nr - 1, jb);
+    const int32_t *__restrict__ val = a.val;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += kExBlock) {
+        // largest i in [0, nr) with soff[i] <= j
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (soff[mid] <= j) lo = mid; else hi = mid - 1;
         }
-        int64_t r_beg = staged ? soff[r - r_lo] : __ldg(a.off + r);
-        int64_t r_end = staged ? soff[r - r_lo + 1] : __ldg(a.off + r + 1);
-        int64_t rr[kExVec];
-        int32_t nv[kExVec];
-#pragma unroll
-        for (int q = 0; q < kExVec; ++q) {
-            const int64_t j = jb + q;
-            rr[q] = r;
-            nv[q] = 0;
-            if (j < j1) {
-                while (j >= r_end) {
-                    ++r;
-                    r_beg = r_end;
-                    r_end = staged ? soff[r - r_lo + 1] : __ldg(a.off + r + 1);
-                }
-                rr[q] = r;
-                nv[q] = __ldg(a.val + __ldg(a.first + r) + (j - r_beg));
-            }
-        }
-        if (jb + kExVec <= j1) {
-            for (int c = 0; c < k; ++c) {
-                const int32_t *src = a.in.c[c];
-                int4 v;
-                v.x = __ldg(src + rr[0]);
-                v.y = __ldg(src + rr[1]);
-                v.z = __ldg(src + rr[2]);
-                v.w = __ldg(src + rr[3]);
-                *reinterpret_cast<int4 *>(a.out.c[c] + jb) = v;
-            }
-            *reinterpret_cast<int4 *>(a.out.c[k] + jb) = make_int4(nv[0], nv[1], nv[2], nv[3]);
-        } else {
-            for (int q = 0; q < kExVec; ++q) {
-                const int64_t j = jb + q;
-                if (j >= j1) break;
-                for (int c = 0; c < k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + rr[q]);
-                a.out.c[k][j] = nv[q];
-            }
-        }
+        const int64_t r = r0 + lo;
+        for (int c = 0; c < k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + r);
+        a.out.c[k][j] = __ldg(val + sfirst[lo] + (j - soff[lo]));
     }
 }
 
@@ -254,6 +226,19 @@ __global__ void iota_u32_kernel(uint32_t *v, int64_t n) {
     }
 }
 
+__global__ void finalize_rows_kernel(const uint64_t *__restrict__ keys, int k0, int bits, const uint32_t *__restrict__ perm,
+                                     Cols rest, int n_rest, int64_t n, OutCols out) {
+    const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = __ldg(keys + i);
+        for (int c = 0; c < k0; ++c) out.c[c][i] = (int32_t)((key >> ((k0 - 1 - c) * bits)) & mask);
+        if (n_rest > 0) {
+            const uint32_t r = __ldg(perm + i);
+            for (int c = 0; c < n_rest; ++c) out.c[k0 + c][i] = __ldg(rest.c[c] + r);
+        }
+    }
+}
+
 __global__ void gather_rows_kernel(Cols in, int k, const uint32_t *__restrict__ perm, int64_t n, OutCols out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t r = __ldg(perm + i);
@@ -299,7 +284,11 @@ int launch_count_scan(const StoreView &sv, int side, const PredSide &ps, const i
 
 int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t n_in, const int64_t *off,
                   const int32_t *first, int64_t total, OutCols out, cudaStream_t st) {
-    if (total <= 0) return GSMAT_OK;
+    if (total <= 0 || n_in <= 0) return GSMAT_OK;
+    const int64_t n_parts = (n_in + total + kExItems - 1) / kExItems;
+    if (n_parts > INT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "expand into %lld rows", (long long)total);
+    DevBuf cuts;
+    GS_TRY(cuts.alloc(sizeof(int64_t) * (size_t)(n_parts + 1), st));
     ExpandArgs a;
     a.val = sv.side[side].val;
     a.in = in;
@@ -308,14 +297,16 @@ int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t 
     a.off = off;
     a.first = first;
     a.total = total;
+    a.cuts = cuts.as<int64_t>();
     a.out = out;
-    const int64_t grid = (total + kExSlots - 1) / kExSlots;
-    // algorithmic bytes (per the method): read k bound columns and the
-    // offsets once per parent row, one neighbour id per output row, write
-    // k + 1 columns per output row.
+    // algorithmic bytes (per the method): read k bound columns, the offset
+    // and the first entry once per parent row, one neighbour id per output
+    // row, write k + 1 columns per output row.
     KernelTimer t("expand", st, (double)n_in * (4.0 * k + 8.0 + 4.0) + (double)total * (4.0 + 4.0 * (k + 1)),
                   (double)total);
-    expand_kernel<<<(unsigned)grid, kExBlock, 0, st>>>(a);
+    expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts,
+                                                                                  cuts.as<int64_t>());
+    expand_kernel<<<(unsigned)n_parts, kExBlock, 0, st>>>(a);
     GS_LAUNCH_CHECK();
     t.stop();
     return GSMAT_OK;
@@ -381,6 +372,17 @@ int launch_iota(uint32_t *v, int64_t n, cudaStream_t st) {
     if (n <= 0) return GSMAT_OK;
     iota_u32_kernel<<<grid_1d(n, 256), 256, 0, st>>>(v, n);
     GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+int launch_finalize_rows(const uint64_t *keys, int k0, int bits, const uint32_t *perm, const Cols &rest, int n_rest,
+                         int64_t n, OutCols out, cudaStream_t st) {
+    if (n <= 0) return GSMAT_OK;
+    KernelTimer t("finalize_rows", st, (double)n * (8.0 + 4.0 * (k0 + n_rest) + (n_rest ? 4.0 + 4.0 * n_rest : 0.0)),
+                  (double)n);
+    finalize_rows_kernel<<<grid_1d(n, 256), 256, 0, st>>>(keys, k0, bits, perm, rest, n_rest, n, out);
+    GS_LAUNCH_CHECK();
+    t.stop();
     return GSMAT_OK;
 }
 

@@ -58,6 +58,10 @@ int launch_const_lookup(const StoreView &sv, const PredSide *d_sides, int n_pred
 int launch_pack_rows(const Cols &cols, int nc, int bits, const uint32_t *perm, int64_t n, uint64_t *keys,
                      cudaStream_t st);
 int launch_iota(uint32_t *v, int64_t n, cudaStream_t st);
+// out[c][i] for c < k0: field c (most significant first, `bits` wide) of
+// keys[i]; out[k0 + c][i] = rest[c][perm[i]] for c < n_rest.
+int launch_finalize_rows(const uint64_t *keys, int k0, int bits, const uint32_t *perm, const Cols &rest, int n_rest,
+                         int64_t n, OutCols out, cudaStream_t st);
 // out[c][i] = in[c][perm[i]] for c < k.
 int launch_gather_rows(const Cols &in, int k, const uint32_t *perm, int64_t n, OutCols out, cudaStream_t st);
 // dst[i * k + c] = in[c][i] (row-major interleave).

@@ -115,34 +115,37 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
     const int64_t n = t.rows;
     const int bits = std::max(1, bits_for((uint64_t)std::max(cx.S->max_entity, 0)));
     const int per_key = 64 / bits;
+    // The m sort variables in chunks of per_key, most significant first;
+    // least-significant-digit order sorts by the last chunk first.
+    const int n_chunks = (m + per_key - 1) / per_key;
     DevBuf keys, perm;
     GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, cx.st));
     GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)n, cx.st));
-    bool first = true;
-    for (int e = m; e > 0;) {
-        const int b = std::max(0, e - per_key);
+    for (int ci = n_chunks - 1; ci >= 0; --ci) {
+        const int b = ci * per_key;
+        const int e = std::min(m, b + per_key);
         Cols kc;
         for (int v = b; v < e; ++v) kc.c[v - b] = t.col[colof[v]];
         const int nc = e - b;
-        if (first) {
+        if (ci == n_chunks - 1) {
             GS_TRY(launch_iota(perm.as<uint32_t>(), n, cx.st));
             GS_TRY(launch_pack_rows(kc, nc, bits, nullptr, n, keys.as<uint64_t>(), cx.st));
-            first = false;
         } else {
             GS_TRY(launch_pack_rows(kc, nc, bits, perm.as<uint32_t>(), n, keys.as<uint64_t>(), cx.st));
         }
         GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, nc * bits, cx.st));
-        e = b;
     }
-    keys.release();
+    // variables 0..k0-1 are unpacked from the sorted keys, the others are
+    // gathered through the permutation
+    const int k0 = std::min(m, per_key);
     OutCols oc;
     GS_TRY(alloc_cols(out, V, n, cx.st, &oc));
-    Cols in;
+    Cols rest;
     for (int v = 0; v < V; ++v) {
-        in.c[v] = t.col[colof[v]];
+        if (v >= k0) rest.c[v - k0] = t.col[colof[v]];
         out.vars[v] = v;
     }
-    GS_TRY(launch_gather_rows(in, V, perm.as<uint32_t>(), n, oc, cx.st));
+    GS_TRY(launch_finalize_rows(keys.as<uint64_t>(), k0, bits, perm.as<uint32_t>(), rest, V - k0, n, oc, cx.st));
     return GSMAT_OK;
 }
 

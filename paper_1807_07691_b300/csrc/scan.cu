@@ -16,27 +16,29 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 // reading its kScanItems consecutive values hits distinct banks.
 __device__ __forceinline__ int padded(int i) { return i + (i >> 5); }
 
-__global__ void __launch_bounds__(kScanBlock) scan_i32_kernel(const int32_t *__restrict__ in, int64_t *__restrict__ out,
-                                                              int64_t n, LookbackScratch ls) {
+template <class InT, class OutT, bool WriteTotal>
+__global__ void __launch_bounds__(kScanBlock) scan_kernel(const InT *in, OutT *out, int64_t n, LookbackScratch ls) {
+    // in and out may be the same array: a tile reads its inputs before the
+    // look-back and writes its outputs after it
     __shared__ int tile_sm;
     __shared__ int64_t scan_sm[kScanBlock / 32 + 1];
     __shared__ int64_t prefix_sm;
-    __shared__ int32_t stage[kScanTile + kScanTile / 32];
+    __shared__ InT stage[kScanTile + kScanTile / 32];
     const int tile = acquire_tile_id(ls, &tile_sm);
     const int64_t t0 = (int64_t)tile * kScanTile;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int idx = j * kScanBlock + threadIdx.x;
         const int64_t i = t0 + idx;
-        stage[padded(idx)] = i < n ? __ldg(in + i) : 0;
+        stage[padded(idx)] = i < n ? in[i] : InT(0);
     }
     __syncthreads();
-    int32_t v[kScanItems];
+    InT v[kScanItems];
     int64_t s = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         v[j] = stage[padded(threadIdx.x * kScanItems + j)];
-        s += v[j];
+        s += (int64_t)v[j];
     }
     int64_t tot;
     const int64_t ex = block_exclusive_sum<kScanBlock>(s, scan_sm, &tot);
@@ -45,10 +47,10 @@ __global__ void __launch_bounds__(kScanBlock) scan_i32_kernel(const int32_t *__r
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = t0 + threadIdx.x * kScanItems + j;
-        if (i < n) out[i] = run;
-        run += v[j];
+        if (i < n) out[i] = (OutT)run;
+        run += (int64_t)v[j];
     }
-    if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) out[n] = pre + tot;
+    if (WriteTotal && tile == (int)gridDim.x - 1 && threadIdx.x == 0) out[n] = (OutT)(pre + tot);
 }
 
 struct SelectI32Op {
@@ -72,9 +74,20 @@ int exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t 
     LookbackBuf lb;
     GS_TRY(lb.make(ntiles, st, err_word));
     KernelTimer t("scan_i32", st, (double)n * 12.0, (double)n);
-    scan_i32_kernel<<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, out, n, lb.view);
+    scan_kernel<int32_t, int64_t, true><<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, out, n, lb.view);
     GS_LAUNCH_CHECK();
     t.stop();
+    return GSMAT_OK;
+}
+
+int exclusive_scan_u32_inplace(uint32_t *data, int64_t n, cudaStream_t st) {
+    if (n <= 0) return GSMAT_OK;
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    if (ntiles > INT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "scan over %lld items", (long long)n);
+    LookbackBuf lb;
+    GS_TRY(lb.make(ntiles, st));
+    scan_kernel<uint32_t, uint32_t, false><<<(unsigned)ntiles, kScanBlock, 0, st>>>(data, data, n, lb.view);
+    GS_LAUNCH_CHECK();
     return GSMAT_OK;
 }
 

@@ -64,23 +64,6 @@ __global__ void __launch_bounds__(kBlock) radix_upsweep(const K *__restrict__ ke
     }
 }
 
-// Exclusive scan of the digit-major count table (one CTA).
-__global__ void __launch_bounds__(1024) radix_scan_counts(uint32_t *counts, int len) {
-    __shared__ int64_t sm[1024 / 32 + 1];
-    const int per = (len + 1023) / 1024;
-    const int a = threadIdx.x * per;
-    const int b = a + per < len ? a + per : len;
-    int64_t s = 0;
-    for (int i = a; i < b; ++i) s += counts[i];
-    int64_t total;
-    int64_t ex = block_exclusive_sum<1024>(s, sm, &total);
-    for (int i = a; i < b; ++i) {
-        uint32_t c = counts[i];
-        counts[i] = (uint32_t)ex;
-        ex += c;
-    }
-}
-
 template <class K, bool HasVals>
 __global__ void __launch_bounds__(kBlock) radix_downsweep(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                                                          K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
@@ -242,7 +225,7 @@ int radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_b
         const int width = end_bit - shift < 8 ? end_bit - shift : 8;
         const int mask = (1 << width) - 1;
         radix_upsweep<K><<<num_ctas, kBlock, 0, st>>>(src_k, n, span, shift, mask, num_ctas, counts.as<uint32_t>());
-        radix_scan_counts<<<1, 1024, 0, st>>>(counts.as<uint32_t>(), kBins * num_ctas);
+        GS_TRY(exclusive_scan_u32_inplace(counts.as<uint32_t>(), (int64_t)kBins * num_ctas, st));
         if (vals) {
             radix_downsweep<K, true><<<num_ctas, kBlock, smem, st>>>(src_k, src_v, dst_k, dst_v, n, span, shift, mask,
                                                                      num_ctas, counts.as<uint32_t>());

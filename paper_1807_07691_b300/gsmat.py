@@ -212,6 +212,24 @@ class Table:
             _check(_lib.gsmat_table_copy(self._h, out.ctypes.data, 0, _stream_ptr(stream)))
         return out
 
+    def copy_to(self, dst, stream=None):
+        """Copy the table row-major into dst: a host numpy array or a host
+        (ideally pinned) / CUDA torch tensor of int32 with rows*cols
+        elements."""
+        rows, cols = self.shape
+        if rows == 0 or cols == 0:
+            return dst
+        if hasattr(dst, "data_ptr"):
+            if dst.numel() < rows * cols:
+                raise ValueError("destination too small")
+            _check(_lib.gsmat_table_copy(self._h, ctypes.c_void_p(dst.data_ptr()), 1 if dst.is_cuda else 0,
+                                         _stream_ptr(stream)))
+        else:
+            if dst.size < rows * cols or dst.dtype != np.int32 or not dst.flags.c_contiguous:
+                raise ValueError("destination must be a contiguous int32 array of rows*cols elements")
+            _check(_lib.gsmat_table_copy(self._h, dst.ctypes.data, 0, _stream_ptr(stream)))
+        return dst
+
     def to_torch(self, stream=None):
         """Row-major (rows, cols) int32 CUDA tensor (a copy)."""
         import torch
