@@ -245,6 +245,30 @@ GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n
  * Does not synchronise. */
 GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int64_t n, gsmat_stream_t stream);
 
+/* The same exclusive prefix sum, for callers that cannot allocate device
+ * memory: code that runs under a fixed device-memory budget already handed
+ * out to another allocator, or on a latency-critical path that must not
+ * enter the driver's allocator (which can block and synchronise the device).
+ * The paper has no counterpart; this is a library convenience.
+ *  - Allocates nothing: no cudaMalloc/cudaFree, no allocator hook.  The tile
+ *    descriptors live in a file-scope static device array of 256 KB (plus
+ *    32 bytes), which every GPU that loads the library holds until the
+ *    process exits.
+ *  - n <= gsmat_exclusive_scan_i32_noalloc_max() (2^26 = 67,108,864);
+ *    larger n returns GSMAT_ERR_CAPACITY without touching the device.
+ *  - The first call on a device looks the array's device address up once
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and clears the part it uses (stream-ordered
+ *    memsets) before its kernel; calls whose work overlaps on the GPU (other
+ *    streams, other host threads) race on it and must be serialised by the
+ *    caller.
+ *  - d_in, d_out: device arrays as for gsmat_exclusive_scan_i32.  Does not
+ *    synchronise. */
+GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_out, int64_t n,
+                                               gsmat_stream_t stream);
+GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void);
+
 /* ------------------------------------------------------------------------ */
 /* Kernel timing (CUDA events on the launching stream)                       */
 

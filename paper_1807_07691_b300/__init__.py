@@ -2,22 +2,25 @@
 
 The compute path is libgsmat.so (CUDA for sm_103a, C ABI in
 include/gsmat.h); ``gsmat`` is its ctypes binding.  Build the library with
-``python -m paper_1807_07691_b300.build``.
+``python -m paper_1807_07691_b300.build``.  The library is loaded on first
+use of any binding name (so the build module imports without it); a missing
+library raises ImportError then.
 """
 
-from .gsmat import (  # noqa: F401
-    COUNT_ONLY,
-    PLAN_ORDER,
-    SORTED,
-    GsmatError,
-    Store,
-    Table,
-    exclusive_scan_i32,
-    header_functions,
-    lib,
-    plan,
-    profile_enable,
-    profile_read,
-    radix_sort_u64,
-    use_torch_allocator,
-)
+_BINDING_NAMES = {
+    "COUNT_ONLY", "PLAN_ORDER", "SORTED", "GsmatError", "Store", "Table", "exclusive_scan_i32",
+    "exclusive_scan_i32_noalloc", "exclusive_scan_i32_noalloc_max", "header_functions", "lib", "plan",
+    "profile_enable", "profile_read", "radix_sort_u64", "use_torch_allocator",
+}
+
+
+def __getattr__(name):
+    if name in _BINDING_NAMES:
+        from . import gsmat
+
+        return getattr(gsmat, name)
+    raise AttributeError(name)
+
+
+def __dir__():
+    return sorted(_BINDING_NAMES | {"build", "gsmat"})

@@ -164,6 +164,14 @@ GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int6
     return gs::exclusive_scan_i32(d_in, d_out, n, (cudaStream_t)stream, nullptr);
 }
 
+GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_out, int64_t n,
+                                               gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::exclusive_scan_i32_noalloc(d_in, d_out, n, (cudaStream_t)stream);
+}
+
+GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void) { return gs::exclusive_scan_i32_noalloc_max(); }
+
 GSMAT_API int gsmat_profile_enable(int on) { return gs::profile_enable(on); }
 
 GSMAT_API int gsmat_profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset) {

@@ -326,6 +326,11 @@ int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
 // set if a bounded wait expired (may be null).
 int exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st, int *err_word);
 
+// exclusive_scan_i32 with its scratch in a static device array (no
+// allocation); n at most exclusive_scan_i32_noalloc_max().
+int exclusive_scan_i32_noalloc(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st);
+int64_t exclusive_scan_i32_noalloc_max();
+
 // In-place exclusive scan of uint32 values whose total fits in 32 bits.
 int exclusive_scan_u32_inplace(uint32_t *data, int64_t n, cudaStream_t st);
 

@@ -2,6 +2,8 @@
 // stable selection of int32 values.  The scan is the offset computation of
 // the pre-allocation step of the GPU join (Sec. 7.2.2, Alg. 4: P_i =
 // P_{i-1} + N_{i-1}), done on the device in int64.
+#include <mutex>
+
 #include "common.cuh"
 #include "select.cuh"
 
@@ -87,6 +89,81 @@ int exclusive_scan_u32_inplace(uint32_t *data, int64_t n, cudaStream_t st) {
     LookbackBuf lb;
     GS_TRY(lb.make(ntiles, st));
     scan_kernel<uint32_t, uint32_t, false><<<(unsigned)ntiles, kScanBlock, 0, st>>>(data, data, n, lb.view);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan that allocates nothing (for callers that cannot allocate
+// device memory).  Its scratch -- one descriptor per tile, the dynamic tile
+// counter and an error word -- is this file-scope array, resident on every
+// device that loads the library until the process exits.  Host code must not
+// pass the array's name to a kernel (on the host it is only a stand-in);
+// the device address is looked up once per device with
+// cudaGetSymbolAddress and cached.
+
+constexpr int64_t kNoAllocMaxTiles = 32768;  // 256 KB of tile descriptors
+constexpr int64_t kNoAllocMaxItems = kNoAllocMaxTiles * kScanTile;  // 67,108,864
+// [0, kNoAllocMaxTiles): tile descriptors; then 4 words: counter | error
+static __device__ __align__(256) unsigned long long g_noalloc_scan_scratch[kNoAllocMaxTiles + 4];
+
+namespace {
+
+struct NoAllocSetup {
+    std::mutex mu;
+    unsigned long long *addr[64] = {nullptr};
+};
+NoAllocSetup &noalloc_setup() {
+    static NoAllocSetup s;
+    return s;
+}
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device).
+int noalloc_scratch_ptr(unsigned long long **out) {
+    int dev = 0;
+    GS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(GSMAT_ERR_CUDA, "device ordinal %d out of range", dev);
+    NoAllocSetup &s = noalloc_setup();
+    std::lock_guard<std::mutex> lk(s.mu);
+    if (!s.addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scan_scratch);
+        if (e != cudaSuccess || !p) {
+            return set_error(GSMAT_ERR_CUDA, "cudaGetSymbolAddress of the scan scratch: %s", cudaGetErrorString(e));
+        }
+        s.addr[dev] = static_cast<unsigned long long *>(p);
+    }
+    *out = s.addr[dev];
+    return GSMAT_OK;
+}
+
+}  // namespace
+
+int64_t exclusive_scan_i32_noalloc_max() { return kNoAllocMaxItems; }
+
+int exclusive_scan_i32_noalloc(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st) {
+    if (n < 0 || (n > 0 && !in) || !out) return set_error(GSMAT_ERR_INVALID_ARG, "scan: bad arguments");
+    if (n > kNoAllocMaxItems) {
+        return set_error(GSMAT_ERR_CAPACITY, "scan without allocation: n = %lld exceeds the maximum %lld",
+                         (long long)n, (long long)kNoAllocMaxItems);
+    }
+    unsigned long long *scratch = nullptr;
+    GS_TRY(noalloc_scratch_ptr(&scratch));
+    if (n == 0) {
+        GS_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+        return GSMAT_OK;
+    }
+    const int64_t ntiles = (n + kScanTile - 1) / kScanTile;
+    // the array keeps the previous call's contents: clear the descriptors in
+    // use and the counter / error words
+    GS_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)ntiles, st));
+    GS_CUDA(cudaMemsetAsync(scratch + kNoAllocMaxTiles, 0, sizeof(unsigned long long) * 4, st));
+    LookbackScratch view;
+    view.status = scratch;
+    view.tile_counter = reinterpret_cast<unsigned int *>(scratch + kNoAllocMaxTiles);
+    view.error = reinterpret_cast<int *>(scratch + kNoAllocMaxTiles + 1);
+    scan_kernel<int32_t, int64_t, true><<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, out, n, view);
     GS_LAUNCH_CHECK();
     return GSMAT_OK;
 }

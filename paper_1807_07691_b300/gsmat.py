@@ -97,6 +97,8 @@ def _load():
         "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
         "gsmat_radix_sort_u64": ([vp, vp, i64, c_int, c_int, vp], c_int),
         "gsmat_exclusive_scan_i32": ([vp, vp, i64, vp], c_int),
+        "gsmat_exclusive_scan_i32_noalloc": ([vp, vp, i64, vp], c_int),
+        "gsmat_exclusive_scan_i32_noalloc_max": ([], i64),
         "gsmat_profile_enable": ([c_int], c_int),
         "gsmat_profile_read": ([vp, i32, P(i32), c_int], c_int),
     }
@@ -359,6 +361,17 @@ def exclusive_scan_i32(src, dst, stream=None):
     """dst[0..n] (int64 CUDA tensor) = exclusive prefix sums of src (int32)."""
     _check(_lib.gsmat_exclusive_scan_i32(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
                                          src.numel(), _stream_ptr(stream)))
+
+
+def exclusive_scan_i32_noalloc(src, dst, stream=None):
+    """As exclusive_scan_i32, with no device allocation (static scratch;
+    n <= exclusive_scan_i32_noalloc_max(); overlapping calls race)."""
+    _check(_lib.gsmat_exclusive_scan_i32_noalloc(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                                 src.numel(), _stream_ptr(stream)))
+
+
+def exclusive_scan_i32_noalloc_max() -> int:
+    return int(_lib.gsmat_exclusive_scan_i32_noalloc_max())
 
 
 def profile_enable(on: bool = True):
