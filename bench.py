@@ -120,6 +120,27 @@ class ClockSampler:
         return out
 
 
+def reduce_over_ranks(my_ms: float, my_rows: int, device: str = "cpu"):
+    """Max of the ranks' timed milliseconds and sum of their result rows
+    (replicas: every rank runs the whole workload; the slowest rank sets the
+    job's time).  Identity when torch.distributed is not initialised."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(my_ms), int(my_rows)
+    t = torch.tensor([float(my_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    r = torch.tensor([int(my_rows)], dtype=torch.int64, device=device)
+    dist.all_reduce(r, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(r.item())
+
+
+def job_value(world_size: int, steps: int, queries_per_step: int, total_ms: float) -> float:
+    """Whole-job queries/s: all ranks' queries over the slowest rank's time."""
+    return world_size * steps * queries_per_step / (total_ms / 1e3)
+
+
 def _flush_l2(torch, buf):
     buf.add_(1)
 
@@ -197,14 +218,7 @@ def run_gsmat(args):
     gs.profile_enable(False)
     prof = gs.profile_read(reset=True)
     my_ms = float(sum(step_ms))
-    if ws > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([my_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    else:
-        total_ms = my_ms
+    total_ms, _ = reduce_over_ranks(my_ms, rows_total, device="cuda")
     q_lat = np.array([e0.elapsed_time(e1) for (e0, e1) in lat])
 
     # end-to-end through the public API with host buffers: H2D of the triples
@@ -233,6 +247,8 @@ def run_gsmat(args):
         if it > 0:
             e2e_ms.append(a.elapsed_time(b))
 
+    batched = None if args.no_batched else run_batched(args, gs, torch, d_tri, stream)
+
     if rank != 0:
         if ws > 1:
             import torch.distributed as dist
@@ -252,7 +268,7 @@ def run_gsmat(args):
                 "per_launch_ms": round(p["total_ms"] / max(1, p["launches"]), 4),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
     launches = int(sum(p["launches"] for p in prof.values()))
-    value = ws * args.steps * nq / (total_ms / 1e3)
+    value = job_value(ws, args.steps, nq, total_ms)
     rows_per_s = ws * rows_total / (total_ms / 1e3)
     e2e_value = nq / (float(np.median(e2e_ms)) / 1e3)
     out = {
@@ -291,12 +307,85 @@ def run_gsmat(args):
         "clocks": clk.summary(),
         "generation_s": round(gen_s, 1),
     }
+    if batched is not None:
+        out["batched"] = batched
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(triples, queries, budget_s=args.cpu_budget)
     if ws > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+    return out
+
+
+def run_batched(args, gs, torch, d_tri, stream):
+    """The batched mix (medium graph, 4096 BGPs of 2-8 patterns, star:chain:
+    snowflake:cycle = 4:3:2:1): the plain path one query at a time against
+    one prepared batch (persistent kernel, CUDA graph), each timed with CUDA
+    events after a warm-up pass; results are bit-identical (tested)."""
+    import synth
+
+    t0 = time.time()
+    bq = synth.make_batched_queries(args.batched_n)
+    gen_s = time.time() - t0
+    S = gs.Store(d_tri, stream=stream)
+
+    def plain_pass():
+        rows = 0
+        for q in bq:
+            T = S.query(q, stream=stream)
+            rows += T.rows
+            T.free()
+        return rows
+
+    plain_pass()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    rows_plain = plain_pass()
+    b.record(stream)
+    b.synchronize()
+    plain_ms = a.elapsed_time(b)
+
+    tuned = gs.batch_autotune(S, bq[:512], stream=stream)
+    t_prep = time.perf_counter()
+    B = gs.Batch(S, bq, config=tuned, stream=stream)
+    prep_ms = 1e3 * (time.perf_counter() - t_prep)
+    B.execute(stream)
+    torch.cuda.synchronize()
+    runs = []
+    for _ in range(max(3, args.steps)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.execute(stream)
+        b.record(stream)
+        b.synchronize()
+        runs.append(a.elapsed_time(b))
+    st = B.stats()
+    rows_batch = sum(B.result(i)[0] for i in range(len(bq)))
+    assert rows_batch == rows_plain, (rows_batch, rows_plain)
+    batch_ms = float(np.median(runs))
+    out = {
+        "workload": f"{len(bq)} BGPs, 2-8 patterns, star:chain:snowflake:cycle 4:3:2:1, medium graph",
+        "queries_per_s": round(len(bq) / (batch_ms / 1e3), 1),
+        "plain_queries_per_s": round(len(bq) / (plain_ms / 1e3), 1),
+        "speedup_vs_plain": round(plain_ms / batch_ms, 2),
+        "batch_ms": round(batch_ms, 3),
+        "plain_ms": round(plain_ms, 3),
+        "prepare_ms": round(prep_ms, 2),
+        "kernel_ms": round(st["kernel_ms"], 3),
+        "reorder_ms": round(st["reorder_ms"], 3),
+        "in_kernel": st["n_in_kernel"],
+        "reordered": st["n_reordered"],
+        "fallback": st["n_fallback"],
+        "result_rows": int(rows_batch),
+        "tuned": {"block": tuned["block"], "ctas_per_sm": tuned["ctas_per_sm"]},
+        "generation_s": round(gen_s, 1),
+    }
+    B.free()
+    S.free()
     return out
 
 
@@ -425,12 +514,31 @@ def run_micro(args):
                 ms.append(a.elapsed_time(b))
         t = float(np.median(ms))
         out.update({"ms": round(t, 4), "algo_GBps": round(n * 12.0 / 1e9 / (t / 1e3), 1)})
+    elif args.micro == "query":
+        triples, queries, _ = _workload()
+        S = gs.Store(torch.from_numpy(np.array(triples, copy=True)).cuda())
+        q = queries[args.query_index]
+        ms = []
+        rows = 0
+        for it in range(args.warmup + args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            T = S.query(q)
+            b.record()
+            b.synchronize()
+            rows = T.rows
+            T.free()
+            if it >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        out.update({"query": q.name, "rows": rows, "ms": round(float(np.median(ms)), 4)})
     return out
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["sort", "scan"], default=None,
+    ap.add_argument("--query-index", type=int, default=14)
+    ap.add_argument("--micro", choices=["sort", "scan", "query"], default=None,
                     help="time one primitive on a synthetic input instead of the workload")
     ap.add_argument("--n", type=int, default=1 << 25)
     ap.add_argument("--bits", type=int, default=40)
@@ -439,6 +547,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsmat", choices=["gsmat", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-n", type=int, default=4096)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.micro:

@@ -210,6 +210,82 @@ GSMAT_API int gsmat_table_stats(const gsmat_table *table, gsmat_query_stats *sta
 GSMAT_API void gsmat_table_free(gsmat_table *table);
 
 /* ------------------------------------------------------------------------ */
+/* Batched evaluation: many BGPs in one persistent kernel                    */
+/* (the same results as gsmat_query with GSMAT_SORTED, query by query)       */
+
+typedef struct {
+    const gsmat_pattern *pats; /* host array */
+    int32_t n_pats;
+    int32_t n_vars;
+} gsmat_bgp;
+
+typedef struct gsmat_batch gsmat_batch;
+
+typedef struct {
+    int32_t block;        /* threads per CTA: 128, 256 or 512 (0: 256) */
+    int32_t ctas_per_sm;  /* persistent CTAs per SM, 1..16 (0: 4) */
+    int64_t arena_bytes;  /* device arena for intermediate tables (0: 1 GiB) */
+    int64_t max_rows;     /* largest table a CTA builds (0: 2^22); queries that
+                             need more run on the plain path */
+    int32_t use_graph;    /* 1: capture the device work as a CUDA graph */
+    int32_t _reserved;
+} gsmat_batch_config;
+
+typedef struct {
+    int32_t n_queries;
+    int32_t n_in_kernel;  /* finished inside the persistent kernel */
+    int32_t n_reordered;  /* kernel result reordered by the multi-CTA sort */
+    int32_t n_fallback;   /* re-run on the plain path (arena or row cap) */
+    double kernel_ms;     /* device time of the last run's graph / kernel */
+    double reorder_ms;    /* device time of the batched reorder of large results */
+    int64_t arena_used;   /* bytes of arena the last run used */
+    int32_t block;
+    int32_t grid;
+} gsmat_batch_stats_t;
+
+/* Plan a batch of n >= 1 BGPs against a store and prepare its device run.
+ * Each query is planned by Alg. 1 (Sec. 6.2) into a step program; all
+ * programs are uploaded together; the device work (queue and arena reset,
+ * the persistent kernel, the copy of result descriptors) is captured as a
+ * CUDA graph when cfg->use_graph (cfg may be NULL: defaults).  Validation
+ * and errors as gsmat_query for every BGP.  The store must outlive the
+ * batch.  Synchronises `stream`. */
+GSMAT_API int gsmat_batch_prepare(const gsmat_store *store, const gsmat_bgp *bgps, int32_t n,
+                                  const gsmat_batch_config *cfg, gsmat_stream_t stream, gsmat_batch **out);
+
+/* Run (or re-run) a prepared batch.  A persistent kernel pulls query ids
+ * from a device work queue; each CTA runs one query's joins at a time with
+ * tables bump-allocated from the arena; queries that overflow are re-run on
+ * the plain path, large results are reordered by the multi-CTA sort.  After
+ * the call every result is final and valid until the next execute or free.
+ * Work is ordered after prior work on `stream`, and later work on `stream`
+ * is ordered after it.  Synchronises internally. */
+GSMAT_API int gsmat_batch_execute(gsmat_batch *batch, gsmat_stream_t stream);
+
+/* Shape of query i's result (columns = variables 0..V-1, rows ascending);
+ * *path (may be NULL): 0 kernel, 1 plain path, 2 kernel + multi-CTA reorder. */
+GSMAT_API int gsmat_batch_result(const gsmat_batch *batch, int32_t i, int64_t *rows, int32_t *cols, int32_t *path);
+
+/* Device pointer to column `col` of query i's result (it may point into the
+ * store for single-pattern results; read only). */
+GSMAT_API int gsmat_batch_column(const gsmat_batch *batch, int32_t i, int32_t col, const int32_t **d_col);
+
+/* Copy query i's result as row-major int32[rows][cols] (as gsmat_table_copy). */
+GSMAT_API int gsmat_batch_copy(const gsmat_batch *batch, int32_t i, int32_t *dst, int dst_on_device,
+                               gsmat_stream_t stream);
+
+GSMAT_API int gsmat_batch_stats(const gsmat_batch *batch, gsmat_batch_stats_t *stats);
+
+GSMAT_API void gsmat_batch_free(gsmat_batch *batch);
+
+/* Autotuner of the persistent kernel's CTA shape: times every (block,
+ * ctas_per_sm) in {128, 256, 512} x {1, 2, 4, 8} (at most 2048 threads per
+ * SM) on the given sample batch and writes the fastest into *best (the other
+ * fields come from base, which may be NULL).  Synchronises `stream`. */
+GSMAT_API int gsmat_batch_autotune(const gsmat_store *store, const gsmat_bgp *bgps, int32_t n,
+                                   const gsmat_batch_config *base, gsmat_stream_t stream, gsmat_batch_config *best);
+
+/* ------------------------------------------------------------------------ */
 /* Host planner (Alg. 1; Sec. 6.2), callable without a GPU                   */
 
 /* Order a BGP's patterns and estimate the intermediate sizes.

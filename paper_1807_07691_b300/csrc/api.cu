@@ -6,6 +6,16 @@
 #include "store.cuh"
 
 namespace gs {
+int batch_prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *cfg,
+                  cudaStream_t st, gsmat_batch **out);
+int batch_execute(gsmat_batch *B, cudaStream_t st);
+int batch_result(const gsmat_batch *B, int32_t i, int64_t *rows, int32_t *cols, int32_t *path);
+int batch_column(const gsmat_batch *B, int32_t i, int32_t c, const int32_t **d_col);
+int batch_copy(const gsmat_batch *B, int32_t i, int32_t *dst, int dst_on_device, cudaStream_t st);
+int batch_stats(const gsmat_batch *B, gsmat_batch_stats_t *s);
+int batch_autotune(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *base,
+                   cudaStream_t st, gsmat_batch_config *best);
+void batch_free(gsmat_batch *B);
 const char *last_error();
 int set_allocator(gsmat_alloc_fn a, gsmat_free_fn f, void *ctx);
 int profile_enable(int on);
@@ -143,6 +153,46 @@ GSMAT_API int gsmat_table_stats(const gsmat_table *T, gsmat_query_stats *stats) 
 }
 
 GSMAT_API void gsmat_table_free(gsmat_table *T) { delete T; }
+
+GSMAT_API int gsmat_batch_prepare(const gsmat_store *store, const gsmat_bgp *bgps, int32_t n,
+                                  const gsmat_batch_config *cfg, gsmat_stream_t stream, gsmat_batch **out) {
+    gs::clear_error();
+    return gs::batch_prepare(store, bgps, n, cfg, (cudaStream_t)stream, out);
+}
+
+GSMAT_API int gsmat_batch_execute(gsmat_batch *batch, gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::batch_execute(batch, (cudaStream_t)stream);
+}
+
+GSMAT_API int gsmat_batch_result(const gsmat_batch *batch, int32_t i, int64_t *rows, int32_t *cols, int32_t *path) {
+    gs::clear_error();
+    return gs::batch_result(batch, i, rows, cols, path);
+}
+
+GSMAT_API int gsmat_batch_column(const gsmat_batch *batch, int32_t i, int32_t col, const int32_t **d_col) {
+    gs::clear_error();
+    return gs::batch_column(batch, i, col, d_col);
+}
+
+GSMAT_API int gsmat_batch_copy(const gsmat_batch *batch, int32_t i, int32_t *dst, int dst_on_device,
+                               gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::batch_copy(batch, i, dst, dst_on_device, (cudaStream_t)stream);
+}
+
+GSMAT_API int gsmat_batch_stats(const gsmat_batch *batch, gsmat_batch_stats_t *stats) {
+    gs::clear_error();
+    return gs::batch_stats(batch, stats);
+}
+
+GSMAT_API void gsmat_batch_free(gsmat_batch *batch) { gs::batch_free(batch); }
+
+GSMAT_API int gsmat_batch_autotune(const gsmat_store *store, const gsmat_bgp *bgps, int32_t n,
+                                   const gsmat_batch_config *base, gsmat_stream_t stream, gsmat_batch_config *best) {
+    gs::clear_error();
+    return gs::batch_autotune(store, bgps, n, base, (cudaStream_t)stream, best);
+}
 
 GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
                          const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out, double *est_out) {

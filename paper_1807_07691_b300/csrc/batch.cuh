@@ -1,0 +1,76 @@
+// Device-side program of a batch of BGPs and the persistent kernel's
+// arguments (see batch.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace gs {
+
+// One plan step, with every operand resolved to a column of the running
+// table (or a constant) on the host.
+struct BStep {
+    int32_t kind;      // GSMAT_STEP_*
+    int32_t slot;      // predicate slot in the store
+    int32_t s_col;     // column holding the subject, -1 when constant or new
+    int32_t o_col;     // column holding the object, -1 when constant or new
+    int32_t s_const;   // subject constant (when s_col < 0 and the subject is known)
+    int32_t o_const;
+    int32_t diag;      // CROSS of ?x p ?x
+    int32_t c_first;   // EXPAND from a constant: entry range of its row
+    int32_t c_last;
+    int32_t _pad;
+};
+
+struct BQuery {
+    int32_t step0;     // first step in the step array
+    int32_t n_steps;
+    int32_t n_vars;
+    int32_t m_sort;    // leading variables to sort for variable order (0: none)
+    int32_t absent;    // a predicate is missing: empty result
+    int32_t _pad;
+    int32_t col_of_var[32];  // final plan column of each variable
+};
+
+enum { BR_OK = 0, BR_OVERFLOW = 1, BR_NEEDS_SORT = 2 };
+
+struct BResult {
+    int64_t rows;
+    int32_t status;
+    int32_t ncols;
+    const int32_t *col[32];  // per variable
+};
+
+struct BatchArgs {
+    StoreView sv;
+    const PredSide *sides;   // [2][n_pred]
+    int n_pred;
+    int bits;                // bits per packed variable in the sort key
+    const BStep *steps;
+    const BQuery *queries;
+    int n_queries;
+    BResult *results;
+    char *arena;
+    unsigned long long *arena_top;
+    unsigned long long arena_cap;
+    unsigned int *queue_head;
+    int64_t max_rows;        // per table; larger tables send the query to the plain path
+};
+
+int launch_batch_kernel(const BatchArgs &a, int block, int grid, cudaStream_t st);
+
+// One result table of a segmented reorder: its rows are rows
+// [row_off, row_off + rows) of the concatenation; col[v] = the column of
+// variable v (variables 0..m-1 are the sort key); out = V columns of rows.
+struct SegDesc {
+    int64_t row_off;
+    int64_t rows;
+    int32_t m;
+    int32_t V;
+    const int32_t *col[32];
+    int32_t *out;
+};
+int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, const uint32_t *perm_in,
+                    int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st);
+int launch_seg_gather(const SegDesc *segs, int n_segs, int64_t total, const uint32_t *perm, cudaStream_t st);
+
+}  // namespace gs

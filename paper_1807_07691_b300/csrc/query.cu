@@ -25,6 +25,20 @@
 
 namespace gs {
 
+int leading_sort_vars(const int32_t *plan_vars, int V) {
+    for (int cand = 0; cand <= V; ++cand) {
+        int want = cand;
+        bool ok = true;
+        for (int c = 0; c < V && ok; ++c) {
+            if (plan_vars[c] < cand) continue;
+            if (plan_vars[c] != want) ok = false;
+            want++;
+        }
+        if (ok) return cand;
+    }
+    return V;
+}
+
 namespace {
 
 struct Tbl {
@@ -87,20 +101,7 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
     // smallest m: dropping variables 0..m-1 from the column order leaves
     // m, m+1, ..., V-1 in order (stable sort by a key over an input sorted
     // by S yields order (key, S))
-    int m = V;
-    for (int cand = 0; cand <= V; ++cand) {
-        int want = cand;
-        bool ok = true;
-        for (int c = 0; c < V && ok; ++c) {
-            if (t.vars[c] < cand) continue;
-            if (t.vars[c] != want) ok = false;
-            want++;
-        }
-        if (ok) {
-            m = cand;
-            break;
-        }
-    }
+    const int m = leading_sort_vars(t.vars, V);
     out.rows = t.rows;
     out.ncols = V;
     if (t.rows <= 1 || m == 0) {
@@ -133,7 +134,7 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
         } else {
             GS_TRY(launch_pack_rows(kc, nc, bits, perm.as<uint32_t>(), n, keys.as<uint64_t>(), cx.st));
         }
-        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, nc * bits, cx.st));
+        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, nc * bits, cx.st, cx.d_err()));
     }
     // variables 0..k0-1 are unpacked from the sorted keys, the others are
     // gathered through the permutation
@@ -421,6 +422,46 @@ int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n
         return rc;
     }
     T->storage.st = nullptr;  // freed on the legacy stream later
+    *out = T;
+    return GSMAT_OK;
+}
+
+int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const int32_t *plan_vars, int V, int64_t rows,
+                 cudaStream_t st, gsmat_table **out) {
+    *out = nullptr;
+    Ctx cx;
+    cx.S = S;
+    cx.st = st;
+    cx.h = pinned_scratch(4 + 4 * GSMAT_MAX_PATTERNS);
+    if (!cx.h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    GS_TRY(cx.qstat.alloc(4 * sizeof(int64_t), st));
+    GS_CUDA(cudaMemsetAsync(cx.qstat.p, 0, 4 * sizeof(int64_t), st));
+    Tbl t;
+    t.rows = rows;
+    t.ncols = V;
+    for (int c = 0; c < V; ++c) {
+        t.col[c] = plan_cols[c];
+        t.vars[c] = plan_vars[c];
+    }
+    Tbl fin;
+    GS_TRY(canonical_order(cx, t, fin));
+    gsmat_table *T = new gsmat_table();
+    T->rows = fin.rows;
+    T->ncols = fin.ncols;
+    for (int c = 0; c < fin.ncols; ++c) {
+        T->vars[c] = fin.vars[c];
+        T->col[c] = fin.col[c];
+    }
+    T->storage = std::move(fin.buf);
+    T->stats.result_rows = fin.rows;
+    GS_CUDA(cudaMemcpyAsync(cx.h, cx.qstat.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || *reinterpret_cast<int *>(cx.h + 1)) {
+        delete T;
+        return e != cudaSuccess ? set_error(GSMAT_ERR_CUDA, "reorder: %s", cudaGetErrorString(e))
+                                : set_error(GSMAT_ERR_DEVICE_CHECK, "reorder: a bounded wait expired");
+    }
+    T->storage.st = nullptr;
     *out = T;
     return GSMAT_OK;
 }

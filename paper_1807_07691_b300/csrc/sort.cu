@@ -4,12 +4,14 @@
 // (p, o, s), which lays out every predicate's matrix M_h of Sec. 5.3 row by
 // row) and by the final canonical ordering of a result table.
 //
-// Per 8-bit digit pass, three kernels over an even share of the input per
-// CTA: an upsweep digit histogram per CTA, one scan of the digit-major
-// histogram table, and a downsweep that ranks each tile of keys stably
-// (warp match_any over the digit, per-warp counters, cross-warp prefix),
-// stages the tile in shared memory in digit order and writes each digit's
-// run to its global offset, so that the writes of a run are contiguous.
+// Onesweep structure: one histogram kernel counts the digits of every pass
+// at once; then each 8-bit pass is a single kernel in which a CTA ranks one
+// tile of keys stably (warp match_any on the digit, per-warp counters,
+// cross-warp prefix), publishes its per-digit counts, finds the counts of
+// all earlier tiles per digit by decoupled look-back (one thread per
+// digit, bounded waits), stages the tile in shared memory in digit order
+// and writes each digit's run to its global position.  Keys and payloads
+// are read and written once per pass.
 #include "common.cuh"
 
 namespace gs {
@@ -18,6 +20,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kBins = 256;
+constexpr int kMaxPasses = 8;
 
 template <class K>
 struct SortTraits;
@@ -35,130 +38,157 @@ __device__ __forceinline__ int digit_of(K k, int shift, int mask) {
     return (int)((k >> shift) & (K)mask);
 }
 
+// Tile descriptor of one digit: bits 56-63 pass epoch, 54-55 state, 0-53
+// count.  A word whose epoch is not the current pass's is "not ready", so a
+// single memset per sort serves every pass.
+constexpr uint64_t kDescAggregate = 1;
+constexpr uint64_t kDescPrefix = 2;
+__device__ __forceinline__ unsigned long long desc_pack(uint32_t epoch, uint64_t state, uint64_t value) {
+    return ((unsigned long long)epoch << 56) | (state << 54) | value;
+}
+
 template <class K>
-__global__ void __launch_bounds__(kBlock) radix_upsweep(const K *__restrict__ keys, int64_t n, int64_t span,
-                                                       int shift, int mask, int num_ctas,
-                                                       uint32_t *__restrict__ counts) {
-    __shared__ uint32_t hist[kWarps * kBins];
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kBlock) hist[i] = 0;
+__global__ void __launch_bounds__(kBlock) onesweep_histogram(const K *__restrict__ keys, int64_t n, int begin_bit,
+                                                            int end_bit, int n_pass, uint32_t *__restrict__ hist) {
+    extern __shared__ uint32_t hsm[];  // [kWarps][n_pass][kBins]
+    const int per_warp = n_pass * kBins;
+    for (int i = threadIdx.x; i < kWarps * per_warp; i += kBlock) hsm[i] = 0;
     __syncthreads();
-    const int64_t begin = (int64_t)blockIdx.x * span;
-    const int64_t end = begin + span < n ? begin + span : n;
-    uint32_t *wh = hist + (threadIdx.x >> 5) * kBins;
-    int64_t i = begin + threadIdx.x;
-    for (; i + 3 * kBlock < end; i += 4 * kBlock) {
-        K a = __ldg(keys + i), b = __ldg(keys + i + kBlock), c = __ldg(keys + i + 2 * kBlock),
-          d = __ldg(keys + i + 3 * kBlock);
-        atomicAdd(&wh[digit_of(a, shift, mask)], 1u);
-        atomicAdd(&wh[digit_of(b, shift, mask)], 1u);
-        atomicAdd(&wh[digit_of(c, shift, mask)], 1u);
-        atomicAdd(&wh[digit_of(d, shift, mask)], 1u);
+    uint32_t *wh = hsm + (threadIdx.x >> 5) * per_warp;
+    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
+        const K k = __ldg(keys + i);
+        for (int p = 0; p < n_pass; ++p) {
+            const int shift = begin_bit + 8 * p;
+            const int width = end_bit - shift < 8 ? end_bit - shift : 8;
+            atomicAdd(&wh[p * kBins + digit_of(k, shift, (1 << width) - 1)], 1u);
+        }
     }
-    for (; i < end; i += kBlock) atomicAdd(&wh[digit_of(__ldg(keys + i), shift, mask)], 1u);
     __syncthreads();
-    for (int d = threadIdx.x; d < kBins; d += kBlock) {
+    for (int i = threadIdx.x; i < per_warp; i += kBlock) {
         uint32_t s = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += hist[w * kBins + d];
-        counts[(int64_t)d * num_ctas + blockIdx.x] = s;
+        for (int w = 0; w < kWarps; ++w) s += hsm[w * per_warp + i];
+        if (s) atomicAdd(hist + i, s);
     }
 }
 
 template <class K, bool HasVals>
-__global__ void __launch_bounds__(kBlock) radix_downsweep(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                                                         K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                                                         int64_t n, int64_t span, int shift, int mask, int num_ctas,
-                                                         const uint32_t *__restrict__ offsets) {
+__global__ void __launch_bounds__(kBlock, 4) onesweep_pass(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                                                       K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                                                       int64_t n, int shift, int mask,
+                                                       const uint32_t *__restrict__ hist_pass,
+                                                       unsigned long long *__restrict__ desc,
+                                                       unsigned int *__restrict__ tile_counter, uint32_t epoch,
+                                                       int *__restrict__ err) {
     constexpr int ITEMS = SortTraits<K>::kItems;
     constexpr int TILE = kBlock * ITEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *skeys = reinterpret_cast<K *>(smem_raw);
     uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + TILE);
-    uint32_t *whist = svals + (HasVals ? TILE : 0);
-    uint32_t *running = whist + kWarps * kBins;
-    uint32_t *tstart = running + kBins;
-    uint32_t *tcount = tstart + kBins;
+    uint32_t *whist = svals + (HasVals ? TILE : 0);  // [kWarps][kBins]
+    uint32_t *tstart = whist + kWarps * kBins;
+    uint32_t *gbase = tstart + kBins;
     __shared__ int64_t scan_tmp[kWarps + 1];
+    __shared__ int tile_sm;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kBins; d += kBlock) running[d] = offsets[(int64_t)d * num_ctas + blockIdx.x];
-    const int64_t begin = (int64_t)blockIdx.x * span;
-    const int64_t end = begin + span < n ? begin + span : n;
+    if (threadIdx.x == 0) tile_sm = (int)atomicAdd(tile_counter, 1u);
+    for (int i = threadIdx.x; i < kWarps * kBins; i += kBlock) whist[i] = 0;
+    __syncthreads();
+    const int tile = tile_sm;
+    const int64_t t0 = (int64_t)tile * TILE;
+    const int valid = (int)((n - t0) < TILE ? (n - t0) : TILE);
     const unsigned lt_mask = (1u << lane) - 1u;
     uint32_t *wh = whist + warp * kBins;
 
-    for (int64_t tile0 = begin; tile0 < end; tile0 += TILE) {
-        const int valid = (int)((end - tile0) < TILE ? (end - tile0) : TILE);
-        for (int i = threadIdx.x; i < kWarps * kBins; i += kBlock) whist[i] = 0;
-        __syncthreads();
-        K k[ITEMS];
-        uint32_t v[ITEMS];
-        int dg[ITEMS];
-        uint32_t rk[ITEMS];
+    K k[ITEMS];
+    uint32_t v[ITEMS];
+    uint32_t dr[ITEMS];  // rank within the warp << 8 | digit
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            // warp-striped: stable order inside the tile is (warp, j, lane)
-            const int idx = warp * (32 * ITEMS) + j * 32 + lane;
-            if (idx < valid) {
-                k[j] = keys_in[tile0 + idx];
-                v[j] = HasVals ? vals_in[tile0 + idx] : 0u;
-                dg[j] = digit_of(k[j], shift, mask);
-            } else {
-                k[j] = ~K(0);
-                v[j] = 0u;
-                dg[j] = kBins - 1;  // padding ranks last in the last bucket
+    for (int j = 0; j < ITEMS; ++j) {
+        // warp-striped: stable order inside the tile is (warp, j, lane)
+        const int idx = warp * (32 * ITEMS) + j * 32 + lane;
+        if (idx < valid) {
+            k[j] = keys_in[t0 + idx];
+            v[j] = HasVals ? vals_in[t0 + idx] : 0u;
+            dr[j] = (uint32_t)digit_of(k[j], shift, mask);
+        } else {
+            k[j] = ~K(0);
+            v[j] = 0u;
+            dr[j] = kBins - 1;  // padding ranks last in the last bucket
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const int d = (int)dr[j];
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader) {
+            base = wh[d];
+            wh[d] = base + (uint32_t)__popc(peers);
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
+        dr[j] = ((base + (uint32_t)__popc(peers & lt_mask)) << 8) | (uint32_t)d;
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit (thread d): cross-warp prefix, tile count, tile start
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = whist[w * kBins + d];
+        whist[w * kBins + d] = cnt;
+        cnt += c;
+    }
+    int64_t tot;
+    const int64_t ts = block_exclusive_sum<kBlock>((int64_t)cnt, scan_tmp, &tot);
+    tstart[d] = (uint32_t)ts;
+    const uint32_t real = cnt - (d == kBins - 1 ? (uint32_t)(TILE - valid) : 0u);
+    // global start of digit d in this pass (exclusive scan of the histogram)
+    const int64_t dbase = block_exclusive_sum<kBlock>((int64_t)__ldg(hist_pass + d), scan_tmp, &tot);
+    // publish this tile's count of digit d, then look back for the earlier ones
+    uint64_t excl = 0;
+    if (tile == 0) {
+        atomicExch(desc + d, desc_pack(epoch, kDescPrefix, real));
+    } else {
+        atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescAggregate, real));
+        int j = tile - 1;
+        int polls = 0;
+        while (j >= 0) {
+            const unsigned long long w = *(const volatile unsigned long long *)(desc + (int64_t)j * kBins + d);
+            const uint64_t state = (w >> 54) & 3;
+            if ((uint32_t)(w >> 56) != epoch || state == 0) {
+                if (++polls > kLookbackPollLimit) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
             }
+            excl += w & ((1ull << 54) - 1);
+            if (state == kDescPrefix) break;
+            --j;
         }
+        atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescPrefix, excl + real));
+    }
+    gbase[d] = (uint32_t)(dbase + (int64_t)excl);
+    __syncthreads();
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
-            const int leader = __ffs(peers) - 1;
-            uint32_t base = 0;
-            if (lane == leader) {
-                base = wh[dg[j]];
-                wh[dg[j]] = base + (uint32_t)__popc(peers);
-            }
-            base = __shfl_sync(0xffffffffu, base, leader);
-            rk[j] = base + (uint32_t)__popc(peers & lt_mask);
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int d = threadIdx.x; d < kBins; d += kBlock) {
-            uint32_t s = 0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const uint32_t c = whist[w * kBins + d];
-                whist[w * kBins + d] = s;
-                s += c;
-            }
-            tcount[d] = s;
-        }
-        __syncthreads();
-        int64_t tot;
-        const int64_t ex = block_exclusive_sum<kBlock>((int64_t)tcount[threadIdx.x], scan_tmp, &tot);
-        tstart[threadIdx.x] = (uint32_t)ex;
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            const uint32_t pos = tstart[dg[j]] + wh[dg[j]] + rk[j];
-            skeys[pos] = k[j];
-            if (HasVals) svals[pos] = v[j];
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < valid; i += kBlock) {
-            const K kk = skeys[i];
-            const int d = digit_of(kk, shift, mask);
-            const uint32_t dst = running[d] + ((uint32_t)i - tstart[d]);
-            keys_out[dst] = kk;
-            if (HasVals) vals_out[dst] = svals[i];
-        }
-        __syncthreads();
-        for (int d = threadIdx.x; d < kBins; d += kBlock) {
-            uint32_t c = tcount[d];
-            if (d == kBins - 1) c -= (uint32_t)(TILE - valid);
-            running[d] += c;
-        }
-        __syncthreads();
+    for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t dd = dr[j] & 0xffu;
+        const uint32_t pos = tstart[dd] + wh[dd] + (dr[j] >> 8);
+        skeys[pos] = k[j];
+        if (HasVals) svals[pos] = v[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < valid; i += kBlock) {
+        const K kk = skeys[i];
+        const int dd = digit_of(kk, shift, mask);
+        const uint32_t dst = gbase[dd] + ((uint32_t)i - tstart[dd]);
+        keys_out[dst] = kk;
+        if (HasVals) vals_out[dst] = svals[i];
     }
 }
 
@@ -179,14 +209,32 @@ int sm_count() {
 }
 
 template <class K, bool HasVals>
-int downsweep_smem_bytes() {
+int pass_smem_bytes() {
     constexpr int TILE = kBlock * SortTraits<K>::kItems;
-    return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kWarps * kBins + 3 * kBins) * 4;
+    return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kWarps * kBins + 2 * kBins) * 4;
+}
+
+template <class K, bool HasVals>
+int set_pass_attributes() {
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!done[dev]) {
+        GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     pass_smem_bytes<K, HasVals>()));
+        GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
+        GS_CUDA(cudaFuncSetAttribute(onesweep_histogram<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWarps * kMaxPasses * kBins * 4));
+        done[dev] = true;
+    }
+    return GSMAT_OK;
 }
 
 template <class K>
 int radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
-                    const char *timer_name) {
+                    const char *timer_name, int *err_word) {
     if (n < 0) return set_error(GSMAT_ERR_INVALID_ARG, "radix sort: negative n");
     if (begin_bit < 0 || end_bit > (int)(8 * sizeof(K)) || begin_bit > end_bit) {
         return set_error(GSMAT_ERR_INVALID_ARG, "radix sort: bad bit range [%d,%d)", begin_bit, end_bit);
@@ -195,43 +243,48 @@ int radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_b
     if (n > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "radix sort: n = %lld >= 2^32", (long long)n);
     constexpr int TILE = kBlock * SortTraits<K>::kItems;
     const int64_t ntiles = (n + TILE - 1) / TILE;
-    int64_t ctas = (int64_t)sm_count() * 4;
-    if (ctas > ntiles) ctas = ntiles;
-    const int64_t tiles_per_cta = (ntiles + ctas - 1) / ctas;
-    const int64_t span = tiles_per_cta * TILE;
-    const int num_ctas = (int)((n + span - 1) / span);
+    const int n_pass = (end_bit - begin_bit + 7) / 8;
+    const int attr_rc = vals ? set_pass_attributes<K, true>() : set_pass_attributes<K, false>();
+    if (attr_rc != GSMAT_OK) return attr_rc;
 
-    DevBuf alt_k, alt_v, counts;
+    // scratch: digit histograms | tile counters | error word | descriptors
+    const size_t off_cnt = round_up(sizeof(uint32_t) * kBins * n_pass, 256);
+    const size_t off_err = off_cnt + sizeof(uint32_t) * kMaxPasses;
+    const size_t off_desc = round_up(off_err + sizeof(int), 256);
+    const size_t meta_bytes = off_desc + sizeof(unsigned long long) * kBins * (size_t)ntiles;
+    DevBuf alt_k, alt_v, meta;
     GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
     if (vals) GS_TRY(alt_v.alloc(sizeof(uint32_t) * (size_t)n, st));
-    GS_TRY(counts.alloc(sizeof(uint32_t) * (size_t)kBins * num_ctas, st));
+    GS_TRY(meta.alloc(meta_bytes, st));
+    GS_CUDA(cudaMemsetAsync(meta.p, 0, meta_bytes, st));
+    uint32_t *hist = meta.as<uint32_t>();
+    unsigned int *counters = reinterpret_cast<unsigned int *>(meta.as<char>() + off_cnt);
+    int *err = err_word ? err_word : reinterpret_cast<int *>(meta.as<char>() + off_err);
+    unsigned long long *desc = reinterpret_cast<unsigned long long *>(meta.as<char>() + off_desc);
 
-    const int smem = vals ? downsweep_smem_bytes<K, true>() : downsweep_smem_bytes<K, false>();
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[vals ? 1 : 0]) {
-        if (vals) {
-            GS_CUDA(cudaFuncSetAttribute(radix_downsweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        } else {
-            GS_CUDA(cudaFuncSetAttribute(radix_downsweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        }
-        attr_set[vals ? 1 : 0] = true;
+    KernelTimer t(timer_name, st, (double)n * (2.0 * sizeof(K) + (vals ? 8.0 : 0.0)) * n_pass, (double)n);
+    {
+        int64_t g = (n + kBlock * 16 - 1) / (kBlock * 16);
+        const int64_t cap = (int64_t)sm_count() * 2;
+        if (g > cap) g = cap;
+        if (g < 1) g = 1;
+        onesweep_histogram<K><<<(unsigned)g, kBlock, kWarps * n_pass * kBins * 4, st>>>(keys, n, begin_bit, end_bit,
+                                                                                        n_pass, hist);
+        GS_LAUNCH_CHECK();
     }
-
     K *src_k = keys, *dst_k = alt_k.as<K>();
     uint32_t *src_v = vals, *dst_v = alt_v.as<uint32_t>();
-    const int n_pass = (end_bit - begin_bit + 7) / 8;
-    KernelTimer t(timer_name, st, (double)n * (2.0 * sizeof(K) + (vals ? 8.0 : 0.0)) * n_pass, (double)n);
-    for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    for (int p = 0; p < n_pass; ++p) {
+        const int shift = begin_bit + 8 * p;
         const int width = end_bit - shift < 8 ? end_bit - shift : 8;
         const int mask = (1 << width) - 1;
-        radix_upsweep<K><<<num_ctas, kBlock, 0, st>>>(src_k, n, span, shift, mask, num_ctas, counts.as<uint32_t>());
-        GS_TRY(exclusive_scan_u32_inplace(counts.as<uint32_t>(), (int64_t)kBins * num_ctas, st));
         if (vals) {
-            radix_downsweep<K, true><<<num_ctas, kBlock, smem, st>>>(src_k, src_v, dst_k, dst_v, n, span, shift, mask,
-                                                                     num_ctas, counts.as<uint32_t>());
+            onesweep_pass<K, true><<<(unsigned)ntiles, kBlock, pass_smem_bytes<K, true>(), st>>>(
+                src_k, src_v, dst_k, dst_v, n, shift, mask, hist + p * kBins, desc, counters + p, (uint32_t)(p + 1), err);
         } else {
-            radix_downsweep<K, false><<<num_ctas, kBlock, smem, st>>>(src_k, nullptr, dst_k, nullptr, n, span, shift,
-                                                                      mask, num_ctas, counts.as<uint32_t>());
+            onesweep_pass<K, false><<<(unsigned)ntiles, kBlock, pass_smem_bytes<K, false>(), st>>>(
+                src_k, nullptr, dst_k, nullptr, n, shift, mask, hist + p * kBins, desc, counters + p, (uint32_t)(p + 1),
+                err);
         }
         GS_LAUNCH_CHECK();
         K *tk = src_k; src_k = dst_k; dst_k = tk;
@@ -247,12 +300,14 @@ int radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_b
 
 }  // namespace
 
-int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st) {
-    return radix_sort_impl<uint64_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u64");
+int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
+                   int *err_word) {
+    return radix_sort_impl<uint64_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u64", err_word);
 }
 
-int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st) {
-    return radix_sort_impl<uint32_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u32");
+int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
+                   int *err_word) {
+    return radix_sort_impl<uint32_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u32", err_word);
 }
 
 int device_sm_count() { return sm_count(); }

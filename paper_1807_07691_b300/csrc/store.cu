@@ -191,7 +191,7 @@ __global__ void dense_fill_kernel(const int32_t *__restrict__ rowid, const int32
 
 // Sort rows (c, a, b) lexicographically; results into oa/ob/oc.
 int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, int id_bits, int slot_bits,
-               int32_t *oa, int32_t *ob, int32_t *oc, cudaStream_t st) {
+               int32_t *oa, int32_t *ob, int32_t *oc, cudaStream_t st, int *err) {
     if (n == 0) return GSMAT_OK;
     const unsigned g = grid_for(n);
     if (slot_bits + 2 * id_bits <= 64) {
@@ -199,7 +199,7 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
         GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, st));
         pack_kernel<<<g, kThreads, 0, st>>>(a, b, c, n, id_bits, keys.as<uint64_t>());
         GS_LAUNCH_CHECK();
-        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, 0, slot_bits + 2 * id_bits, st));
+        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, 0, slot_bits + 2 * id_bits, st, err));
         unpack_kernel<<<g, kThreads, 0, st>>>(keys.as<uint64_t>(), n, id_bits, oa, ob, oc);
         GS_LAUNCH_CHECK();
         return GSMAT_OK;
@@ -211,10 +211,10 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
     iota_kernel<<<g, kThreads, 0, st>>>(perm.as<uint32_t>(), n);
     gather_key_kernel<<<g, kThreads, 0, st>>>(nullptr, b, 0, nullptr, n, keys.as<uint64_t>());
     GS_LAUNCH_CHECK();
-    GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, id_bits, st));
+    GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, id_bits, st, err));
     gather_key_kernel<<<g, kThreads, 0, st>>>(c, a, id_bits, perm.as<uint32_t>(), n, keys.as<uint64_t>());
     GS_LAUNCH_CHECK();
-    GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, slot_bits + id_bits, st));
+    GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, slot_bits + id_bits, st, err));
     gather3_kernel<<<g, kThreads, 0, st>>>(a, b, c, perm.as<uint32_t>(), n, oa, ob, oc);
     GS_LAUNCH_CHECK();
     return GSMAT_OK;
@@ -338,7 +338,7 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
         GS_TRY(cnt.alloc(sizeof(int64_t), st));
         extract_pred_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, pcol.as<uint32_t>());
         GS_LAUNCH_CHECK();
-        GS_TRY(radix_sort_u32(pcol.as<uint32_t>(), nullptr, n, 0, bits_for((uint64_t)S->max_pred), st));
+        GS_TRY(radix_sort_u32(pcol.as<uint32_t>(), nullptr, n, 0, bits_for((uint64_t)S->max_pred), st, err.as<int>()));
         DistinctU32Op op{pcol.as<uint32_t>(), pdist.as<int32_t>()};
         GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err.as<int>()));
         GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -386,7 +386,7 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     GS_TRY(o_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(slot_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(sort_rows3(s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>(), n, id_bits, slot_bits,
-                      s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(), st));
+                      s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(), st, err.as<int>()));
     // dedupe into the raw buffers (reused)
     GS_TRY(cnt.alloc(sizeof(int64_t), st));
     {
@@ -413,7 +413,7 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)nu, st));
     GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)nu, st));
     GS_TRY(sort_rows3(val0.as<int32_t>(), key0.as<int32_t>(), slot0.as<int32_t>(), nu, id_bits, slot_bits,
-                      key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st));
+                      key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st, err.as<int>()));
     s_sorted.release(); o_sorted.release(); slot_sorted.release();
     // 5. rows, predicate bounds, dense row pointers
     GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err.as<int>(), st));

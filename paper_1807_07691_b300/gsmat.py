@@ -65,6 +65,22 @@ class QueryStats(ctypes.Structure):
                 ("result_rows", ctypes.c_int64)]
 
 
+class BGPStruct(ctypes.Structure):
+    _fields_ = [("pats", ctypes.c_void_p), ("n_pats", ctypes.c_int32), ("n_vars", ctypes.c_int32)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
+                ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int32), ("n_in_kernel", ctypes.c_int32), ("n_reordered", ctypes.c_int32),
+                ("n_fallback", ctypes.c_int32), ("kernel_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
+                ("arena_used", ctypes.c_int64),
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32)]
+
+
 class KernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
                 ("algo_bytes", ctypes.c_double), ("items", ctypes.c_double)]
@@ -95,6 +111,14 @@ def _load():
         "gsmat_table_stats": ([vp, P(QueryStats)], c_int),
         "gsmat_table_free": ([vp], None),
         "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
+        "gsmat_batch_prepare": ([vp, vp, i32, vp, vp, P(vp)], c_int),
+        "gsmat_batch_execute": ([vp, vp], c_int),
+        "gsmat_batch_result": ([vp, i32, P(i64), P(i32), P(i32)], c_int),
+        "gsmat_batch_column": ([vp, i32, i32, P(vp)], c_int),
+        "gsmat_batch_copy": ([vp, i32, vp, c_int, vp], c_int),
+        "gsmat_batch_stats": ([vp, vp], c_int),
+        "gsmat_batch_free": ([vp], None),
+        "gsmat_batch_autotune": ([vp, vp, i32, vp, vp, vp], c_int),
         "gsmat_radix_sort_u64": ([vp, vp, i64, c_int, c_int, vp], c_int),
         "gsmat_exclusive_scan_i32": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc": ([vp, vp, i64, vp], c_int),
@@ -331,6 +355,95 @@ class Store:
 
 
 # ----------------------------------------------------------------------------
+
+
+def _config(cfg):
+    if cfg is None:
+        return None
+    c = BatchConfig()
+    c.block = int(cfg.get("block", 0))
+    c.ctas_per_sm = int(cfg.get("ctas_per_sm", 0))
+    c.arena_bytes = int(cfg.get("arena_bytes", 0))
+    c.max_rows = int(cfg.get("max_rows", 0))
+    c.use_graph = int(cfg.get("use_graph", 1))
+    return c
+
+
+def _bgp_array(bgps, n_vars_list=None):
+    """(BGPStruct array, keep-alive list) from BGP-like objects."""
+    keep = []
+    arr = (BGPStruct * len(bgps))()
+    for i, q in enumerate(bgps):
+        pats, n, nv = _patterns(q)
+        if n_vars_list is not None:
+            nv = n_vars_list[i]
+        if nv is None:
+            raise ValueError("n_vars is required")
+        keep.append(pats)
+        arr[i] = BGPStruct(ctypes.cast(pats, ctypes.c_void_p), n, int(nv))
+    return arr, keep
+
+
+class Batch:
+    """A prepared batch of BGPs run by the persistent kernel (gsmat_batch_*)."""
+
+    def __init__(self, store: "Store", bgps, config: dict | None = None, stream=None, n_vars_list=None):
+        self._arr, self._keep = _bgp_array(bgps, n_vars_list)
+        self.n = len(bgps)
+        self._store = store  # the store must outlive the batch
+        cfg = _config(config)
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_batch_prepare(store.handle, self._arr, self.n, ctypes.byref(cfg) if cfg else None,
+                                        _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.gsmat_batch_free(h)
+        self._h = None
+
+    def execute(self, stream=None):
+        _check(_lib.gsmat_batch_execute(self._h, _stream_ptr(stream)))
+        return self
+
+    def result(self, i: int):
+        rows, cols, path = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.gsmat_batch_result(self._h, i, ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(path)))
+        return int(rows.value), int(cols.value), int(path.value)
+
+    def to_numpy(self, i: int, stream=None) -> np.ndarray:
+        rows, cols, _ = self.result(i)
+        out = np.empty((rows, cols), dtype=np.int32)
+        if rows and cols:
+            _check(_lib.gsmat_batch_copy(self._h, i, out.ctypes.data, 0, _stream_ptr(stream)))
+        return out
+
+    def copy_to(self, i: int, dst, stream=None):
+        rows, cols, _ = self.result(i)
+        if rows and cols:
+            on_dev = 1 if getattr(dst, "is_cuda", False) else 0
+            ptr = dst.data_ptr() if hasattr(dst, "data_ptr") else dst.ctypes.data
+            _check(_lib.gsmat_batch_copy(self._h, i, ctypes.c_void_p(ptr), on_dev, _stream_ptr(stream)))
+        return dst
+
+    def stats(self) -> dict:
+        s = BatchStats()
+        _check(_lib.gsmat_batch_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in BatchStats._fields_}
+
+
+def batch_autotune(store: "Store", bgps, base: dict | None = None, stream=None) -> dict:
+    arr, keep = _bgp_array(bgps)
+    best = BatchConfig()
+    cfg = _config(base)
+    _check(_lib.gsmat_batch_autotune(store.handle, arr, len(bgps), ctypes.byref(cfg) if cfg else None,
+                                     _stream_ptr(stream), ctypes.byref(best)))
+    return {"block": best.block, "ctas_per_sm": best.ctas_per_sm, "arena_bytes": best.arena_bytes,
+            "max_rows": best.max_rows, "use_graph": best.use_graph}
 
 
 def plan(bgp, keys, stats, n_vars=None):

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import dataclasses
 import itertools
+import os
 
 import numpy as np
 
@@ -262,10 +263,10 @@ class _BoundIndex:
             p = int(t[seg[0], 1])
             s = t[seg, 0].astype(np.int64)
             o = t[seg, 2].astype(np.int64)
-            m = sp.csr_matrix((np.ones(seg.size), (s, o)), shape=(self.E, self.E))
+            m = sp.csr_matrix((np.ones(seg.size, dtype=np.float32), (s, o)), shape=(self.E, self.E))
             self.mats[p] = m
-            self.outdeg[p] = np.bincount(s, minlength=self.E).astype(np.float64)
-            self.indeg[p] = np.bincount(o, minlength=self.E).astype(np.float64)
+            self.outdeg[p] = np.bincount(s, minlength=self.E).astype(np.float32)
+            self.indeg[p] = np.bincount(o, minlength=self.E).astype(np.float32)
         self._mt = {}
 
     def mat_t(self, p):
@@ -274,11 +275,18 @@ class _BoundIndex:
         return self._mt[p]
 
 
-def _component_bound(bi: _BoundIndex, pats, var_set):
+def _component_bound(bi: _BoundIndex, pats, var_set, ids=None, memo=None):
     """Upper bound on the rows of the sub-BGP ``pats`` (all vars in var_set
-    connected through pats)."""
+    connected through pats).  ``ids`` (positions of pats in their query) and
+    ``memo`` let messages of identical subtrees be reused across the
+    sub-BGPs of one query."""
     E = bi.E
+    if ids is None:
+        ids = list(range(len(pats)))
+    if memo is None:
+        memo = {}
     unary = {}
+    unary_ids = {v: [] for v in var_set}
     adj = {v: [] for v in var_set}
     parent = {v: v for v in var_set}
 
@@ -288,52 +296,90 @@ def _component_bound(bi: _BoundIndex, pats, var_set):
             v = parent[v]
         return v
 
-    def mul_unary(v, vec):
-        unary[v] = vec if v not in unary else unary[v] * vec
+    def unary_vec(pid, kind, p, c):
+        key = ("u", pid)
+        if key not in memo:
+            m = bi.mats[p]
+            vec = np.zeros(E, dtype=np.float32)
+            if kind == "diag":
+                vec = m.diagonal().astype(np.float32)
+            elif kind == "col":
+                if 0 <= c < E:
+                    mt = bi.mat_t(p)
+                    vec[mt.indices[mt.indptr[c]:mt.indptr[c + 1]]] = 1.0
+            else:
+                if 0 <= c < E:
+                    vec[m.indices[m.indptr[c]:m.indptr[c + 1]]] = 1.0
+            memo[key] = vec
+        return memo[key]
 
-    for (s, p, o, sv, ov) in pats:
+    def mul_unary(v, vec, pid):
+        unary[v] = vec if v not in unary else unary[v] * vec
+        unary_ids[v].append(pid)
+
+    for pid, (s, p, o, sv, ov) in zip(ids, pats):
         if p not in bi.mats:
             return 0.0
-        m = bi.mats[p]
         if sv and ov:
             if s == o:
-                mul_unary(s, m.diagonal().astype(np.float64))
+                mul_unary(s, unary_vec(pid, "diag", p, 0), pid)
             else:
                 rs, ro = find(s), find(o)
                 if rs != ro:
                     parent[rs] = ro
-                    adj[s].append((o, p, "out"))  # s -p-> o
-                    adj[o].append((s, p, "in"))
+                    adj[s].append((o, p, "out", pid))  # s -p-> o
+                    adj[o].append((s, p, "in", pid))
                 # else: a cycle edge; dropping it keeps an upper bound
         elif sv:
-            col = np.zeros(E)
-            if 0 <= o < E:
-                mt = bi.mat_t(p)
-                col[mt.indices[mt.indptr[o]:mt.indptr[o + 1]]] = 1.0
-            mul_unary(s, col)
+            mul_unary(s, unary_vec(pid, "col", p, o), pid)
         elif ov:
-            row = np.zeros(E)
-            if 0 <= s < E:
-                row[m.indices[m.indptr[s]:m.indptr[s + 1]]] = 1.0
-            mul_unary(o, row)
-    # root: the variable with the most tree edges
+            mul_unary(o, unary_vec(pid, "row", p, s), pid)
     root = max(var_set, key=lambda v: len(adj[v]))
+
+    def subtree_ids(v, par):
+        out = list(unary_ids[v])
+        for (c, p, d, pid) in adj[v]:
+            if c != par:
+                out.append(pid)
+                out.extend(subtree_ids(c, v))
+        return out
 
     def f(v, par):
         vec = unary.get(v)
-        for (c, p, d) in adj[v]:
+        for (c, p, d, pid) in adj[v]:
             if c == par:
                 continue
-            fc = f(c, v)
-            if fc is None:
-                msg = bi.outdeg[p] if d == "out" else bi.indeg[p]
+            key = ("m", pid, d, frozenset(subtree_ids(c, v)))
+            if key in memo:
+                msg = memo[key]
             else:
-                msg = (bi.mats[p] @ fc) if d == "out" else (bi.mat_t(p) @ fc)
+                fc = f(c, v)
+                if fc is None:
+                    msg = bi.outdeg[p] if d == "out" else bi.indeg[p]
+                else:
+                    msg = (bi.mats[p] @ fc) if d == "out" else (bi.mat_t(p) @ fc)
+                memo[key] = msg
             vec = msg if vec is None else vec * msg
         return vec
 
     top = f(root, None)
-    return float(E) if top is None else float(top.sum())
+    return float(E) if top is None else float(top.sum(dtype=np.float64))
+
+
+def _single_bound(bi: _BoundIndex, pt) -> float:
+    """Rows of one pattern alone: nnz, a constant's row size, or (?x p ?x)
+    the diagonal count."""
+    s, p, o, sv, ov = pt
+    if p not in bi.mats:
+        return 0.0
+    m = bi.mats[p]
+    if sv and ov:
+        return float(m.diagonal().sum()) if s == o else float(m.nnz)
+    if sv:
+        return float(bi.indeg[p][o]) if 0 <= o < bi.E else 0.0
+    if ov:
+        return float(bi.outdeg[p][s]) if 0 <= s < bi.E else 0.0
+    return 1.0
 
 
 def _pattern_vars(pt):
@@ -384,6 +430,7 @@ def bgp_row_bound(bi: _BoundIndex, bgp: BGP, limit: float = float("inf")) -> flo
     comps = _components(bgp.patterns)
     full = []
     sub_max = []
+    memo = {}
     for idx, vars_ in comps:
         pats = [bgp.patterns[i] for i in idx]
         best = 0.0
@@ -396,8 +443,10 @@ def bgp_row_bound(bi: _BoundIndex, bgp: BGP, limit: float = float("inf")) -> flo
                 vs = set().union(*[_pattern_vars(x) for x in sp_])
                 if not vs:
                     b = 1.0
+                elif len(sp_) == 1:
+                    b = _single_bound(bi, sp_[0])
                 else:
-                    b = _component_bound(bi, sp_, vs)
+                    b = _component_bound(bi, sp_, vs, [idx[i] for i in sub], memo)
                 if b > limit:
                     return b
                 best = max(best, b)
@@ -447,14 +496,16 @@ _SHAPES = {
 }
 
 
-def _draw(adj, bi, rng, shape, n_pat, p_const, limit, max_tries=400):
+def _draw(adj, bi, rng, shape, n_pat, p_const, limit, max_tries=400, force_after=None):
     last = None
+    if force_after is None:
+        force_after = max_tries // 4
     for attempt in range(max_tries):
         edges, vals = _SHAPES[shape](adj, rng, n_pat)
         n_slots = len(vals)
         # later attempts force a constant: unselective draws are the ones
         # rejected by the bound
-        use_const = rng.random() < p_const or attempt >= max_tries // 4
+        use_const = rng.random() < p_const or attempt >= force_after
         const_slot = int(rng.integers(n_slots)) if use_const else None
         bgp = _to_bgp(adj, edges, vals, const_slot, shape)
         if bgp.n_vars == 0:
@@ -524,27 +575,69 @@ def make_queries(cfg: GraphConfig | str, triples: np.ndarray | None = None, seed
     return out
 
 
-def make_batched_queries(n_queries: int = 4096, triples: np.ndarray | None = None, seed: int = 7691 + 3,
-                         limit: int = 1_000_000):
-    """Mixed workload over the medium graph: 2-8 patterns, shapes
-    star:chain:snowflake:cycle = 4:3:2:1, a mix of constant and
-    constant-free queries."""
+_BATCH_SHAPES = ["star"] * 4 + ["chain"] * 3 + ["snowflake"] * 2 + ["cycle"]
+
+
+def _batched_one(adj, bi, seed, qi, limit):
+    """Query qi of the batched mix; its own generator (seed, qi) makes the
+    mix independent of how the queries are split over processes."""
+    rng = np.random.Generator(np.random.PCG64([seed, qi]))
+    shape = _BATCH_SHAPES[int(rng.integers(len(_BATCH_SHAPES)))]
+    if shape == "cycle":
+        n_pat = int(rng.integers(3, 5))
+    elif shape == "snowflake":
+        n_pat = int(rng.integers(3, 9))
+    else:
+        n_pat = int(rng.integers(2, 9))
+    while True:
+        try:
+            bgp = _draw(adj, bi, rng, shape, n_pat, 0.5, limit, max_tries=12, force_after=3)
+            break
+        except RuntimeError:
+            # no instance of this size within the limit: one pattern fewer
+            n_pat -= 1
+            if n_pat < (3 if shape == "cycle" else 2):
+                shape, n_pat = "star", 2
+    bgp.name = f"batched-q{qi:04d}-{shape}{n_pat}"
+    return bgp
+
+
+_WORKER = {}
+
+
+def _batched_worker_init(limit):
     cfg = CONFIGS["medium"]
-    if triples is None:
-        triples = make_graph(cfg)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    adj, bi = _indexes(cfg, triples)
-    shapes = ["star"] * 4 + ["chain"] * 3 + ["snowflake"] * 2 + ["cycle"]
-    out = []
-    for qi in range(n_queries):
-        shape = shapes[int(rng.integers(len(shapes)))]
-        if shape == "cycle":
-            n_pat = int(rng.integers(3, 5))
-        elif shape == "snowflake":
-            n_pat = int(rng.integers(3, 9))
-        else:
-            n_pat = int(rng.integers(2, 9))
-        bgp = _draw(adj, bi, rng, shape, n_pat, 0.5, limit)
-        bgp.name = f"batched-q{qi:04d}-{shape}{n_pat}"
-        out.append(bgp)
-    return out
+    t = make_graph(cfg)
+    _WORKER["idx"] = _indexes(cfg, t)
+    _WORKER["limit"] = limit
+
+
+def _batched_worker(args):
+    seed, lo, hi = args
+    adj, bi = _WORKER["idx"]
+    return [_batched_one(adj, bi, seed, qi, _WORKER["limit"]) for qi in range(lo, hi)]
+
+
+def make_batched_queries(n_queries: int = 4096, triples: np.ndarray | None = None, seed: int = 7691 + 3,
+                         limit: int = 1_000_000, workers: int | None = None):
+    """Mixed workload over the medium graph: 2-8 patterns, shapes
+    star:chain:snowflake:cycle = 4:3:2:1, 0-1 constants (constant-free
+    patterns over this graph's hubs almost never stay within the limit).
+    Each query has its own seeded generator, so the mix does not depend on
+    ``workers`` (spawned processes that rebuild the medium graph)."""
+    cfg = CONFIGS["medium"]
+    if workers is None:
+        workers = min(8, os.cpu_count() or 1) if n_queries >= 512 else 1
+    if workers <= 1:
+        if triples is None:
+            triples = make_graph(cfg)
+        adj, bi = _indexes(cfg, triples)
+        return [_batched_one(adj, bi, seed, qi, limit) for qi in range(n_queries)]
+    import multiprocessing as mp
+
+    chunk = (n_queries + workers * 4 - 1) // (workers * 4)
+    jobs = [(seed, lo, min(n_queries, lo + chunk)) for lo in range(0, n_queries, chunk)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(workers, initializer=_batched_worker_init, initargs=(limit,)) as pool:
+        parts = pool.map(_batched_worker, jobs)
+    return [q for part in parts for q in part]

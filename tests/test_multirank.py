@@ -1,0 +1,59 @@
+"""The benchmark's multi-rank path (replicas, max-over-ranks timing) with
+world_size 2 on the gloo backend (CPU only)."""
+
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import sys
+
+    import torch.distributed as dist
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    # rank 1 is the slow one; rows add up
+    ms, rows = bench.reduce_over_ranks(100.0 + 50.0 * rank, 1000 + rank)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, ms, rows, bench.job_value(world, 3, 40, ms)))
+
+
+def test_two_rank_reduction_gloo():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, rows, value in res:
+        assert ms == 150.0  # the slowest rank's time
+        assert rows == 2001
+        assert value == pytest.approx(2 * 3 * 40 / 0.150)
+
+
+def test_single_process_is_identity():
+    import bench
+
+    assert bench.reduce_over_ranks(12.5, 7) == (12.5, 7)
+    assert bench.job_value(1, 5, 40, 100.0) == pytest.approx(2000.0)
