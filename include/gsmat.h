@@ -158,6 +158,8 @@ typedef struct {
 #define GSMAT_PLAN_ORDER 1u   /* columns in the order the plan binds variables, rows ascending
                                  in that column order (no final sort) */
 #define GSMAT_COUNT_ONLY 2u   /* compute the row count only; the table has no columns */
+#define GSMAT_NO_INTERSECT 4u /* join strictly one pattern per step (Alg. 2 as printed): no
+                                 fusion of an expand with a later filter into an intersection */
 
 /* Evaluate a BGP.
  *  pats, n_pats   host array of 1 <= n_pats <= 64 patterns.
@@ -204,6 +206,9 @@ typedef struct {
 #define GSMAT_STEP_EXPAND_S 1 /* subject end known, object new: expand along CSR rows */
 #define GSMAT_STEP_EXPAND_O 2 /* object end known, subject new: expand along CSC rows */
 #define GSMAT_STEP_FILTER 3   /* both ends known: membership filter + compaction */
+#define GSMAT_STEP_INTERSECT 4 /* (query stats only) an expand fused with a later filter on the
+                                  new variable: the new column is the intersection of two rows */
+#define GSMAT_STEP_FUSED 5     /* (query stats only) a filter executed inside an earlier INTERSECT */
 
 GSMAT_API int gsmat_table_stats(const gsmat_table *table, gsmat_query_stats *stats);
 

@@ -174,6 +174,83 @@ struct FilterOp {
 };
 
 // ---------------------------------------------------------------------------
+// intersect-expand: a new variable bound by two patterns at once.  Row i's
+// candidates are the intersection of two sorted entry lists (the row of
+// a_i in one predicate side and the row of b_i in another); one warp per
+// input row walks the shorter list in chunks of 32, each lane binary
+// searches its element in the part of the longer list not yet passed,
+// and ballot / popc give every match its output position.  Matches come
+// out ascending, the order an expand followed by a filter produces.
+
+struct IsectSrc {
+    SideView sa, sb;
+    PredSide pa, pb;
+    ValueSrc a, b;
+};
+
+// Count (out == nullptr) or write the intersection of row i; returns the
+// count (in every lane).  k parent columns are copied for each match.
+__device__ __forceinline__ int warp_intersect_row(const IsectSrc &s, int64_t i, int64_t out_base, const Cols &in,
+                                                  int k, OutCols *out) {
+    const int lane = threadIdx.x & 31;
+    const int2 ra = row_range(s.sa, s.pa, s.a.at(i));
+    const int2 rb = row_range(s.sb, s.pb, s.b.at(i));
+    const int la = ra.y - ra.x, lb = rb.y - rb.x;
+    if (la <= 0 || lb <= 0) return 0;
+    const int32_t *S = la <= lb ? s.sa.val + ra.x : s.sb.val + rb.x;
+    const int32_t *L = la <= lb ? s.sb.val + rb.x : s.sa.val + ra.x;
+    const int ls = la <= lb ? la : lb, ll = la <= lb ? lb : la;
+    int count = 0;
+    int lo_all = 0;  // no element of L before this position can match any later element of S
+    for (int base = 0; base < ls; base += 32) {
+        const int idx = base + lane;
+        int32_t v = 0;
+        bool found = false;
+        int pos = ll;
+        if (idx < ls) {
+            v = __ldg(S + idx);
+            int lo = lo_all, hi = ll;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(L + mid) < v) lo = mid + 1; else hi = mid;
+            }
+            pos = lo;
+            found = lo < ll && __ldg(L + lo) == v;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, found);
+        if (out && found) {
+            const int64_t j = out_base + count + __popc(m & ((1u << lane) - 1u));
+            for (int c = 0; c < k; ++c) out->c[c][j] = __ldg(in.c[c] + i);
+            out->c[k][j] = v;
+        }
+        count += __popc(m);
+        // the chunk's last element bounds the next chunk's searches from below
+        const int last = min(31, ls - 1 - base);
+        lo_all = __shfl_sync(0xffffffffu, pos, last);
+        if (lo_all >= ll) break;
+    }
+    return count;
+}
+
+__global__ void __launch_bounds__(256) isect_count_kernel(IsectSrc s, int64_t n, int32_t *__restrict__ counts) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        Cols none;
+        const int c = warp_intersect_row(s, i, 0, none, 0, nullptr);
+        if ((threadIdx.x & 31) == 0) counts[i] = c;
+    }
+}
+
+__global__ void __launch_bounds__(256) isect_write_kernel(IsectSrc s, int64_t n, const int64_t *__restrict__ off,
+                                                          Cols in, int k, OutCols out) {
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        if (__ldg(off + i + 1) == __ldg(off + i)) continue;  // warp-uniform
+        warp_intersect_row(s, i, __ldg(off + i), in, k, &out);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Cartesian product
 
 __global__ void __launch_bounds__(256) cross_kernel(Cols in, int k, Cols rel, int rc, uint32_t m, uint64_t total,
@@ -329,6 +406,30 @@ int launch_filter(const StoreView &sv, const PredSide &ps_s, const PredSide &ps_
     // the input size: an upper bound)
     KernelTimer t("filter", st, (double)n_in * (8.0 + 8.0 + 32.0 + 8.0 * k), (double)n_in);
     GS_TRY(run_select(op, n_in, d_count, st, err));
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_isect_count(const StoreView &sv, int side_a, const PredSide &pa, ValueSrc a, int side_b, const PredSide &pb,
+                       ValueSrc b, int64_t n, int32_t *counts, cudaStream_t st) {
+    if (n <= 0) return GSMAT_OK;
+    IsectSrc s{sv.side[side_a], sv.side[side_b], pa, pb, a, b};
+    KernelTimer t("isect_count", st, (double)n * (8.0 + 16.0 + 4.0), (double)n);
+    isect_count_kernel<<<grid_1d(n, 8), 256, 0, st>>>(s, n, counts);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_isect_write(const StoreView &sv, int side_a, const PredSide &pa, ValueSrc a, int side_b, const PredSide &pb,
+                       ValueSrc b, int64_t n, const int64_t *off, const Cols &in, int k, int64_t total, OutCols out,
+                       cudaStream_t st) {
+    if (n <= 0 || total <= 0) return GSMAT_OK;
+    IsectSrc s{sv.side[side_a], sv.side[side_b], pa, pb, a, b};
+    KernelTimer t("isect_write", st, (double)n * (8.0 + 16.0 + 8.0 + 4.0 * k) + (double)total * 4.0 * (k + 1),
+                  (double)total);
+    isect_write_kernel<<<grid_1d(n, 8), 256, 0, st>>>(s, n, off, in, k, out);
+    GS_LAUNCH_CHECK();
     t.stop();
     return GSMAT_OK;
 }

@@ -40,6 +40,16 @@ int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t 
 int launch_filter(const StoreView &sv, const PredSide &ps_s, const PredSide &ps_o, ValueSrc s, ValueSrc o,
                   const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st);
 
+// Intersect-expand, count phase: counts[i] = |row(a_i) of predicate side
+// (side_a, pa)  intersected with  row(b_i) of (side_b, pb)|.
+int launch_isect_count(const StoreView &sv, int side_a, const PredSide &pa, ValueSrc a, int side_b, const PredSide &pb,
+                       ValueSrc b, int64_t n, int32_t *counts, cudaStream_t st);
+// Write phase: input row i's matches go to rows [off[i], off[i+1]) with the
+// k input columns copied and the match appended as column k.
+int launch_isect_write(const StoreView &sv, int side_a, const PredSide &pa, ValueSrc a, int side_b, const PredSide &pb,
+                       ValueSrc b, int64_t n, const int64_t *off, const Cols &in, int k, int64_t total, OutCols out,
+                       cudaStream_t st);
+
 // Cartesian product: output row j = (input row j / m, relation row j % m);
 // the relation has r_cols (1 or 2) columns of length m.
 int launch_cross(const Cols &in, int k, int64_t n_in, const Cols &rel, int r_cols, int64_t m, OutCols out,

@@ -153,7 +153,9 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
 int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
         gsmat_table *T) {
     GS_TRY(validate_bgp(pats, n_pats, n_vars));
-    if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY)) return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY | GSMAT_NO_INTERSECT)) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    }
     Ctx cx;
     cx.S = S;
     cx.st = st;
@@ -237,6 +239,40 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         }
     }
 
+    // Intersect-expand fusion: an EXPAND of a new variable v from a bound
+    // variable, and a later FILTER whose pattern joins v with a variable
+    // bound before the EXPAND (or a constant), run as one step whose new
+    // column is the intersection of the two rows.  Applying the filter
+    // early changes neither the rows nor their order.
+    std::vector<int> partner(n_pats, -1);
+    std::vector<char> fused(n_pats, 0);
+    if (!(flags & GSMAT_NO_INTERSECT)) {
+        uint64_t bound = 0;
+        for (int s = 0; s < n_pats; ++s) {
+            const gsmat_pattern &p = pats[qs.order[s]];
+            const int kind = qs.kind[s];
+            const bool from_var = (kind == GSMAT_STEP_EXPAND_S && p.s_var) || (kind == GSMAT_STEP_EXPAND_O && p.o_var);
+            if (from_var && !fused[s]) {
+                const int32_t v = kind == GSMAT_STEP_EXPAND_S ? p.o : p.s;
+                for (int t = s + 1; t < n_pats; ++t) {
+                    if (qs.kind[t] != GSMAT_STEP_FILTER || fused[t]) continue;
+                    const gsmat_pattern &f = pats[qs.order[t]];
+                    if (f.s_var && f.o_var && f.s == f.o) continue;
+                    const bool v_is_s = f.s_var && f.s == v;
+                    const bool v_is_o = f.o_var && f.o == v;
+                    if (v_is_s == v_is_o) continue;
+                    const bool other_known = v_is_s ? (!f.o_var || ((bound >> f.o) & 1)) : (!f.s_var || ((bound >> f.s) & 1));
+                    if (!other_known) continue;
+                    partner[s] = t;
+                    fused[t] = 1;
+                    break;
+                }
+            }
+            if (p.s_var) bound |= uint64_t(1) << p.s;
+            if (p.o_var) bound |= uint64_t(1) << p.o;
+        }
+    }
+
     Tbl cur;
     cur.rows = absent ? 0 : 1;  // one empty assignment
     cur.ncols = 0;
@@ -249,6 +285,57 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         const bool last = step == n_pats - 1;
         const bool unit = cur.rows == 1 && cur.ncols == 0;
         Tbl nxt;
+        if (fused[step]) {
+            // already applied by the intersect-expand of an earlier step
+            qs.kind[step] = GSMAT_STEP_FUSED;
+            qs.rows[step] = cur.rows;
+            continue;
+        }
+        if (partner[step] >= 0) {
+            const gsmat_pattern &f = pats[qs.order[partner[step]]];
+            const int fslot = slot[qs.order[partner[step]]];
+            const int side_a = kind == GSMAT_STEP_EXPAND_S ? 0 : 1;
+            const PredSide &pa = side_a == 0 ? ps0 : ps1;
+            const int32_t known = side_a == 0 ? p.s : p.o;
+            const int32_t newv = side_a == 0 ? p.o : p.s;
+            ValueSrc a{cur.col[cur.col_of(known)], 0};
+            // the filter's other end selects v's candidates: (v f b) -> the
+            // row of b by object lists subjects; (b f v) -> by subject
+            const bool v_is_s = f.s_var && f.s == newv;
+            const int side_b = v_is_s ? 1 : 0;
+            const bool b_var = v_is_s ? f.o_var : f.s_var;
+            const int32_t b_id = v_is_s ? f.o : f.s;
+            ValueSrc b{b_var ? cur.col[cur.col_of(b_id)] : nullptr, b_var ? 0 : b_id};
+            const PredSide &pb = S->side[side_b][fslot];
+            DevBuf cnt, off;
+            GS_TRY(cnt.alloc(sizeof(int32_t) * (size_t)cur.rows, st));
+            GS_TRY(off.alloc(sizeof(int64_t) * (size_t)(cur.rows + 1), st));
+            GS_TRY(launch_isect_count(S->view, side_a, pa, a, side_b, pb, b, cur.rows, cnt.as<int32_t>(), st));
+            GS_TRY(exclusive_scan_i32(cnt.as<int32_t>(), off.as<int64_t>(), cur.rows, st, cx.d_err()));
+            GS_CUDA(cudaMemcpyAsync(cx.d_count(), off.as<int64_t>() + cur.rows, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+            int64_t total;
+            GS_TRY(cx.read_count(&total));
+            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "step %d: %lld rows", step, (long long)total);
+            bool last_live = true;  // every later step runs inside this one
+            for (int t = step + 1; t < n_pats; ++t) {
+                if (!fused[t]) last_live = false;
+            }
+            if (count_only && last_live) {
+                nxt.rows = total;
+                nxt.ncols = cur.ncols + 1;
+            } else {
+                OutCols oc;
+                GS_TRY(alloc_cols(nxt, cur.ncols + 1, total, st, &oc));
+                GS_TRY(launch_isect_write(S->view, side_a, pa, a, side_b, pb, b, cur.rows, off.as<int64_t>(), cur.cols(),
+                                          cur.ncols, total, oc, st));
+            }
+            for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+            nxt.vars[cur.ncols] = newv;
+            qs.kind[step] = GSMAT_STEP_INTERSECT;
+            cur = std::move(nxt);
+            qs.rows[step] = cur.rows;
+            continue;
+        }
         if (kind == GSMAT_STEP_FILTER) {
             ValueSrc vs{p.s_var ? cur.col[cur.col_of(p.s)] : nullptr, p.s_var ? 0 : p.s};
             ValueSrc vo{p.o_var ? cur.col[cur.col_of(p.o)] : nullptr, p.o_var ? 0 : p.o};

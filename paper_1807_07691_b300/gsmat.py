@@ -28,6 +28,7 @@ ERR_DEVICE_CHECK = 6
 SORTED = 0
 PLAN_ORDER = 1
 COUNT_ONLY = 2
+NO_INTERSECT = 4
 
 STEP_CROSS, STEP_EXPAND_S, STEP_EXPAND_O, STEP_FILTER = 0, 1, 2, 3
 MAX_PATTERNS = 64

@@ -33,7 +33,12 @@ def test_dg_example(gs):
     assert T.to_numpy().tolist() == g["answer_xyzw"]
     st = T.stats()
     assert st["order"] == g["plan_order"]
-    assert st["rows"] == g["plan_step_rows"]
+    # one pattern per step (Alg. 2 as printed) gives the paper's intermediates
+    U = S.query(g["query"], 4, flags=gs.NO_INTERSECT)
+    assert U.stats()["rows"] == g["plan_step_rows"]
+    assert U.to_numpy().tolist() == g["answer_xyzw"]
+    # by default the third step's expand is fused with the fourth's filter
+    assert st["kind"][2:] == [4, 5] and st["rows"][2:] == [1, 1]
     # paper's column order (X, W, Z, Y) = plan order
     P = S.query(g["query"], 4, flags=gs.PLAN_ORDER)
     assert P.col_vars == [0, 3, 2, 1]
@@ -153,3 +158,47 @@ def test_torch_allocator_hook(gs, tiny):
         del S2
     finally:
         gs.use_torch_allocator(False)
+
+
+def _cyclic_bgps(t, rng, n):
+    """Triangles and 4-cycles over the graph's predicates, some anchored."""
+    preds = np.unique(t[:, 1])
+    ents = np.unique(t[:, [0, 2]])
+    out = []
+    for _ in range(n):
+        L = int(rng.integers(3, 5))
+        pats = []
+        for h in range(L):
+            a, b = h, (h + 1) % L
+            if rng.random() < 0.5:
+                a, b = b, a
+            pats.append((a, int(rng.choice(preds)), b, True, True))
+        if rng.random() < 0.4:  # anchor one variable
+            c = int(rng.choice(ents))
+            pats = [(c if (sv and s == 0) else s, p, c if (ov and o == 0) else o, sv and s != 0, ov and o != 0)
+                    for (s, p, o, sv, ov) in pats]
+            remap = {}
+            pats = [((remap.setdefault(s, len(remap)) if sv else s), p, (remap.setdefault(o, len(remap)) if ov else o),
+                     sv, ov) for (s, p, o, sv, ov) in pats]
+            out.append((pats, len(remap)))
+        else:
+            out.append((pats, L))
+    return out
+
+
+def test_cycles_use_intersect_expand(gs, tiny):
+    t, ix, S, qs = tiny
+    tri = [q for q in qs if q.shape == "cycle"][0]
+    T = S.query(tri)
+    assert np.array_equal(T.to_numpy(), ix.query(tri))
+    kinds = T.stats()["kind"]
+    assert 4 in kinds and 5 in kinds  # GSMAT_STEP_INTERSECT, GSMAT_STEP_FUSED
+    rng = np.random.default_rng(77)
+    n_isect = 0
+    for pats, V in _cyclic_bgps(t, rng, 40):
+        want = ix.query(pats, V, row_limit=20_000_000)
+        T = S.query(pats, V)
+        assert np.array_equal(T.to_numpy(), want), pats
+        assert S.query(pats, V, flags=gs.COUNT_ONLY).shape[0] == want.shape[0]
+        n_isect += 4 in T.stats()["kind"]
+    assert n_isect > 10
