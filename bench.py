@@ -247,7 +247,12 @@ def run_gsmat(args):
         if it > 0:
             e2e_ms.append(a.elapsed_time(b))
 
-    batched = None if args.no_batched else run_batched(args, gs, torch, d_tri, stream)
+    batched = None
+    served = None
+    if not args.no_batched:
+        batched, bq = run_batched(args, gs, torch, d_tri, stream)
+        if not args.no_served:
+            served = run_served(args, gs, torch, d_tri, stream, bq)
 
     if rank != 0:
         if ws > 1:
@@ -309,6 +314,8 @@ def run_gsmat(args):
     }
     if batched is not None:
         out["batched"] = batched
+    if served is not None:
+        out["served"] = served
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(triples, queries, budget_s=args.cpu_budget)
     if ws > 1:
@@ -385,6 +392,67 @@ def run_batched(args, gs, torch, d_tri, stream):
         "generation_s": round(gen_s, 1),
     }
     B.free()
+    S.free()
+    return out, bq
+
+
+def _spin_until(t):
+    while True:
+        d = t - time.perf_counter()
+        if d <= 0:
+            return
+        if d > 2e-4:
+            time.sleep(d - 1e-4)
+
+
+def run_served(args, gs, torch, d_tri, stream, bq):
+    """Open-loop Poisson arrivals drawn from the batched mix, served by
+    continuous batching (gsmat_server) and, for comparison, by the plain
+    path one query at a time (FIFO).  Latency = completion - arrival."""
+    S = gs.Store(d_tri, stream=stream)
+    marsh = [gs.Server.marshal(q) for q in bq]
+    rng = np.random.default_rng(7691 + 4)
+    out = {"workload": f"Poisson arrivals over {len(bq)} batched-mix BGPs (medium graph, resident store)",
+           "seconds_per_rate": args.served_seconds, "rates": []}
+    for rate in args.served_rates:
+        n = max(1, int(rate * args.served_seconds))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        pick = rng.integers(len(bq), size=n)
+        # continuous batching
+        srv = gs.Server(S, max_batch=args.served_max_batch, slots=args.served_slots)
+        t0 = time.perf_counter() + 0.02
+        tickets = np.empty(n, dtype=np.int64)
+        sub = np.empty(n)
+        for i in range(n):
+            _spin_until(t0 + arrivals[i])
+            sub[i] = time.perf_counter()
+            tickets[i] = srv.submit_raw(marsh[pick[i]])
+        lat = np.empty(n)
+        for i in range(n):
+            srv.wait(int(tickets[i]))
+            lat[i] = srv.result(int(tickets[i]))[2] / 1e3  # ms from submit
+        done = sub + lat / 1e3
+        lat_arr = (done - (t0 + arrivals)) * 1e3  # from the scheduled arrival
+        st = srv.stats()
+        srv.close()
+        served = {"p50_ms": round(float(np.percentile(lat_arr, 50)), 3),
+                  "p99_ms": round(float(np.percentile(lat_arr, 99)), 3),
+                  "queries_per_s": round(n / (done.max() - t0), 1),
+                  "batches": int(st["batches"]), "fallbacks": int(st["fallbacks"])}
+        # plain path, one query at a time
+        t0 = time.perf_counter() + 0.02
+        lat_p = np.empty(n)
+        last = t0
+        for i in range(n):
+            _spin_until(t0 + arrivals[i])
+            T = S.query(bq[pick[i]], stream=stream)
+            T.free()
+            last = time.perf_counter()
+            lat_p[i] = (last - (t0 + arrivals[i])) * 1e3
+        plain = {"p50_ms": round(float(np.percentile(lat_p, 50)), 3),
+                 "p99_ms": round(float(np.percentile(lat_p, 99)), 3),
+                 "queries_per_s": round(n / (last - t0), 1)}
+        out["rates"].append({"offered_qps": rate, "requests": n, "served": served, "plain": plain})
     S.free()
     return out
 
@@ -549,6 +617,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-n", type=int, default=4096)
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-rates", type=float, nargs="+", default=[1000, 5000, 20000])
+    ap.add_argument("--served-max-batch", type=int, default=1024)
+    ap.add_argument("--served-slots", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.micro:

@@ -233,7 +233,9 @@ typedef struct {
     int64_t max_rows;     /* largest table a CTA builds (0: 2^22); queries that
                              need more run on the plain path */
     int32_t use_graph;    /* 1: capture the device work as a CUDA graph */
-    int32_t _reserved;
+    int32_t compact_results; /* 1: after each run, copy the results into one right-sized
+                                buffer and release the arena (results then outlive the
+                                arena's reuse; costs one copy of the result rows) */
 } gsmat_batch_config;
 
 typedef struct {
@@ -289,6 +291,69 @@ GSMAT_API void gsmat_batch_free(gsmat_batch *batch);
  * fields come from base, which may be NULL).  Synchronises `stream`. */
 GSMAT_API int gsmat_batch_autotune(const gsmat_store *store, const gsmat_bgp *bgps, int32_t n,
                                    const gsmat_batch_config *base, gsmat_stream_t stream, gsmat_batch_config *best);
+
+/* ------------------------------------------------------------------------ */
+/* Served evaluation: continuous batching over a resident store              */
+
+typedef struct gsmat_server gsmat_server;
+
+typedef struct {
+    int32_t max_batch;     /* queries per micro-batch (0: 1024) */
+    int32_t slots;         /* micro-batches in flight at once, each on its own stream (0: 4) */
+    int64_t budget_bytes;  /* admission budget: estimated device bytes of admitted, unfinished
+                              requests (0: 120 GiB) */
+    gsmat_batch_config batch; /* kernel shape and caps of every micro-batch (zeros: block 512,
+                                 1 CTA/SM, arena up to 8 GiB sized from the estimates) */
+} gsmat_server_config;
+
+typedef struct {
+    int64_t submitted;
+    int64_t completed;
+    int64_t failed;
+    int64_t batches;        /* micro-batches launched */
+    int64_t fallbacks;      /* requests re-run on the plain path */
+    int64_t queued;         /* now waiting for admission */
+    int64_t in_flight;      /* micro-batches now on the device or being planned */
+    int64_t in_flight_bytes;/* estimated bytes now admitted */
+} gsmat_server_stats_t;
+
+/* Start a server (two host threads) over a store, which must outlive it.
+ * A scheduler admits queued requests in arrival order into a micro-batch
+ * whenever a slot is free and their estimated bytes (the accumulated
+ * intermediate-size estimate of Sec. 6.2 times the row width) fit in the
+ * unclaimed budget; a request larger than the whole budget runs alone.
+ * Each micro-batch is planned and run as by gsmat_batch_prepare/execute on
+ * its own stream, so micro-batches overlap on the device; a completion
+ * thread finishes each as its device work ends. */
+GSMAT_API int gsmat_server_create(const gsmat_store *store, const gsmat_server_config *cfg, gsmat_server **out);
+
+/* Queue one BGP (copied; validated as gsmat_query) and return its ticket at
+ * once.  Thread-safe. */
+GSMAT_API int gsmat_server_submit(gsmat_server *srv, const gsmat_pattern *pats, int n_pats, int n_vars,
+                                  int64_t *ticket);
+
+/* Wait up to timeout_us (< 0: forever) for a request; *done = 1 when its
+ * result is ready.  Returns the request's error status if it failed. */
+GSMAT_API int gsmat_server_wait(gsmat_server *srv, int64_t ticket, int64_t timeout_us, int32_t *done);
+
+/* Shape of a finished request's result (as gsmat_table_info, columns =
+ * variables, rows ascending) and its latency from submit to completion. */
+GSMAT_API int gsmat_server_result(gsmat_server *srv, int64_t ticket, int64_t *rows, int32_t *cols,
+                                  double *latency_us);
+
+/* Copy a finished request's result (as gsmat_table_copy). */
+GSMAT_API int gsmat_server_copy(gsmat_server *srv, int64_t ticket, int32_t *dst, int dst_on_device,
+                                gsmat_stream_t stream);
+
+/* Forget a finished request; its micro-batch's device memory is freed when
+ * the last of its requests is released. */
+GSMAT_API int gsmat_server_release(gsmat_server *srv, int64_t ticket);
+
+GSMAT_API int gsmat_server_stats(gsmat_server *srv, gsmat_server_stats_t *stats);
+
+/* Stop admitting, finish what is in flight, fail what is still queued, join
+ * the threads and free everything (results included). */
+GSMAT_API void gsmat_server_destroy(gsmat_server *srv);
 
 /* ------------------------------------------------------------------------ */
 /* Host planner (Alg. 1; Sec. 6.2), callable without a GPU                   */

@@ -16,6 +16,14 @@ int batch_stats(const gsmat_batch *B, gsmat_batch_stats_t *s);
 int batch_autotune(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *base,
                    cudaStream_t st, gsmat_batch_config *best);
 void batch_free(gsmat_batch *B);
+int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_server **out);
+int server_submit(gsmat_server *srv, const gsmat_pattern *pats, int n_pats, int n_vars, int64_t *ticket);
+int server_wait(gsmat_server *srv, int64_t ticket, int64_t timeout_us, int32_t *done);
+int server_result(gsmat_server *srv, int64_t ticket, int64_t *rows, int32_t *cols, double *latency_us);
+int server_copy(gsmat_server *srv, int64_t ticket, int32_t *dst, int dst_on_device, cudaStream_t st);
+int server_release(gsmat_server *srv, int64_t ticket);
+int server_stats(gsmat_server *srv, gsmat_server_stats_t *s);
+void server_destroy(gsmat_server *srv);
 const char *last_error();
 int set_allocator(gsmat_alloc_fn a, gsmat_free_fn f, void *ctx);
 int profile_enable(int on);
@@ -193,6 +201,48 @@ GSMAT_API int gsmat_batch_autotune(const gsmat_store *store, const gsmat_bgp *bg
     gs::clear_error();
     return gs::batch_autotune(store, bgps, n, base, (cudaStream_t)stream, best);
 }
+
+GSMAT_API int gsmat_server_create(const gsmat_store *store, const gsmat_server_config *cfg, gsmat_server **out) {
+    gs::clear_error();
+    return gs::server_create(store, cfg, out);
+}
+
+GSMAT_API int gsmat_server_submit(gsmat_server *srv, const gsmat_pattern *pats, int n_pats, int n_vars,
+                                  int64_t *ticket) {
+    gs::clear_error();
+    return gs::server_submit(srv, pats, n_pats, n_vars, ticket);
+}
+
+GSMAT_API int gsmat_server_wait(gsmat_server *srv, int64_t ticket, int64_t timeout_us, int32_t *done) {
+    gs::clear_error();
+    return gs::server_wait(srv, ticket, timeout_us, done);
+}
+
+GSMAT_API int gsmat_server_result(gsmat_server *srv, int64_t ticket, int64_t *rows, int32_t *cols,
+                                  double *latency_us) {
+    gs::clear_error();
+    return gs::server_result(srv, ticket, rows, cols, latency_us);
+}
+
+GSMAT_API int gsmat_server_copy(gsmat_server *srv, int64_t ticket, int32_t *dst, int dst_on_device,
+                                gsmat_stream_t stream) {
+    gs::clear_error();
+    if (!srv) return set_error(GSMAT_ERR_INVALID_ARG, "server is NULL");
+    return gs::server_copy(srv, ticket, dst, dst_on_device, (cudaStream_t)stream);
+}
+
+GSMAT_API int gsmat_server_release(gsmat_server *srv, int64_t ticket) {
+    gs::clear_error();
+    if (!srv) return set_error(GSMAT_ERR_INVALID_ARG, "server is NULL");
+    return gs::server_release(srv, ticket);
+}
+
+GSMAT_API int gsmat_server_stats(gsmat_server *srv, gsmat_server_stats_t *stats) {
+    gs::clear_error();
+    return gs::server_stats(srv, stats);
+}
+
+GSMAT_API void gsmat_server_destroy(gsmat_server *srv) { gs::server_destroy(srv); }
 
 GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
                          const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out, double *est_out) {

@@ -406,7 +406,7 @@ __global__ void seg_gather_kernel(const SegDesc *__restrict__ segs, int n_segs, 
             if (segs[mid].row_off <= p) lo = mid; else hi = mid - 1;
         }
         const SegDesc &s = segs[lo];
-        const int64_t r = (int64_t)__ldg(perm + p) - s.row_off;  // source row (same segment)
+        const int64_t r = (perm ? (int64_t)__ldg(perm + p) : p) - s.row_off;  // source row (same segment)
         const int64_t i = p - s.row_off;                          // destination row
         for (int v = 0; v < s.V; ++v) s.out[(size_t)v * s.rows + i] = __ldg(s.col[v] + r);
     }

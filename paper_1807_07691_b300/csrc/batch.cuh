@@ -58,6 +58,18 @@ struct BatchArgs {
 
 int launch_batch_kernel(const BatchArgs &a, int block, int grid, cudaStream_t st);
 
+// Host resources a batch may borrow instead of creating its own (a server
+// keeps one set per in-flight slot and reuses it): a stream, four events and
+// pinned buffers for up to `cap` result descriptors and the two control
+// words.
+struct BatchResources {
+    cudaStream_t st;
+    cudaEvent_t ev[4];
+    BResult *results_host;
+    unsigned long long *ctrl_host;
+    int cap;
+};
+
 // One result table of a segmented reorder: its rows are rows
 // [row_off, row_off + rows) of the concatenation; col[v] = the column of
 // variable v (variables 0..m-1 are the sort key); out = V columns of rows.
@@ -71,6 +83,8 @@ struct SegDesc {
 };
 int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, const uint32_t *perm_in,
                     int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st);
+// out rows of every segment from the rows perm[p] (a plain copy when perm
+// is null).
 int launch_seg_gather(const SegDesc *segs, int n_segs, int64_t total, const uint32_t *perm, cudaStream_t st);
 
 }  // namespace gs

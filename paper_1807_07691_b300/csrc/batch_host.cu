@@ -26,6 +26,7 @@ struct gsmat_batch {
     std::vector<std::vector<int32_t>> plan_vars;
     gs::DevBuf prog, arena, ctrl, results_dev;
     std::vector<gs::DevBuf> seg_outs;  // columns of the results reordered together after the kernel
+    gs::DevBuf compact;                // results copied out of the arena (compact_results)
     gs::BResult *results_host = nullptr;   // pinned
     unsigned long long *ctrl_host = nullptr;  // pinned: queue head | arena top
     cudaStream_t priv = nullptr;
@@ -33,17 +34,29 @@ struct gsmat_batch {
     cudaGraphExec_t gexec = nullptr;
     std::vector<gsmat_table *> owned;  // per query: plain-path or reordered table, else null
     std::vector<int32_t> path;         // 0 kernel, 1 plain path, 2 kernel + multi-CTA reorder
+    std::vector<gs::BResult> results_final;  // descriptors after finish (ordinary host memory)
+    bool borrowed = false;             // stream, events and pinned buffers belong to a server slot
     gsmat_batch_stats_t stats{};
 
     ~gsmat_batch() {
         for (auto *t : owned) delete t;
         owned.clear();
+        if (borrowed) {
+            prog.release();
+            arena.release();
+            ctrl.release();
+            results_dev.release();
+            seg_outs.clear();
+            compact.release();
+            return;
+        }
         if (priv) cudaStreamSynchronize(priv);
         prog.release();
         arena.release();
         ctrl.release();
         results_dev.release();
         seg_outs.clear();
+        compact.release();
         if (gexec) cudaGraphExecDestroy(gexec);
         if (results_host) cudaFreeHost(results_host);
         if (ctrl_host) cudaFreeHost(ctrl_host);
@@ -79,6 +92,8 @@ int resolve_config(const gsmat_batch_config *in, gsmat_batch_config *out) {
         if (in->arena_bytes) c.arena_bytes = in->arena_bytes;
         if (in->max_rows) c.max_rows = in->max_rows;
         c.use_graph = in->use_graph;
+        c.compact_results = in->compact_results;
+        if (c.compact_results) c.use_graph = 0;  // the arena is re-allocated per run
     }
     if (c.block != 128 && c.block != 256 && c.block != 512) {
         return set_error(GSMAT_ERR_INVALID_ARG, "batch block must be 128, 256 or 512 (got %d)", c.block);
@@ -145,16 +160,28 @@ int capture_graph(gsmat_batch *B) {
 }
 
 int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *cfg_in,
-            cudaStream_t user_st, gsmat_batch *B) {
+            cudaStream_t user_st, const BatchResources *res, gsmat_batch *B) {
     if (!S || !bgps || n < 1) return set_error(GSMAT_ERR_INVALID_ARG, "store, bgps or n");
     B->S = S;
     B->n = n;
     GS_TRY(resolve_config(cfg_in, &B->cfg));
     B->grid = device_sm_count() * B->cfg.ctas_per_sm;
-    GS_CUDA(cudaStreamCreateWithFlags(&B->priv, cudaStreamNonBlocking));
-    for (cudaEvent_t *e : {&B->ev_in, &B->ev_a, &B->ev_b, &B->ev_done}) GS_CUDA(cudaEventCreate(e));
-    GS_CUDA(cudaEventRecord(B->ev_in, user_st));
-    GS_CUDA(cudaStreamWaitEvent(B->priv, B->ev_in, 0));
+    if (res) {
+        if (res->cap < n) return set_error(GSMAT_ERR_INVALID_ARG, "borrowed buffers hold %d results, not %d", res->cap, n);
+        B->borrowed = true;
+        B->priv = res->st;
+        B->ev_in = res->ev[0];
+        B->ev_a = res->ev[1];
+        B->ev_b = res->ev[2];
+        B->ev_done = res->ev[3];
+        B->results_host = res->results_host;
+        B->ctrl_host = res->ctrl_host;
+    } else {
+        GS_CUDA(cudaStreamCreateWithFlags(&B->priv, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&B->ev_in, &B->ev_a, &B->ev_b, &B->ev_done}) GS_CUDA(cudaEventCreate(e));
+        GS_CUDA(cudaEventRecord(B->ev_in, user_st));
+        GS_CUDA(cudaStreamWaitEvent(B->priv, B->ev_in, 0));
+    }
     B->pats.resize(n);
     B->plan_vars.resize(n);
     for (int i = 0; i < n; ++i) {
@@ -286,8 +313,10 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
     GS_TRY(B->arena.alloc((size_t)B->cfg.arena_bytes, B->priv));
     GS_TRY(B->ctrl.alloc(2 * sizeof(unsigned long long), B->priv));
     GS_TRY(B->results_dev.alloc(sizeof(BResult) * n, B->priv));
-    GS_CUDA(cudaMallocHost((void **)&B->results_host, sizeof(BResult) * n));
-    GS_CUDA(cudaMallocHost((void **)&B->ctrl_host, 2 * sizeof(unsigned long long)));
+    if (!B->borrowed) {
+        GS_CUDA(cudaMallocHost((void **)&B->results_host, sizeof(BResult) * n));
+        GS_CUDA(cudaMallocHost((void **)&B->ctrl_host, 2 * sizeof(unsigned long long)));
+    }
     GS_CUDA(cudaStreamSynchronize(B->priv));
     for (DevBuf *d : {&B->prog, &B->arena, &B->ctrl, &B->results_dev}) d->st = nullptr;
     B->owned.assign(n, nullptr);
@@ -384,6 +413,57 @@ int reorder_large_results(gsmat_batch *B) {
     return GSMAT_OK;
 }
 
+// Copy every kernel-path result into one right-sized buffer (one
+// segmented copy kernel) and release the arena and reorder buffers.
+int compact_results(gsmat_batch *B) {
+    std::vector<SegDesc> segs;
+    std::vector<int> qi;
+    int64_t rows = 0, words = 0;
+    for (int i = 0; i < B->n; ++i) {
+        const BResult &R = B->results_host[i];
+        if (B->owned[i] || R.status != BR_OK || R.rows == 0 || R.ncols == 0) continue;
+        SegDesc d;
+        memset(&d, 0, sizeof(d));
+        d.row_off = rows;
+        d.rows = R.rows;
+        d.V = R.ncols;
+        for (int v = 0; v < R.ncols; ++v) d.col[v] = R.col[v];
+        segs.push_back(d);
+        qi.push_back(i);
+        rows += R.rows;
+        words += R.rows * R.ncols;
+    }
+    B->compact.release();
+    if (!segs.empty()) {
+        GS_TRY(B->compact.alloc(sizeof(int32_t) * (size_t)words, B->priv));
+        int64_t w = 0;
+        for (SegDesc &d : segs) {
+            d.out = B->compact.as<int32_t>() + w;
+            w += d.rows * d.V;
+        }
+        DevBuf d_segs;
+        GS_TRY(d_segs.alloc(sizeof(SegDesc) * segs.size(), B->priv));
+        GS_CUDA(cudaMemcpyAsync(d_segs.p, segs.data(), sizeof(SegDesc) * segs.size(), cudaMemcpyHostToDevice, B->priv));
+        GS_TRY(launch_seg_gather(d_segs.as<SegDesc>(), (int)segs.size(), rows, nullptr, B->priv));
+        GS_CUDA(cudaStreamSynchronize(B->priv));
+        for (size_t k = 0; k < segs.size(); ++k) {
+            BResult &R = B->results_host[qi[k]];
+            for (int v = 0; v < R.ncols; ++v) R.col[v] = segs[k].out + (size_t)v * segs[k].rows;
+        }
+        B->compact.st = nullptr;
+    }
+    // a result with no rows or columns keeps no pointer into the arena
+    for (int i = 0; i < B->n; ++i) {
+        BResult &R = B->results_host[i];
+        if (!B->owned[i] && (R.rows == 0 || R.ncols == 0)) {
+            for (int v = 0; v < 32; ++v) R.col[v] = nullptr;
+        }
+    }
+    B->arena.release();
+    B->seg_outs.clear();
+    return GSMAT_OK;
+}
+
 // Device work only (no fallbacks); kernel time in *ms.
 int run_device(gsmat_batch *B, float *ms) {
     GS_CUDA(cudaEventRecord(B->ev_a, B->priv));
@@ -398,17 +478,32 @@ int run_device(gsmat_batch *B, float *ms) {
     return GSMAT_OK;
 }
 
-int execute(gsmat_batch *B, cudaStream_t user_st) {
-    GS_CUDA(cudaEventRecord(B->ev_in, user_st));
-    GS_CUDA(cudaStreamWaitEvent(B->priv, B->ev_in, 0));
+// Enqueue the device work of a run on the batch's stream and return.
+int launch_async(gsmat_batch *B) {
     for (auto *&t : B->owned) {
         delete t;
         t = nullptr;
     }
+    if (!B->arena.p) {  // released by the previous run's compaction
+        GS_TRY(B->arena.alloc((size_t)B->cfg.arena_bytes, B->priv));
+        B->arena.st = nullptr;
+    }
+    GS_CUDA(cudaEventRecord(B->ev_a, B->priv));
+    if (B->gexec) {
+        GS_CUDA(cudaGraphLaunch(B->gexec, B->priv));
+    } else {
+        GS_TRY(enqueue_device_work(B));
+    }
+    GS_CUDA(cudaEventRecord(B->ev_b, B->priv));
+    return GSMAT_OK;
+}
+
+// Wait for the run's device work, then finish the results the kernel handed
+// back (batched reorder of large results, plain-path re-runs).
+int finish(gsmat_batch *B) {
+    GS_CUDA(cudaEventSynchronize(B->ev_b));
     float ms = 0;
-    KernelTimer timer("batch_kernel", B->priv, 0.0, (double)B->n);
-    GS_TRY(run_device(B, &ms));
-    timer.stop();
+    GS_CUDA(cudaEventElapsedTime(&ms, B->ev_a, B->ev_b));
     gsmat_batch_stats_t &s = B->stats;
     memset(&s, 0, sizeof(s));
     s.n_queries = B->n;
@@ -445,6 +540,18 @@ int execute(gsmat_batch *B, cudaStream_t user_st) {
             s.n_fallback++;
         }
     }
+    if (B->cfg.compact_results) GS_TRY(compact_results(B));
+    B->results_final.assign(B->results_host, B->results_host + B->n);
+    return GSMAT_OK;
+}
+
+int execute(gsmat_batch *B, cudaStream_t user_st) {
+    GS_CUDA(cudaEventRecord(B->ev_in, user_st));
+    GS_CUDA(cudaStreamWaitEvent(B->priv, B->ev_in, 0));
+    KernelTimer timer("batch_kernel", B->priv, 0.0, (double)B->n);
+    GS_TRY(launch_async(B));
+    timer.stop();
+    GS_TRY(finish(B));
     GS_CUDA(cudaEventRecord(B->ev_done, B->priv));
     GS_CUDA(cudaStreamWaitEvent(user_st, B->ev_done, 0));
     profile_flush();
@@ -461,7 +568,8 @@ int result_view(const gsmat_batch *B, int32_t i, int64_t *rows, int32_t *cols, c
         if (col_ptrs) for (int c = 0; c < T->ncols; ++c) col_ptrs[c] = T->col[c];
         return GSMAT_OK;
     }
-    const BResult &R = B->results_host[i];
+    if ((int)B->results_final.size() != B->n) return set_error(GSMAT_ERR_INVALID_ARG, "batch has not been executed");
+    const BResult &R = B->results_final[i];
     if (rows) *rows = R.rows;
     if (cols) *cols = R.ncols;
     if (col_ptrs) for (int c = 0; c < R.ncols; ++c) col_ptrs[c] = R.col[c];
@@ -470,18 +578,35 @@ int result_view(const gsmat_batch *B, int32_t i, int64_t *rows, int32_t *cols, c
 
 }  // namespace
 
-int batch_prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *cfg,
-                  cudaStream_t st, gsmat_batch **out) {
+int batch_prepare_with(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *cfg,
+                       cudaStream_t st, const BatchResources *res, gsmat_batch **out) {
     if (!out) return set_error(GSMAT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     gsmat_batch *B = new gsmat_batch();
-    int rc = prepare(S, bgps, n, cfg, st, B);
+    int rc = prepare(S, bgps, n, cfg, st, res, B);
     if (rc != GSMAT_OK) {
         delete B;
         return rc;
     }
     *out = B;
     return GSMAT_OK;
+}
+
+int batch_prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_batch_config *cfg,
+                  cudaStream_t st, gsmat_batch **out) {
+    return batch_prepare_with(S, bgps, n, cfg, st, nullptr, out);
+}
+
+int batch_launch_async(gsmat_batch *B) { return launch_async(B); }
+int batch_kernel_done(gsmat_batch *B) {
+    const cudaError_t e = cudaEventQuery(B->ev_b);
+    if (e == cudaErrorNotReady) return 0;
+    if (e != cudaSuccess) cudaGetLastError();
+    return 1;  // done, or failed: finish() reports the error
+}
+int batch_finish(gsmat_batch *B) { return finish(B); }
+int batch_result_view(const gsmat_batch *B, int32_t i, int64_t *rows, int32_t *cols, const int32_t **col_ptrs) {
+    return result_view(B, i, rows, cols, col_ptrs);
 }
 
 int batch_execute(gsmat_batch *B, cudaStream_t st) {

@@ -72,7 +72,7 @@ class BGPStruct(ctypes.Structure):
 
 class BatchConfig(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
-                ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("_reserved", ctypes.c_int32)]
+                ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("compact_results", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -80,6 +80,16 @@ class BatchStats(ctypes.Structure):
                 ("n_fallback", ctypes.c_int32), ("kernel_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
                 ("arena_used", ctypes.c_int64),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
+                ("batch", BatchConfig)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "fallbacks", "queued",
+                                              "in_flight", "in_flight_bytes")]
 
 
 class KernelProfile(ctypes.Structure):
@@ -120,6 +130,14 @@ def _load():
         "gsmat_batch_stats": ([vp, vp], c_int),
         "gsmat_batch_free": ([vp], None),
         "gsmat_batch_autotune": ([vp, vp, i32, vp, vp, vp], c_int),
+        "gsmat_server_create": ([vp, vp, P(vp)], c_int),
+        "gsmat_server_submit": ([vp, vp, c_int, c_int, P(i64)], c_int),
+        "gsmat_server_wait": ([vp, i64, i64, P(i32)], c_int),
+        "gsmat_server_result": ([vp, i64, P(i64), P(i32), P(ctypes.c_double)], c_int),
+        "gsmat_server_copy": ([vp, i64, vp, c_int, vp], c_int),
+        "gsmat_server_release": ([vp, i64], c_int),
+        "gsmat_server_stats": ([vp, vp], c_int),
+        "gsmat_server_destroy": ([vp], None),
         "gsmat_radix_sort_u64": ([vp, vp, i64, c_int, c_int, vp], c_int),
         "gsmat_exclusive_scan_i32": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc": ([vp, vp, i64, vp], c_int),
@@ -367,6 +385,7 @@ def _config(cfg):
     c.arena_bytes = int(cfg.get("arena_bytes", 0))
     c.max_rows = int(cfg.get("max_rows", 0))
     c.use_graph = int(cfg.get("use_graph", 1))
+    c.compact_results = int(cfg.get("compact_results", 0))
     return c
 
 
@@ -435,6 +454,74 @@ class Batch:
         s = BatchStats()
         _check(_lib.gsmat_batch_stats(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in BatchStats._fields_}
+
+
+class Server:
+    """Continuous-batching server over a resident store (gsmat_server_*)."""
+
+    def __init__(self, store: "Store", max_batch: int = 0, slots: int = 0, budget_bytes: int = 0,
+                 batch: dict | None = None):
+        c = ServerConfig()
+        c.max_batch = max_batch
+        c.slots = slots
+        c.budget_bytes = budget_bytes
+        bc = _config(batch)
+        if bc is not None:
+            c.batch = bc
+        self._store = store  # must outlive the server
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_server_create(store.handle, ctypes.byref(c), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.gsmat_server_destroy(h)
+        self._h = None
+
+    @staticmethod
+    def marshal(bgp, n_vars=None):
+        """Pre-converted arguments for submit_raw (saves the conversion on a
+        hot submission path)."""
+        pats, n, nv = _patterns(bgp)
+        return pats, n, int(nv if n_vars is None else n_vars)
+
+    def submit_raw(self, marshalled) -> int:
+        pats, n, nv = marshalled
+        t = ctypes.c_int64()
+        _check(_lib.gsmat_server_submit(self._h, pats, n, nv, ctypes.byref(t)))
+        return int(t.value)
+
+    def submit(self, bgp, n_vars=None) -> int:
+        return self.submit_raw(self.marshal(bgp, n_vars))
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> bool:
+        done = ctypes.c_int32()
+        _check(_lib.gsmat_server_wait(self._h, ticket, timeout_us, ctypes.byref(done)))
+        return bool(done.value)
+
+    def result(self, ticket: int):
+        rows, cols, lat = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_double()
+        _check(_lib.gsmat_server_result(self._h, ticket, ctypes.byref(rows), ctypes.byref(cols), ctypes.byref(lat)))
+        return int(rows.value), int(cols.value), float(lat.value)
+
+    def to_numpy(self, ticket: int, stream=None) -> np.ndarray:
+        rows, cols, _ = self.result(ticket)
+        out = np.empty((rows, cols), dtype=np.int32)
+        if rows and cols:
+            _check(_lib.gsmat_server_copy(self._h, ticket, out.ctypes.data, 0, _stream_ptr(stream)))
+        return out
+
+    def release(self, ticket: int):
+        _check(_lib.gsmat_server_release(self._h, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(_lib.gsmat_server_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
 
 
 def batch_autotune(store: "Store", bgps, base: dict | None = None, stream=None) -> dict:

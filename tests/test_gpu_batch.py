@@ -122,6 +122,15 @@ def test_batch_graph_replay_identical(gs, tiny):
             assert np.array_equal(B.to_numpy(i), first[i])
 
 
+def test_batch_compact_results_rerun(gs, tiny):
+    t, ix, S, qs = tiny
+    B = gs.Batch(S, qs, config={"compact_results": 1})
+    for _ in range(2):
+        B.execute()
+        for i, q in enumerate(qs):
+            assert np.array_equal(B.to_numpy(i), ix.query(q))
+
+
 def test_batch_autotune(gs, tiny):
     t, ix, S, qs = tiny
     cfg = gs.batch_autotune(S, qs)

@@ -1,0 +1,92 @@
+"""Served evaluation (continuous batching): each result is the same alone
+and in the mix (GPU)."""
+
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import random_bgp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    import torch
+
+    torch.cuda.init()
+    import paper_1807_07691_b300 as g
+
+    return g
+
+
+@pytest.fixture(scope="module")
+def tiny(gs):
+    t = synth.make_graph("tiny")
+    S = gs.Store(t)
+    items = [(q.patterns, q.n_vars) for q in synth.make_queries("tiny", t)]
+    rng = np.random.default_rng(31)
+    ix = oracle.OracleIndex(t)
+    while len(items) < 200:
+        pats, V = random_bgp(rng, t, n_vars_max=4, n_pats_max=4, p_const=0.5)
+        try:
+            ix.query(pats, V, row_limit=500_000)  # keep the mix small enough
+        except oracle.OracleError:
+            continue
+        items.append((pats, V))
+    alone = [S.query(p, v).to_numpy() for p, v in items]
+    return S, items, alone
+
+
+def _run(srv, items):
+    tickets = [srv.submit(p, v) for p, v in items]
+    for t in tickets:
+        assert srv.wait(t)
+    return tickets
+
+
+def test_results_same_alone_and_in_the_mix(gs, tiny):
+    S, items, alone = tiny
+    srv = gs.Server(S, max_batch=32, slots=4)
+    tickets = _run(srv, items)
+    for t, want in zip(tickets, alone):
+        got = srv.to_numpy(t)
+        assert got.shape == want.shape and np.array_equal(got, want)
+        rows, cols, lat = srv.result(t)
+        assert lat > 0
+        srv.release(t)
+    st = srv.stats()
+    assert st["completed"] == len(items) and st["failed"] == 0 and st["batches"] >= len(items) // 32
+    srv.close()
+
+
+def test_tight_budget_and_concurrent_submitters(gs, tiny):
+    S, items, alone = tiny
+    srv = gs.Server(S, max_batch=8, slots=2, budget_bytes=1 << 20)
+    out = {}
+
+    def worker(lo, hi):
+        for i in range(lo, hi):
+            out[i] = srv.submit(*items[i])
+
+    ths = [threading.Thread(target=worker, args=(k * 50, (k + 1) * 50)) for k in range(len(items) // 50)]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    for i, t in out.items():
+        assert srv.wait(t)
+        assert np.array_equal(srv.to_numpy(t), alone[i])
+    assert srv.stats()["in_flight_bytes"] == 0
+    srv.close()
+
+
+def test_close_with_pending_work(gs, tiny):
+    S, items, alone = tiny
+    srv = gs.Server(S, max_batch=4, slots=1)
+    for p, v in items:
+        srv.submit(p, v)
+    srv.close()  # finishes what is in flight, fails the rest, does not hang
