@@ -163,16 +163,18 @@ def run_gsmat(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    marsh = [gs.Store.marshal(q) for q in queries]  # BGPs converted to the C layout once
+
     def step(profile_rows=None, lat=None):
         S = gs.Store(d_tri, stream=stream)
         tabs = []
         rows = 0
-        for q in queries:
+        for q in marsh:
             if lat is not None:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            T = S.query(q, stream=stream)
+            T = S.query_raw(q, stream=stream)
             if lat is not None:
                 e1.record(stream)
                 lat.append((e0, e1))
@@ -233,8 +235,8 @@ def run_gsmat(args):
         a.record(stream)
         S = gs.Store(h_tri.numpy(), stream=stream)
         d2h = 0
-        for qi, q in enumerate(queries):
-            T = S.query(q, stream=stream)
+        for qi, q in enumerate(marsh):
+            T = S.query_raw(q, stream=stream)
             rows, cols = T.shape
             if qi not in host_out or host_out[qi].numel() < rows * cols:
                 host_out[qi] = torch.empty(max(1, rows * cols), dtype=torch.int32).pin_memory()
@@ -337,10 +339,12 @@ def run_batched(args, gs, torch, d_tri, stream):
     gen_s = time.time() - t0
     S = gs.Store(d_tri, stream=stream)
 
+    bmarsh = [gs.Store.marshal(q) for q in bq]
+
     def plain_pass():
         rows = 0
-        for q in bq:
-            T = S.query(q, stream=stream)
+        for q in bmarsh:
+            T = S.query_raw(q, stream=stream)
             rows += T.rows
             T.free()
         return rows
@@ -411,6 +415,7 @@ def run_served(args, gs, torch, d_tri, stream, bq):
     path one query at a time (FIFO).  Latency = completion - arrival."""
     S = gs.Store(d_tri, stream=stream)
     marsh = [gs.Server.marshal(q) for q in bq]
+    marsh_plain = [gs.Store.marshal(q) for q in bq]
     rng = np.random.default_rng(7691 + 4)
     out = {"workload": f"Poisson arrivals over {len(bq)} batched-mix BGPs (medium graph, resident store)",
            "seconds_per_rate": args.served_seconds, "rates": []}
@@ -445,7 +450,7 @@ def run_served(args, gs, torch, d_tri, stream, bq):
         last = t0
         for i in range(n):
             _spin_until(t0 + arrivals[i])
-            T = S.query(bq[pick[i]], stream=stream)
+            T = S.query_raw(marsh_plain[pick[i]], stream=stream)
             T.free()
             last = time.perf_counter()
             lat_p[i] = (last - (t0 + arrivals[i])) * 1e3

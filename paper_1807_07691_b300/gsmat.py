@@ -362,15 +362,24 @@ class Store:
                                        ent.ctypes.data, _stream_ptr(stream)))
         return rid[:nr], ptr, ent[: st["nnz"]]
 
-    def query(self, bgp, n_vars=None, flags: int = SORTED, stream=None) -> Table:
+    @staticmethod
+    def marshal(bgp, n_vars=None):
+        """Pre-converted arguments for query_raw: (patterns, n, n_vars)."""
         pats, n, nv = _patterns(bgp)
         if n_vars is None:
             n_vars = nv
         if n_vars is None:
             raise ValueError("n_vars is required")
+        return pats, n, int(n_vars)
+
+    def query_raw(self, marshalled, flags: int = SORTED, stream=None) -> Table:
+        pats, n, nv = marshalled
         h = ctypes.c_void_p()
-        _check(_lib.gsmat_query(self._h, pats, n, int(n_vars), flags, _stream_ptr(stream), ctypes.byref(h)))
+        _check(_lib.gsmat_query(self._h, pats, n, nv, flags, _stream_ptr(stream), ctypes.byref(h)))
         return Table(h)
+
+    def query(self, bgp, n_vars=None, flags: int = SORTED, stream=None) -> Table:
+        return self.query_raw(self.marshal(bgp, n_vars), flags, stream)
 
 
 # ----------------------------------------------------------------------------

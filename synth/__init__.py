@@ -14,7 +14,7 @@ reproduced.
 """
 
 from .graphs import CONFIGS, GraphConfig, make_graph, graph_stats, small_random_graph
-from .queries import BGP, make_queries, make_batched_queries, bgp_row_bound
+from .queries import BGP, make_queries, make_batched_queries, make_large_queries, bgp_row_bound
 
 __all__ = [
     "CONFIGS",
@@ -25,5 +25,6 @@ __all__ = [
     "BGP",
     "make_queries",
     "make_batched_queries",
+    "make_large_queries",
     "bgp_row_bound",
 ]

@@ -17,7 +17,10 @@ Configurations (graph seed = 1807 + k):
   style: subject and object ranks are drawn with weight (r + 1)^(-1/(alpha-1)),
   alpha = 2.1, through two independent random permutations of the entity ids;
   predicates follow Zipf(1.1).
-* ``large``  (k=2): 4x10^7 entities, 256 predicates, 3x10^8 triples, same laws.
+* ``large``  (k=2): 4x10^7 entities, 256 predicates, 3x10^8 triples, the
+  same laws with ranks drawn from the continuous power law's closed-form
+  inverse CDF; returned in (s, p, o) key order (duplicates are removed by
+  sorting and the surplus draws are dropped uniformly at random).
 """
 
 from __future__ import annotations
@@ -97,13 +100,27 @@ def _tiny(cfg: GraphConfig, rng: np.random.Generator) -> np.ndarray:
     return out
 
 
+def _power_law_ranks(u: np.ndarray, E: int, beta: float) -> np.ndarray:
+    """Ranks r in [0, E) with density proportional to (r + 1)^(-beta): the
+    closed-form inverse of the continuous law's CDF, floored (used for the
+    large configuration, where a binary search per draw into an E-entry
+    discrete CDF is too slow)."""
+    g = 1.0 - beta
+    hi = (E + 1.0) ** g
+    x = (1.0 + u * (hi - 1.0)) ** (1.0 / g) - 1.0
+    return np.minimum(x.astype(np.int64), E - 1)
+
+
 def _chung_lu(cfg: GraphConfig, rng: np.random.Generator) -> np.ndarray:
     pred_ids = _predicate_ids(rng, cfg.n_predicates)
     E = cfg.n_entities
     expo = -1.0 / (cfg.alpha - 1.0)
-    w = (np.arange(E, dtype=np.float64) + 1.0) ** expo
-    cdf = np.cumsum(w)
-    cdf /= cdf[-1]
+    if cfg.n_triples >= 100_000_000:
+        cdf = None
+    else:
+        w = (np.arange(E, dtype=np.float64) + 1.0) ** expo
+        cdf = np.cumsum(w)
+        cdf /= cdf[-1]
     perm_out = rng.permutation(E).astype(np.int32)
     perm_in = rng.permutation(E).astype(np.int32)
     pred_cdf = np.cumsum(_zipf_pmf(cfg.n_predicates, cfg.pred_zipf))
@@ -119,10 +136,35 @@ def _chung_lu(cfg: GraphConfig, rng: np.random.Generator) -> np.ndarray:
         o = np.empty(n_draw, dtype=np.int32)
         for a in range(0, n_draw, chunk):
             b = min(n_draw, a + chunk)
-            s[a:b] = perm_out[np.searchsorted(cdf, rng.random(b - a), side="right").clip(0, E - 1)]
-            o[a:b] = perm_in[np.searchsorted(cdf, rng.random(b - a), side="right").clip(0, E - 1)]
+            if cfg.n_triples >= 100_000_000:
+                s[a:b] = perm_out[_power_law_ranks(rng.random(b - a), E, -expo)]
+                o[a:b] = perm_in[_power_law_ranks(rng.random(b - a), E, -expo)]
+            else:
+                s[a:b] = perm_out[np.searchsorted(cdf, rng.random(b - a), side="right").clip(0, E - 1)]
+                o[a:b] = perm_in[np.searchsorted(cdf, rng.random(b - a), side="right").clip(0, E - 1)]
             p[a:b] = np.searchsorted(pred_cdf, rng.random(b - a), side="right").clip(0, cfg.n_predicates - 1)
         keys = (s.astype(np.int64) * cfg.n_predicates + p.astype(np.int64)) * E + o.astype(np.int64)
+        if cfg.n_triples >= 100_000_000:
+            # large sets: sort-based dedupe, then drop the surplus uniformly
+            # at random (first-occurrence order would need an argsort)
+            del s, p, o
+            keys = np.unique(keys)
+            if keys.size >= cfg.n_triples:
+                excess = keys.size - cfg.n_triples
+                if excess:
+                    drop = np.argpartition(rng.random(keys.size), excess)[:excess]
+                    keep = np.ones(keys.size, dtype=bool)
+                    keep[drop] = False
+                    keys = keys[keep]
+                out = np.empty((cfg.n_triples, 3), dtype=np.int32)
+                out[:, 2] = (keys % E).astype(np.int32)
+                keys //= E
+                out[:, 1] = pred_ids[(keys % cfg.n_predicates).astype(np.int64)]
+                out[:, 0] = (keys // cfg.n_predicates).astype(np.int32)
+                return out
+            del keys
+            surplus *= 1.25
+            continue
         first = _first_unique(keys)
         del keys
         if first.size >= cfg.n_triples:

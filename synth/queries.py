@@ -641,3 +641,164 @@ def make_batched_queries(n_queries: int = 4096, triples: np.ndarray | None = Non
     with ctx.Pool(workers, initializer=_batched_worker_init, initargs=(limit,)) as pool:
         parts = pool.map(_batched_worker, jobs)
     return [q for part in parts for q in part]
+
+
+# ----------------------------------------------------------------------------
+# large configuration: anchored queries with exact frontier counts
+#
+# Dense walk-count vectors over 4x10^7 entities per predicate do not fit, so
+# every large query is anchored at a constant (a star's centre, a chain's
+# first vertex, a snowflake's centre) whose row is far shorter than the
+# smallest predicate; the planner then starts at the anchor, and every plan
+# prefix is a sub-pattern containing it, whose size is bounded below from the
+# sparse frontier of walks out of the anchor.
+
+
+class _LargeAdjacency:
+    def __init__(self, triples: np.ndarray, n_entities: int):
+        t = np.asarray(triples)
+        self.n = t.shape[0]
+        self.E = int(max(n_entities, int(t[:, [0, 2]].max()) + 1))
+        s = t[:, 0]
+        if np.all(s[1:] >= s[:-1]):
+            self.by_s = None  # already in subject order
+        else:
+            self.by_s = np.argsort(s, kind="stable")
+        ss = s if self.by_s is None else s[self.by_s]
+        self.s_ptr = np.searchsorted(ss, np.arange(self.E + 1, dtype=np.int64))
+        self.out_p = t[:, 1] if self.by_s is None else t[self.by_s, 1]
+        self.out_o = t[:, 2] if self.by_s is None else t[self.by_s, 2]
+        self.by_o = np.argsort(t[:, 2], kind="stable")
+        self.o_ptr = np.searchsorted(t[self.by_o, 2], np.arange(self.E + 1, dtype=np.int64))
+        self.in_p = t[self.by_o, 1]
+        self.in_s = t[self.by_o, 0]
+        self.preds, self.pred_nnz = np.unique(t[:, 1], return_counts=True)
+
+    def edges(self, v, direction):
+        """(predicates, neighbours) of entity v's out- or in-edges."""
+        if direction == "out":
+            a, b = self.s_ptr[v], self.s_ptr[v + 1]
+            return self.out_p[a:b], self.out_o[a:b]
+        a, b = self.o_ptr[v], self.o_ptr[v + 1]
+        return self.in_p[a:b], self.in_s[a:b]
+
+    def frontier_step(self, verts, mult, pred, direction, cap):
+        """Multiset of neighbours (by pred, in direction) of a weighted vertex
+        set; None if it would exceed cap entries."""
+        ptr = self.s_ptr if direction == "out" else self.o_ptr
+        lo, hi = ptr[verts], ptr[verts + 1]
+        lens = hi - lo
+        if int(lens.sum()) > cap:
+            return None
+        idx = np.repeat(lo - np.concatenate([[0], np.cumsum(lens)[:-1]]), lens) + np.arange(int(lens.sum()))
+        P = self.out_p if direction == "out" else self.in_p
+        N = self.out_o if direction == "out" else self.in_s
+        w = np.repeat(mult, lens)
+        keep = P[idx] == pred
+        nb, ww = N[idx][keep], w[keep]
+        if nb.size == 0:
+            return np.zeros(0, np.int64), np.zeros(0, np.float64)
+        u, inv = np.unique(nb, return_inverse=True)
+        return u.astype(np.int64), np.bincount(inv, weights=ww)
+
+
+def _large_one(adj, rng, shape, n_pat, limit, max_anchor_deg, min_bound=0.0):
+    for _ in range(20000):
+        t = int(rng.integers(adj.n))
+        if shape in ("star", "snowflake"):
+            c = int(np.searchsorted(adj.s_ptr, t, side="right") - 1)  # subject of entry t
+            ps, os_ = adj.edges(c, "out")
+            if ps.size == 0 or ps.size > max_anchor_deg:
+                continue
+            n_arms = n_pat if shape == "star" else max(2, n_pat // 2)
+            picks = rng.integers(ps.size, size=n_arms)
+            arms = [(int(ps[i]), int(os_[i])) for i in picks]
+            pats = [(c, p, v, False, True) for v, (p, _) in enumerate(arms)]
+            # degree of c per arm predicate
+            factors = [float(np.sum(ps == p)) for p, _ in arms]
+            if shape == "snowflake":
+                n_sub = n_pat - n_arms
+                next_var = n_arms
+                for j in range(n_sub):
+                    a = j % n_arms
+                    y = arms[a][1]
+                    yp, _ = adj.edges(y, "out")
+                    if yp.size == 0:
+                        break
+                    pb = int(yp[rng.integers(yp.size)])
+                    pats.append((a, pb, next_var, True, True))
+                    next_var += 1
+                    # bound for the arm: sum over its candidates of max(1, deg)
+                    ys = os_[ps == arms[a][0]].astype(np.int64)
+                    lo, hi = adj.s_ptr[ys], adj.s_ptr[ys + 1]
+                    degs = np.array([np.sum(adj.out_p[l:h] == pb) for l, h in zip(lo, hi)], dtype=np.float64)
+                    factors[a] = float(np.maximum(degs, 1.0).sum()) if factors[a] > 0 else 0.0
+                if len(pats) != n_pat:
+                    continue
+            bound = float(np.prod(factors))
+            if bound > limit or bound < max(1.0, min_bound):
+                continue
+            exact = bound if shape == "star" else None
+            return pats, next_var if shape == "snowflake" else n_arms, bound, exact
+        # chain from an anchor: exact frontier counts hop by hop
+        c = int(np.searchsorted(adj.s_ptr, t, side="right") - 1)
+        if adj.s_ptr[c + 1] - adj.s_ptr[c] > max_anchor_deg:
+            continue
+        verts, mult = np.array([c], np.int64), np.array([1.0])
+        pats, cur_slot, best = [], None, 0.0
+        ok = True
+        for h in range(n_pat):
+            d = "out" if (h == 0 or rng.random() < 0.6) else "in"
+            v0 = int(verts[rng.integers(verts.size)])
+            ps, nbs = adj.edges(v0, d)
+            if ps.size == 0:
+                ok = False
+                break
+            pred = int(ps[rng.integers(ps.size)])
+            step = adj.frontier_step(verts, mult, pred, d, cap=50_000_000)
+            if step is None or step[0].size == 0:
+                ok = False
+                break
+            verts, mult = step
+            total = float(mult.sum())
+            best = max(best, total)
+            if best > limit:
+                ok = False
+                break
+            src = (c, False) if h == 0 else (h - 1, True)
+            dst = (h, True)
+            if d == "out":
+                pats.append((src[0], pred, dst[0], src[1], dst[1]))
+            else:
+                pats.append((dst[0], pred, src[0], dst[1], src[1]))
+        if ok and best >= min_bound:
+            return pats, n_pat, best, float(mult.sum())
+    raise RuntimeError(f"no large {shape}/{n_pat} query")
+
+
+def make_large_queries(triples: np.ndarray | None = None, seed: int | None = None, n_queries: int = 20,
+                       limit: float = 1e9):
+    """20 anchored BGPs of 4-8 patterns over the large graph: stars,
+    chains and snowflakes, from selective ones to intermediates of 10^8-10^9
+    rows.  ``bgp.bound`` is the exact row count (stars, chains' largest
+    frontier) or an upper bound (snowflakes)."""
+    cfg = CONFIGS["large"]
+    if triples is None:
+        triples = make_graph(cfg)
+    seed = cfg.query_seed if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed))
+    adj = _LargeAdjacency(triples, cfg.n_entities)
+    min_pred = int(adj.pred_nnz.min())
+    out = []
+    for qi in range(n_queries):
+        shape = ("star", "chain", "snowflake", "star", "chain")[qi % 5]
+        n_pat = int(rng.integers(4, 9)) if shape != "chain" else int(rng.integers(4, 7))
+        # every fourth query is unselective: some plan prefix reaches 10^8 rows
+        pats, n_vars, bound, exact = _large_one(adj, rng, shape, n_pat, limit,
+                                                max_anchor_deg=min(min_pred // 4, 20000),
+                                                min_bound=1e8 if qi % 4 == 3 else 0.0)
+        bgp = BGP(pats, n_vars, shape, f"large-q{qi:02d}-{shape}{len(pats)}")
+        bgp.bound = bound
+        bgp.count = exact  # exact result rows (stars, chains) or None
+        out.append(bgp)
+    return out
