@@ -148,7 +148,12 @@ def _chung_lu(cfg: GraphConfig, rng: np.random.Generator) -> np.ndarray:
             # large sets: sort-based dedupe, then drop the surplus uniformly
             # at random (first-occurrence order would need an argsort)
             del s, p, o
-            keys = np.unique(keys)
+            keys.sort()  # in place; numpy's hash-based unique is far slower here
+            distinct = np.empty(keys.size, dtype=bool)
+            distinct[0] = True
+            np.not_equal(keys[1:], keys[:-1], out=distinct[1:])
+            keys = keys[distinct]
+            del distinct
             if keys.size >= cfg.n_triples:
                 excess = keys.size - cfg.n_triples
                 if excess:
