@@ -385,6 +385,18 @@ GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, cons
 GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int begin_bit, int end_bit,
                                    gsmat_stream_t stream);
 
+/* Canonical output of a binding table (the result row of Sec. 6.3 over the
+ * variables in id order): stable lexicographic reorder of n rows by their
+ * first m of V columns.  d_cols[v] / d_out[v] (v < V) are device int32
+ * columns of n rows; every value must lie in [0, 2^bits).  Keys pack
+ * floor(64 / bits) columns each; wider orders sort chunk by chunk, least
+ * significant first, each chunk being 8-bit onesweep passes whose first pass
+ * packs the keys from the columns and whose last pass writes d_out.
+ * 1 <= m <= V <= 32, 1 <= bits <= 31, 0 <= n < 2^32; d_out must not alias
+ * d_cols.  Scratch comes from the allocator hook.  Does not synchronise. */
+GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bits, int64_t n,
+                              int32_t *const *d_out, gsmat_stream_t stream);
+
 /* Exclusive prefix sum of n int32 counts (each >= 0) into d_out[0..n]
  * (int64; d_out[n] = total), single pass with decoupled look-back over
  * tiles.  Scratch (tile descriptors) comes from the allocator hook.

@@ -1,6 +1,7 @@
 // The C ABI of libgsmat (include/gsmat.h): argument checks and dispatch.
 #include <string.h>
 
+#include "join.cuh"
 #include "plan.h"
 #include "query.cuh"
 #include "store.cuh"
@@ -257,6 +258,20 @@ GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n
     gs::clear_error();
     if (n > 0 && !d_keys) return set_error(GSMAT_ERR_INVALID_ARG, "keys is NULL");
     return gs::radix_sort_u64(d_keys, d_vals, n, begin_bit, end_bit, (cudaStream_t)stream);
+}
+
+GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bits, int64_t n,
+                              int32_t *const *d_out, gsmat_stream_t stream) {
+    gs::clear_error();
+    if (V < 1 || V > gs::kMaxCols || !d_cols || !d_out) return set_error(GSMAT_ERR_INVALID_ARG, "bad columns");
+    gs::Cols in;
+    gs::OutCols out;
+    for (int v = 0; v < gs::kMaxCols; ++v) {
+        in.c[v] = v < V ? d_cols[v] : nullptr;
+        out.c[v] = v < V ? d_out[v] : nullptr;
+        if (v < V && n > 0 && (!in.c[v] || !out.c[v])) return set_error(GSMAT_ERR_INVALID_ARG, "column %d is NULL", v);
+    }
+    return gs::reorder_rows(in, V, m, bits, n, out, (cudaStream_t)stream, nullptr);
 }
 
 GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int64_t n, gsmat_stream_t stream) {

@@ -225,9 +225,10 @@ __device__ void run_query(const BatchArgs &a, CtaShared<BLOCK> &sm, int q) {
                 m = carry;
                 rc = 1;
             } else {
-                rel0 = a.sv.side[0].key + p0.ent_base;
-                rel1 = a.sv.side[0].val + p0.ent_base;
-                m = p0.nnz;
+                const PredSide &pp = S.swap ? p1 : p0;
+                rel0 = a.sv.side[S.swap].key + pp.ent_base;
+                rel1 = a.sv.side[S.swap].val + pp.ent_base;
+                m = pp.nnz;
                 rc = 2;
             }
             if (unit) {

@@ -18,7 +18,7 @@ struct BStep {
     int32_t diag;      // CROSS of ?x p ?x
     int32_t c_first;   // EXPAND from a constant: entry range of its row
     int32_t c_last;
-    int32_t _pad;
+    int32_t swap;      // CROSS of M_p: take it by object, columns (o, s)
 };
 
 struct BQuery {

@@ -289,11 +289,13 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
                 pv.push_back(p.s);
             } else if (S1.kind == GSMAT_STEP_CROSS) {
                 S1.diag = p.s == p.o ? 1 : 0;
-                col_of_var[p.s] = ncols++;
-                pv.push_back(p.s);
+                S1.swap = (!S1.diag && p.o < p.s) ? 1 : 0;  // lower variable id first
+                const int32_t first = S1.swap ? p.o : p.s, second = S1.swap ? p.s : p.o;
+                col_of_var[first] = ncols++;
+                pv.push_back(first);
                 if (!S1.diag) {
-                    col_of_var[p.o] = ncols++;
-                    pv.push_back(p.o);
+                    col_of_var[second] = ncols++;
+                    pv.push_back(second);
                 }
             }
             B->hs.push_back(S1);

@@ -285,43 +285,7 @@ __global__ void const_lookup_kernel(StoreView sv, const PredSide *__restrict__ s
 }
 
 // ---------------------------------------------------------------------------
-// canonical ordering helpers
-
-__global__ void pack_rows_kernel(Cols cols, int nc, int bits, const uint32_t *__restrict__ perm, int64_t n,
-                                 uint64_t *__restrict__ keys) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = perm ? __ldg(perm + i) : (uint32_t)i;
-        uint64_t key = 0;
-        for (int c = 0; c < nc; ++c) key = (key << bits) | (uint64_t)(uint32_t)__ldg(cols.c[c] + r);
-        keys[i] = key;
-    }
-}
-
-__global__ void iota_u32_kernel(uint32_t *v, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        v[i] = (uint32_t)i;
-    }
-}
-
-__global__ void finalize_rows_kernel(const uint64_t *__restrict__ keys, int k0, int bits, const uint32_t *__restrict__ perm,
-                                     Cols rest, int n_rest, int64_t n, OutCols out) {
-    const uint64_t mask = (bits >= 64) ? ~0ull : ((1ull << bits) - 1);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t key = __ldg(keys + i);
-        for (int c = 0; c < k0; ++c) out.c[c][i] = (int32_t)((key >> ((k0 - 1 - c) * bits)) & mask);
-        if (n_rest > 0) {
-            const uint32_t r = __ldg(perm + i);
-            for (int c = 0; c < n_rest; ++c) out.c[k0 + c][i] = __ldg(rest.c[c] + r);
-        }
-    }
-}
-
-__global__ void gather_rows_kernel(Cols in, int k, const uint32_t *__restrict__ perm, int64_t n, OutCols out) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = __ldg(perm + i);
-        for (int c = 0; c < k; ++c) out.c[c][i] = __ldg(in.c[c] + r);
-    }
-}
+// row gathers and layout conversion
 
 __global__ void interleave_kernel(Cols in, int k, int64_t n, int32_t *__restrict__ dst) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -456,43 +420,6 @@ int launch_const_lookup(const StoreView &sv, const PredSide *d_sides, int n_pred
     if (n_req <= 0) return GSMAT_OK;
     const_lookup_kernel<<<(n_req + 127) / 128, 128, 0, st>>>(sv, d_sides, n_pred, d_req, n_req, d_out);
     GS_LAUNCH_CHECK();
-    return GSMAT_OK;
-}
-
-int launch_pack_rows(const Cols &cols, int nc, int bits, const uint32_t *perm, int64_t n, uint64_t *keys,
-                     cudaStream_t st) {
-    if (n <= 0) return GSMAT_OK;
-    KernelTimer t("pack_rows", st, (double)n * (4.0 * nc + 8.0 + (perm ? 4.0 : 0.0)), (double)n);
-    pack_rows_kernel<<<grid_1d(n, 256), 256, 0, st>>>(cols, nc, bits, perm, n, keys);
-    GS_LAUNCH_CHECK();
-    t.stop();
-    return GSMAT_OK;
-}
-
-int launch_iota(uint32_t *v, int64_t n, cudaStream_t st) {
-    if (n <= 0) return GSMAT_OK;
-    iota_u32_kernel<<<grid_1d(n, 256), 256, 0, st>>>(v, n);
-    GS_LAUNCH_CHECK();
-    return GSMAT_OK;
-}
-
-int launch_finalize_rows(const uint64_t *keys, int k0, int bits, const uint32_t *perm, const Cols &rest, int n_rest,
-                         int64_t n, OutCols out, cudaStream_t st) {
-    if (n <= 0) return GSMAT_OK;
-    KernelTimer t("finalize_rows", st, (double)n * (8.0 + 4.0 * (k0 + n_rest) + (n_rest ? 4.0 + 4.0 * n_rest : 0.0)),
-                  (double)n);
-    finalize_rows_kernel<<<grid_1d(n, 256), 256, 0, st>>>(keys, k0, bits, perm, rest, n_rest, n, out);
-    GS_LAUNCH_CHECK();
-    t.stop();
-    return GSMAT_OK;
-}
-
-int launch_gather_rows(const Cols &in, int k, const uint32_t *perm, int64_t n, OutCols out, cudaStream_t st) {
-    if (n <= 0) return GSMAT_OK;
-    KernelTimer t("gather_rows", st, (double)n * (4.0 + 8.0 * k), (double)n);
-    gather_rows_kernel<<<grid_1d(n, 256), 256, 0, st>>>(in, k, perm, n, out);
-    GS_LAUNCH_CHECK();
-    t.stop();
     return GSMAT_OK;
 }
 

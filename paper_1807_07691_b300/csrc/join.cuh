@@ -65,15 +65,13 @@ int launch_const_lookup(const StoreView &sv, const PredSide *d_sides, int n_pred
 
 // keys[i] = columns cols[0..nc) of row perm[i] (or row i if perm is null)
 // packed most-significant first with `bits` bits each.
-int launch_pack_rows(const Cols &cols, int nc, int bits, const uint32_t *perm, int64_t n, uint64_t *keys,
-                     cudaStream_t st);
-int launch_iota(uint32_t *v, int64_t n, cudaStream_t st);
-// out[c][i] for c < k0: field c (most significant first, `bits` wide) of
-// keys[i]; out[k0 + c][i] = rest[c][perm[i]] for c < n_rest.
-int launch_finalize_rows(const uint64_t *keys, int k0, int bits, const uint32_t *perm, const Cols &rest, int n_rest,
-                         int64_t n, OutCols out, cudaStream_t st);
-// out[c][i] = in[c][perm[i]] for c < k.
-int launch_gather_rows(const Cols &in, int k, const uint32_t *perm, int64_t n, OutCols out, cudaStream_t st);
+// Stable reorder of an n-row table (cols = its V columns in variable order)
+// by variables 0..m-1, lexicographically, into out (V columns).  Keys pack
+// the variables `bits` bits each, as many per 64-bit key as fit; wider
+// orders sort chunk by chunk, least significant first.  *err_word is set if a
+// bounded wait expired (may be null).
+int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutCols &out, cudaStream_t st,
+                 int *err_word);
 // dst[i * k + c] = in[c][i] (row-major interleave).
 int launch_interleave(const Cols &in, int k, int64_t n, int32_t *dst, cudaStream_t st);
 // out[c][i] = in[c][i] (copy k columns).

@@ -113,41 +113,13 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
         out.buf = std::move(t.buf);
         return GSMAT_OK;
     }
-    const int64_t n = t.rows;
     const int bits = std::max(1, bits_for((uint64_t)std::max(cx.S->max_entity, 0)));
-    const int per_key = 64 / bits;
-    // The m sort variables in chunks of per_key, most significant first;
-    // least-significant-digit order sorts by the last chunk first.
-    const int n_chunks = (m + per_key - 1) / per_key;
-    DevBuf keys, perm;
-    GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, cx.st));
-    GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)n, cx.st));
-    for (int ci = n_chunks - 1; ci >= 0; --ci) {
-        const int b = ci * per_key;
-        const int e = std::min(m, b + per_key);
-        Cols kc;
-        for (int v = b; v < e; ++v) kc.c[v - b] = t.col[colof[v]];
-        const int nc = e - b;
-        if (ci == n_chunks - 1) {
-            GS_TRY(launch_iota(perm.as<uint32_t>(), n, cx.st));
-            GS_TRY(launch_pack_rows(kc, nc, bits, nullptr, n, keys.as<uint64_t>(), cx.st));
-        } else {
-            GS_TRY(launch_pack_rows(kc, nc, bits, perm.as<uint32_t>(), n, keys.as<uint64_t>(), cx.st));
-        }
-        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, nc * bits, cx.st, cx.d_err()));
-    }
-    // variables 0..k0-1 are unpacked from the sorted keys, the others are
-    // gathered through the permutation
-    const int k0 = std::min(m, per_key);
+    Cols in;
+    for (int v = 0; v < kMaxCols; ++v) in.c[v] = v < V ? t.col[colof[v]] : nullptr;
     OutCols oc;
-    GS_TRY(alloc_cols(out, V, n, cx.st, &oc));
-    Cols rest;
-    for (int v = 0; v < V; ++v) {
-        if (v >= k0) rest.c[v - k0] = t.col[colof[v]];
-        out.vars[v] = v;
-    }
-    GS_TRY(launch_finalize_rows(keys.as<uint64_t>(), k0, bits, perm.as<uint32_t>(), rest, V - k0, n, oc, cx.st));
-    return GSMAT_OK;
+    GS_TRY(alloc_cols(out, V, t.rows, cx.st, &oc));
+    for (int v = 0; v < V; ++v) out.vars[v] = v;
+    return reorder_rows(in, V, m, bits, t.rows, oc, cx.st, cx.d_err());
 }
 
 int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
@@ -234,8 +206,12 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         uint64_t seen = 0;
         for (int s = 0; s < n_pats; ++s) {
             const gsmat_pattern &p = pats[qs.order[s]];
-            if (p.s_var && !((seen >> p.s) & 1)) { plan_vars.push_back(p.s); seen |= uint64_t(1) << p.s; }
-            if (p.o_var && !((seen >> p.o) & 1)) { plan_vars.push_back(p.o); seen |= uint64_t(1) << p.o; }
+            // a CROSS of two new variables binds the lower id first (see the step)
+            const bool swap = qs.kind[s] == GSMAT_STEP_CROSS && p.s_var && p.o_var && p.o < p.s;
+            const int32_t a = swap ? p.o : p.s, b = swap ? p.s : p.o;
+            const bool a_var = swap ? p.o_var : p.s_var, b_var = swap ? p.s_var : p.o_var;
+            if (a_var && !((seen >> a) & 1)) { plan_vars.push_back(a); seen |= uint64_t(1) << a; }
+            if (b_var && !((seen >> b) & 1)) { plan_vars.push_back(b); seen |= uint64_t(1) << b; }
         }
     }
 
@@ -413,12 +389,18 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
                 rc = 1;
                 rv[0] = p.s;
             } else {
-                rel.c[0] = S->view.side[0].key + ps0.ent_base;
-                rel.c[1] = S->view.side[0].val + ps0.ent_base;
-                m = ps0.nnz;
+                // M_p from whichever side puts the lower variable id first:
+                // rows by subject are (s, o)-ascending, rows by object
+                // (o, s)-ascending, so the result stays sorted and the final
+                // reorder to variable order has less to do
+                const int sd = p.o < p.s ? 1 : 0;
+                const PredSide &pss = sd == 0 ? ps0 : ps1;
+                rel.c[0] = S->view.side[sd].key + pss.ent_base;
+                rel.c[1] = S->view.side[sd].val + pss.ent_base;
+                m = pss.nnz;
                 rc = 2;
-                rv[0] = p.s;
-                rv[1] = p.o;
+                rv[0] = sd == 0 ? p.s : p.o;
+                rv[1] = sd == 0 ? p.o : p.s;
             }
             if (unit) {
                 nxt.rows = m;

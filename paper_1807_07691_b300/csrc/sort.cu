@@ -12,7 +12,14 @@
 // digit, bounded waits), stages the tile in shared memory in digit order
 // and writes each digit's run to its global position.  Keys and payloads
 // are read and written once per pass.
+//
+// The canonical reorder of a result table (reorder_rows) runs the same passes
+// with the ends fused: the first pass packs each row's key from the table's
+// columns itself (payload = row index), and the last pass writes the sorted
+// table's columns directly (key fields unpacked, other columns gathered
+// through the payload), so no key array is packed or unpacked separately.
 #include "common.cuh"
+#include "join.cuh"
 
 namespace gs {
 namespace {
@@ -47,35 +54,186 @@ __device__ __forceinline__ unsigned long long desc_pack(uint32_t epoch, uint64_t
     return ((unsigned long long)epoch << 56) | (state << 54) | value;
 }
 
-template <class K>
-__global__ void __launch_bounds__(kBlock) onesweep_histogram(const K *__restrict__ keys, int64_t n, int begin_bit,
-                                                            int end_bit, int n_pass, uint32_t *__restrict__ hist) {
-    extern __shared__ uint32_t hsm[];  // [kWarps][n_pass][kBins]
-    const int per_warp = n_pass * kBins;
-    for (int i = threadIdx.x; i < kWarps * per_warp; i += kBlock) hsm[i] = 0;
-    __syncthreads();
-    uint32_t *wh = hsm + (threadIdx.x >> 5) * per_warp;
-    for (int64_t i = blockIdx.x * (int64_t)kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
-        const K k = __ldg(keys + i);
-        for (int p = 0; p < n_pass; ++p) {
-            const int shift = begin_bit + 8 * p;
-            const int width = end_bit - shift < 8 ? end_bit - shift : 8;
-            atomicAdd(&wh[p * kBins + digit_of(k, shift, (1 << width) - 1)], 1u);
+// Key sources and sinks of a pass.  A source yields the key and payload of
+// input position i; a sink stores the sorted key and payload at position dst.
+// Key sources and sinks of a pass.  A source loads a thread's ITEMS keys and
+// payloads of a tile (input positions t0 + base + 32 j, those below `valid`);
+// a sink stores a sorted key and payload at position dst.
+template <class K, bool HasVals>
+struct SrcArray {
+    const K *keys;
+    const uint32_t *vals;
+    template <int ITEMS>
+    __device__ __forceinline__ void load_tile(int64_t t0, int base, int valid, K (&k)[ITEMS],
+                                              uint32_t (&v)[ITEMS]) const {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = base + 32 * j;
+            if (idx < valid) {
+                k[j] = keys[t0 + idx];
+                v[j] = HasVals ? vals[t0 + idx] : 0u;
+            }
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < per_warp; i += kBlock) {
-        uint32_t s = 0;
+    // keys base + stride * j (those below n), all loads in flight together
+    template <int H>
+    __device__ __forceinline__ void hist_keys(int64_t base, int stride, int64_t n, K (&k)[H]) const {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += hsm[w * per_warp + i];
-        if (s) atomicAdd(hist + i, s);
+        for (int j = 0; j < H; ++j) k[j] = base + (int64_t)stride * j < n ? __ldg(keys + base + (int64_t)stride * j) : K(0);
+    }
+};
+
+// Rows of a column table: key = the fields of columns c[0..nc-1] of row r
+// (most significant first, `bits` each), payload = r, where r = perm[i] (a
+// permutation of 0..n-1) or i.  A tile's loads go column by column with all
+// of a thread's rows in flight together.
+//
+// With idx_bits > 0 the row index rides in the key's low idx_bits bits
+// instead of a separate payload (fields << idx_bits | r), so a pass moves 8
+// bytes per row instead of 12; the passes then sort bits from idx_bits up.
+struct SrcRows {
+    const int32_t *c[kMaxCols];
+    const uint32_t *perm;
+    int nc;
+    int bits;
+    int idx_bits;
+    template <int ITEMS>
+    __device__ __forceinline__ void load_tile(int64_t t0, int base, int valid, uint64_t (&k)[ITEMS],
+                                              uint32_t (&v)[ITEMS]) const {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = base + 32 * j;
+            v[j] = idx < valid ? (perm ? __ldg(perm + t0 + idx) : (uint32_t)(t0 + idx)) : 0u;
+            k[j] = 0;
+        }
+        for (int cc = 0; cc < nc; ++cc) {
+            const int32_t *col = c[cc];
+            uint32_t x[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) x[j] = base + 32 * j < valid ? (uint32_t)__ldg(col + v[j]) : 0u;
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) k[j] = (k[j] << bits) | x[j];
+        }
+        if (idx_bits) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) k[j] = (k[j] << idx_bits) | v[j];
+        }
+    }
+    // digit counts do not depend on the order, so the histogram reads the
+    // columns in place (fields only: pass p's digit is bits [8p, 8p + 8) of
+    // the fields, at idx_bits + 8p in a packed key)
+    template <int H>
+    __device__ __forceinline__ void hist_keys(int64_t base, int stride, int64_t n, uint64_t (&k)[H]) const {
+#pragma unroll
+        for (int j = 0; j < H; ++j) k[j] = 0;
+        for (int cc = 0; cc < nc; ++cc) {
+            const int32_t *col = c[cc];
+            uint32_t x[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                const int64_t i = base + (int64_t)stride * j;
+                x[j] = i < n ? (uint32_t)__ldg(col + i) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < H; ++j) k[j] = (k[j] << bits) | x[j];
+        }
+    }
+};
+
+template <class K, bool HasVals>
+struct SinkArray {
+    K *keys;
+    uint32_t *vals;
+    __device__ __forceinline__ void store(uint32_t dst, K k, uint32_t v) const {
+        keys[dst] = k;
+        if (HasVals) vals[dst] = v;
+    }
+};
+
+// Payload only (the permutation a later chunk starts from).
+struct SinkPerm {
+    uint32_t *vals;
+    int idx_bits;  // > 0: the payload is the key's low idx_bits bits
+    __device__ __forceinline__ void store(uint32_t dst, uint64_t k, uint32_t v) const {
+        vals[dst] = idx_bits ? (uint32_t)(k & ((1ull << idx_bits) - 1)) : v;
+    }
+};
+
+// The sorted table's leading columns: out[0..k0-1] unpacked from the key;
+// the payload goes to perm (when not null) for the gather of the other
+// columns, which runs as its own kernel at full occupancy.
+struct SinkRows {
+    int32_t *out[kMaxCols];
+    uint32_t *perm;
+    int k0;
+    int bits;
+    int idx_bits;  // > 0: the payload is the key's low idx_bits bits
+    __device__ __forceinline__ void store(uint32_t dst, uint64_t k, uint32_t v) const {
+        const uint64_t fmask = (1ull << bits) - 1;
+        const uint64_t f = k >> idx_bits;
+        for (int j = 0; j < k0; ++j) out[j][dst] = (int32_t)((f >> ((k0 - 1 - j) * bits)) & fmask);
+        if (perm) perm[dst] = idx_bits ? (uint32_t)(k & ((1ull << idx_bits) - 1)) : v;
+    }
+};
+
+// out[j][i] = rest[j][perm[i]]: each thread keeps kGatherRows rows' loads of
+// a column in flight.
+constexpr int kGatherRows = 4;
+__global__ void __launch_bounds__(256) gather_rest_kernel(Cols rest, OutCols out, int n_rest,
+                                                          const uint32_t *__restrict__ perm, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += stride * kGatherRows) {
+        uint32_t r[kGatherRows];
+#pragma unroll
+        for (int u = 0; u < kGatherRows; ++u) {
+            const int64_t i = i0 + u * stride;
+            r[u] = i < n ? __ldg(perm + i) : 0u;
+        }
+        for (int j = 0; j < n_rest; ++j) {
+            int32_t x[kGatherRows];
+#pragma unroll
+            for (int u = 0; u < kGatherRows; ++u) x[u] = i0 + u * stride < n ? __ldg(rest.c[j] + r[u]) : 0;
+#pragma unroll
+            for (int u = 0; u < kGatherRows; ++u) {
+                if (i0 + u * stride < n) out.c[j][i0 + u * stride] = x[u];
+            }
+        }
     }
 }
 
-template <class K, bool HasVals>
-__global__ void __launch_bounds__(kBlock, 4) onesweep_pass(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                                                       K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                                                       int64_t n, int shift, int mask,
+// Digit counts of every pass in one read of the keys: a CTA-wide shared
+// histogram per pass, each thread keeping kHistItems keys' loads in flight.
+constexpr int kHistItems = 8;
+template <class K, class Src>
+__global__ void __launch_bounds__(kBlock) onesweep_histogram(Src src, int64_t n, int begin_bit, int end_bit,
+                                                            int n_pass, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t hsm[kMaxPasses * kBins];
+    for (int i = threadIdx.x; i < n_pass * kBins; i += kBlock) hsm[i] = 0;
+    __syncthreads();
+    const int64_t span = (int64_t)kBlock * kHistItems;
+    for (int64_t base = blockIdx.x * span + threadIdx.x; base < n; base += (int64_t)gridDim.x * span) {
+        K k[kHistItems];
+        src.template hist_keys<kHistItems>(base, kBlock, n, k);
+#pragma unroll
+        for (int j = 0; j < kHistItems; ++j) {
+            if (base + (int64_t)kBlock * j < n) {
+                for (int p = 0; p < n_pass; ++p) {
+                    const int shift = begin_bit + 8 * p;
+                    const int width = end_bit - shift < 8 ? end_bit - shift : 8;
+                    atomicAdd(&hsm[p * kBins + digit_of(k[j], shift, (1 << width) - 1)], 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_pass * kBins; i += kBlock) {
+        const uint32_t c = hsm[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+}
+
+template <class K, bool HasVals, class Src, class Sink>
+__global__ void __launch_bounds__(kBlock, 4) onesweep_pass(Src src, Sink sink, int64_t n, int shift, int mask,
                                                        const uint32_t *__restrict__ hist_pass,
                                                        unsigned long long *__restrict__ desc,
                                                        unsigned int *__restrict__ tile_counter, uint32_t epoch,
@@ -104,13 +262,12 @@ __global__ void __launch_bounds__(kBlock, 4) onesweep_pass(const K *__restrict__
     K k[ITEMS];
     uint32_t v[ITEMS];
     uint32_t dr[ITEMS];  // rank within the warp << 8 | digit
+    // warp-striped: stable order inside the tile is (warp, j, lane)
+    src.template load_tile<ITEMS>(t0, warp * (32 * ITEMS) + lane, valid, k, v);
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        // warp-striped: stable order inside the tile is (warp, j, lane)
         const int idx = warp * (32 * ITEMS) + j * 32 + lane;
         if (idx < valid) {
-            k[j] = keys_in[t0 + idx];
-            v[j] = HasVals ? vals_in[t0 + idx] : 0u;
             dr[j] = (uint32_t)digit_of(k[j], shift, mask);
         } else {
             k[j] = ~K(0);
@@ -187,8 +344,7 @@ __global__ void __launch_bounds__(kBlock, 4) onesweep_pass(const K *__restrict__
         const K kk = skeys[i];
         const int dd = digit_of(kk, shift, mask);
         const uint32_t dst = gbase[dd] + ((uint32_t)i - tstart[dd]);
-        keys_out[dst] = kk;
-        if (HasVals) vals_out[dst] = svals[i];
+        sink.store(dst, kk, HasVals ? svals[i] : 0u);
     }
 }
 
@@ -214,20 +370,94 @@ int pass_smem_bytes() {
     return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kWarps * kBins + 2 * kBins) * 4;
 }
 
-template <class K, bool HasVals>
-int set_pass_attributes() {
-    static bool done[64] = {false};
+int current_device() {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
+    return (dev < 0 || dev >= 64) ? 0 : dev;
+}
+
+template <class K, bool HasVals, class Src, class Sink>
+int launch_pass(const Src &src, const Sink &sink, int64_t n, int shift, int width, const uint32_t *hist_pass,
+                unsigned long long *desc, unsigned int *counter, uint32_t epoch, int *err, cudaStream_t st) {
+    static bool done[64] = {false};
+    const int dev = current_device();
     if (!done[dev]) {
-        GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      pass_smem_bytes<K, HasVals>()));
-        GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     cudaSharedmemCarveoutMaxShared));
-        GS_CUDA(cudaFuncSetAttribute(onesweep_histogram<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kWarps * kMaxPasses * kBins * 4));
+        GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
         done[dev] = true;
+    }
+    constexpr int TILE = kBlock * SortTraits<K>::kItems;
+    const int64_t ntiles = (n + TILE - 1) / TILE;
+    onesweep_pass<K, HasVals, Src, Sink><<<(unsigned)ntiles, kBlock, pass_smem_bytes<K, HasVals>(), st>>>(
+        src, sink, n, shift, (1 << width) - 1, hist_pass, desc, counter, epoch, err);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+template <class K, class Src>
+int launch_histogram(const Src &src, int64_t n, int begin_bit, int end_bit, int n_pass, uint32_t *hist,
+                     cudaStream_t st) {
+    const int64_t span = (int64_t)kBlock * kHistItems;
+    int64_t g = (n + span - 1) / span;
+    const int64_t cap = (int64_t)sm_count() * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    onesweep_histogram<K, Src><<<(unsigned)g, kBlock, 0, st>>>(src, n, begin_bit, end_bit, n_pass, hist);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+// Per-sort scratch: digit histograms | tile counters | error word | tile
+// descriptors, zeroed by one memset.
+struct SortMeta {
+    DevBuf buf;
+    uint32_t *hist = nullptr;
+    unsigned int *counters = nullptr;
+    int *err = nullptr;
+    unsigned long long *desc = nullptr;
+
+    int make(int64_t n, int n_pass, int tile, cudaStream_t st, int *err_word) {
+        const int64_t ntiles = (n + tile - 1) / tile;
+        const size_t off_cnt = round_up(sizeof(uint32_t) * kBins * n_pass, 256);
+        const size_t off_err = off_cnt + sizeof(uint32_t) * kMaxPasses;
+        const size_t off_desc = round_up(off_err + sizeof(int), 256);
+        const size_t bytes = off_desc + sizeof(unsigned long long) * kBins * (size_t)ntiles;
+        GS_TRY(buf.alloc(bytes, st));
+        GS_CUDA(cudaMemsetAsync(buf.p, 0, bytes, st));
+        hist = buf.as<uint32_t>();
+        counters = reinterpret_cast<unsigned int *>(buf.as<char>() + off_cnt);
+        err = err_word ? err_word : reinterpret_cast<int *>(buf.as<char>() + off_err);
+        desc = reinterpret_cast<unsigned long long *>(buf.as<char>() + off_desc);
+        return GSMAT_OK;
+    }
+};
+
+template <class K, bool HasVals>
+int sort_passes(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word) {
+    const int n_pass = (end_bit - begin_bit + 7) / 8;
+    SortMeta meta;
+    GS_TRY(meta.make(n, n_pass, kBlock * SortTraits<K>::kItems, st, err_word));
+    DevBuf alt_k, alt_v;
+    GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
+    if (HasVals) GS_TRY(alt_v.alloc(sizeof(uint32_t) * (size_t)n, st));
+    GS_TRY((launch_histogram<K, SrcArray<K, HasVals>>(SrcArray<K, HasVals>{keys, vals}, n, begin_bit, end_bit, n_pass,
+                                                     meta.hist, st)));
+    K *src_k = keys, *dst_k = alt_k.as<K>();
+    uint32_t *src_v = vals, *dst_v = alt_v.as<uint32_t>();
+    for (int p = 0; p < n_pass; ++p) {
+        const int shift = begin_bit + 8 * p;
+        const int width = end_bit - shift < 8 ? end_bit - shift : 8;
+        GS_TRY((launch_pass<K, HasVals, SrcArray<K, HasVals>, SinkArray<K, HasVals>>(
+            SrcArray<K, HasVals>{src_k, src_v}, SinkArray<K, HasVals>{dst_k, dst_v}, n, shift, width,
+            meta.hist + p * kBins, meta.desc, meta.counters + p, (uint32_t)(p + 1), meta.err, st)));
+        K *tk = src_k; src_k = dst_k; dst_k = tk;
+        uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
+    }
+    if (src_k != keys) {
+        GS_CUDA(cudaMemcpyAsync(keys, src_k, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        if (HasVals) GS_CUDA(cudaMemcpyAsync(vals, src_v, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     }
     return GSMAT_OK;
 }
@@ -241,61 +471,42 @@ int radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_b
     }
     if (n <= 1 || begin_bit == end_bit) return GSMAT_OK;
     if (n > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "radix sort: n = %lld >= 2^32", (long long)n);
-    constexpr int TILE = kBlock * SortTraits<K>::kItems;
-    const int64_t ntiles = (n + TILE - 1) / TILE;
     const int n_pass = (end_bit - begin_bit + 7) / 8;
-    const int attr_rc = vals ? set_pass_attributes<K, true>() : set_pass_attributes<K, false>();
-    if (attr_rc != GSMAT_OK) return attr_rc;
-
-    // scratch: digit histograms | tile counters | error word | descriptors
-    const size_t off_cnt = round_up(sizeof(uint32_t) * kBins * n_pass, 256);
-    const size_t off_err = off_cnt + sizeof(uint32_t) * kMaxPasses;
-    const size_t off_desc = round_up(off_err + sizeof(int), 256);
-    const size_t meta_bytes = off_desc + sizeof(unsigned long long) * kBins * (size_t)ntiles;
-    DevBuf alt_k, alt_v, meta;
-    GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
-    if (vals) GS_TRY(alt_v.alloc(sizeof(uint32_t) * (size_t)n, st));
-    GS_TRY(meta.alloc(meta_bytes, st));
-    GS_CUDA(cudaMemsetAsync(meta.p, 0, meta_bytes, st));
-    uint32_t *hist = meta.as<uint32_t>();
-    unsigned int *counters = reinterpret_cast<unsigned int *>(meta.as<char>() + off_cnt);
-    int *err = err_word ? err_word : reinterpret_cast<int *>(meta.as<char>() + off_err);
-    unsigned long long *desc = reinterpret_cast<unsigned long long *>(meta.as<char>() + off_desc);
-
     KernelTimer t(timer_name, st, (double)n * (2.0 * sizeof(K) + (vals ? 8.0 : 0.0)) * n_pass, (double)n);
-    {
-        int64_t g = (n + kBlock * 16 - 1) / (kBlock * 16);
-        const int64_t cap = (int64_t)sm_count() * 2;
-        if (g > cap) g = cap;
-        if (g < 1) g = 1;
-        onesweep_histogram<K><<<(unsigned)g, kBlock, kWarps * n_pass * kBins * 4, st>>>(keys, n, begin_bit, end_bit,
-                                                                                        n_pass, hist);
-        GS_LAUNCH_CHECK();
-    }
-    K *src_k = keys, *dst_k = alt_k.as<K>();
-    uint32_t *src_v = vals, *dst_v = alt_v.as<uint32_t>();
-    for (int p = 0; p < n_pass; ++p) {
-        const int shift = begin_bit + 8 * p;
-        const int width = end_bit - shift < 8 ? end_bit - shift : 8;
-        const int mask = (1 << width) - 1;
-        if (vals) {
-            onesweep_pass<K, true><<<(unsigned)ntiles, kBlock, pass_smem_bytes<K, true>(), st>>>(
-                src_k, src_v, dst_k, dst_v, n, shift, mask, hist + p * kBins, desc, counters + p, (uint32_t)(p + 1), err);
-        } else {
-            onesweep_pass<K, false><<<(unsigned)ntiles, kBlock, pass_smem_bytes<K, false>(), st>>>(
-                src_k, nullptr, dst_k, nullptr, n, shift, mask, hist + p * kBins, desc, counters + p, (uint32_t)(p + 1),
-                err);
-        }
-        GS_LAUNCH_CHECK();
-        K *tk = src_k; src_k = dst_k; dst_k = tk;
-        uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
-    }
+    const int rc = vals ? sort_passes<K, true>(keys, vals, n, begin_bit, end_bit, st, err_word)
+                        : sort_passes<K, false>(keys, nullptr, n, begin_bit, end_bit, st, err_word);
+    if (rc != GSMAT_OK) return rc;
     t.stop();
-    if (src_k != keys) {
-        GS_CUDA(cudaMemcpyAsync(keys, src_k, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        if (vals) GS_CUDA(cudaMemcpyAsync(vals, src_v, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    }
     return GSMAT_OK;
+}
+
+// One pass of a row sort, with the source and sink the pass's place calls for.
+template <bool HasVals>
+int row_pass(bool first, bool last, bool final_chunk, const SrcRows &rows, const SinkRows &out, const SinkPerm &perm,
+             const uint64_t *sk, const uint32_t *sv, uint64_t *dk, uint32_t *dv, int64_t n, int shift, int width,
+             const uint32_t *hist_pass, unsigned long long *desc, unsigned int *counter, uint32_t epoch, int *err,
+             cudaStream_t st) {
+    using SA = SrcArray<uint64_t, HasVals>;
+    using KA = SinkArray<uint64_t, HasVals>;
+    const SA arr{sk, sv};
+    const KA to{dk, dv};
+    if (first && last) {
+        return final_chunk ? launch_pass<uint64_t, HasVals, SrcRows, SinkRows>(rows, out, n, shift, width, hist_pass,
+                                                                               desc, counter, epoch, err, st)
+                           : launch_pass<uint64_t, HasVals, SrcRows, SinkPerm>(rows, perm, n, shift, width, hist_pass,
+                                                                               desc, counter, epoch, err, st);
+    }
+    if (first) {
+        return launch_pass<uint64_t, HasVals, SrcRows, KA>(rows, to, n, shift, width, hist_pass, desc, counter, epoch,
+                                                           err, st);
+    }
+    if (last) {
+        return final_chunk ? launch_pass<uint64_t, HasVals, SA, SinkRows>(arr, out, n, shift, width, hist_pass, desc,
+                                                                          counter, epoch, err, st)
+                           : launch_pass<uint64_t, HasVals, SA, SinkPerm>(arr, perm, n, shift, width, hist_pass, desc,
+                                                                          counter, epoch, err, st);
+    }
+    return launch_pass<uint64_t, HasVals, SA, KA>(arr, to, n, shift, width, hist_pass, desc, counter, epoch, err, st);
 }
 
 }  // namespace
@@ -308,6 +519,114 @@ int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
                    int *err_word) {
     return radix_sort_impl<uint32_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u32", err_word);
+}
+
+int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutCols &out, cudaStream_t st,
+                 int *err_word) {
+    if (V < 1 || V > kMaxCols || m < 1 || m > V || bits < 1 || bits > 31 || n < 0) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "reorder: V=%d m=%d bits=%d n=%lld", V, m, bits, (long long)n);
+    }
+    if (n == 0) return GSMAT_OK;
+    if (n > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "reorder: n = %lld >= 2^32", (long long)n);
+    const int per_key = 64 / bits;
+    const int n_chunks = (m + per_key - 1) / per_key;
+    const int k0 = m < per_key ? m : per_key;
+    DevBuf ka, kb, va, vb, pa, pb;
+    GS_TRY(ka.alloc(sizeof(uint64_t) * (size_t)n, st));
+    GS_TRY(kb.alloc(sizeof(uint64_t) * (size_t)n, st));
+    GS_TRY(va.alloc(sizeof(uint32_t) * (size_t)n, st));
+    GS_TRY(vb.alloc(sizeof(uint32_t) * (size_t)n, st));
+    if (n_chunks > 1) {
+        GS_TRY(pa.alloc(sizeof(uint32_t) * (size_t)n, st));
+        GS_TRY(pb.alloc(sizeof(uint32_t) * (size_t)n, st));
+    }
+    const int n_rest = V - k0;
+    // row index width for keys that carry it in their low bits
+    const int idx_bits = std::max(1, bits_for((uint64_t)(n - 1)));
+    // algorithmic bytes: the histogram reads the key columns; the first pass
+    // reads them (and the previous chunk's permutation); the last writes the
+    // permutation, or the k0 leading output columns and (when other columns
+    // follow) the payload, which the gather reads back with the n_rest
+    // gathered values and writes n_rest columns; every other transfer is a
+    // key and a payload
+    double algo = n_rest > 0 ? 4.0 + 8.0 * n_rest : 0.0;
+    for (int ci = n_chunks - 1; ci >= 0; --ci) {
+        const int nc = (ci * per_key + per_key < m ? per_key : m - ci * per_key);
+        const int n_pass = (nc * bits + 7) / 8;
+        const double e = nc * bits + idx_bits <= 64 ? 8.0 : 12.0;  // bytes of one row between passes
+        const double in0 = 4.0 * nc + (ci < n_chunks - 1 ? 4.0 : 0.0);
+        const double outl = ci == 0 ? 4.0 * k0 + (n_rest > 0 ? 4.0 : 0.0) : 4.0;
+        algo += 4.0 * nc + in0 + outl + (n_pass > 1 ? 2.0 * e : 0.0) + 2.0 * e * (n_pass > 2 ? n_pass - 2 : 0);
+    }
+    KernelTimer t("reorder_sort", st, algo * (double)n, (double)n);
+    const uint32_t *perm_in = nullptr;
+    const uint32_t *final_perm = nullptr;
+    for (int ci = n_chunks - 1; ci >= 0; --ci) {
+        const int b = ci * per_key;
+        const int e = m < b + per_key ? m : b + per_key;
+        const int nc = e - b;
+        const int key_bits = nc * bits;
+        const int n_pass = (key_bits + 7) / 8;
+        SrcRows src;
+        memset(&src, 0, sizeof(src));
+        for (int j = 0; j < nc; ++j) src.c[j] = cols.c[b + j];
+        src.perm = perm_in;
+        src.nc = nc;
+        src.bits = bits;
+        const bool packed = key_bits + idx_bits <= 64;
+        src.idx_bits = packed ? idx_bits : 0;
+        uint32_t *pout = ((n_chunks - 1 - ci) & 1) ? pb.as<uint32_t>() : pa.as<uint32_t>();
+        const SinkPerm sink_perm{pout, src.idx_bits};
+        SortMeta meta;
+        GS_TRY(meta.make(n, n_pass, kBlock * SortTraits<uint64_t>::kItems, st, err_word));
+        GS_TRY((launch_histogram<uint64_t, SrcRows>(src, n, 0, key_bits, n_pass, meta.hist, st)));
+        for (int p = 0; p < n_pass; ++p) {
+            const int shift = src.idx_bits + 8 * p;
+            const int width = key_bits - 8 * p < 8 ? key_bits - 8 * p : 8;
+            // pass p writes buffer set p & 1 and reads set (p - 1) & 1 (the
+            // last pass of the final chunk writes the output columns and
+            // its payload into set p & 1, which nothing reads then)
+            uint64_t *dk = (p & 1) ? kb.as<uint64_t>() : ka.as<uint64_t>();
+            uint32_t *dv = (p & 1) ? vb.as<uint32_t>() : va.as<uint32_t>();
+            const uint64_t *sk = (p & 1) ? ka.as<uint64_t>() : kb.as<uint64_t>();
+            const uint32_t *sv = (p & 1) ? va.as<uint32_t>() : vb.as<uint32_t>();
+            SinkRows sink_rows;
+            memset(&sink_rows, 0, sizeof(sink_rows));
+            for (int v = 0; v < k0; ++v) sink_rows.out[v] = out.c[v];
+            sink_rows.perm = n_rest > 0 ? dv : nullptr;
+            sink_rows.k0 = k0;
+            sink_rows.bits = bits;
+            sink_rows.idx_bits = src.idx_bits;
+            if (ci == 0 && p == n_pass - 1) final_perm = sink_rows.perm;
+            if (packed) {
+                GS_TRY(row_pass<false>(p == 0, p == n_pass - 1, ci == 0, src, sink_rows, sink_perm, sk, nullptr, dk,
+                                       nullptr, n, shift, width, meta.hist + p * kBins, meta.desc, meta.counters + p,
+                                       (uint32_t)(p + 1), meta.err, st));
+            } else {
+                GS_TRY(row_pass<true>(p == 0, p == n_pass - 1, ci == 0, src, sink_rows, sink_perm, sk, sv, dk, dv, n,
+                                      shift, width, meta.hist + p * kBins, meta.desc, meta.counters + p,
+                                      (uint32_t)(p + 1), meta.err, st));
+            }
+        }
+        perm_in = pout;
+    }
+    if (n_rest > 0) {
+        Cols rest;
+        OutCols ro;
+        memset(&rest, 0, sizeof(rest));
+        memset(&ro, 0, sizeof(ro));
+        for (int j = 0; j < n_rest; ++j) {
+            rest.c[j] = cols.c[k0 + j];
+            ro.c[j] = out.c[k0 + j];
+        }
+        int64_t g = (n + 256 * kGatherRows - 1) / (256 * kGatherRows);
+        const int64_t cap = (int64_t)sm_count() * 8;
+        if (g > cap) g = cap;
+        gather_rest_kernel<<<(unsigned)g, 256, 0, st>>>(rest, ro, n_rest, final_perm, n);
+        GS_LAUNCH_CHECK();
+    }
+    t.stop();
+    return GSMAT_OK;
 }
 
 int device_sm_count() { return sm_count(); }

@@ -99,3 +99,11 @@ def test_plan_on_tiny_workload(gs):
         keys = [s["nnz"] for s in stats]
         order, kinds, est = gs.plan(q, keys, stats)
         assert order == oplan.plan_order(q.patterns, keys)
+
+
+def test_lazy_package_names_resolve(gs):
+    import paper_1807_07691_b300 as pkg
+
+    for name in dir(pkg):
+        if name not in ("build", "gsmat"):
+            assert getattr(pkg, name) is getattr(gs, name), name

@@ -68,3 +68,47 @@ def test_scan_total_beyond_int32(env):
     want = np.concatenate([[0], np.cumsum(x, dtype=np.int64)])
     assert np.array_equal(out.cpu().numpy(), want)
     assert want[-1] > 2**31
+
+
+# (V, m, bits, n, value range): single chunk with gathered columns; two and
+# three chunks; a one-pass chunk that is not the last one sorted (SrcRows ->
+# permutation) and a one-pass final chunk; tile edges; narrow value ranges
+# so that equal keys are common and stability decides the order.
+SORT_ROWS_CASES = [
+    (3, 1, 20, 100_000, 1 << 20),
+    (5, 4, 20, 300_001, 1 << 20),
+    (5, 4, 20, 300_001, 3),
+    (4, 4, 3, 50_000, 8),
+    (1, 1, 5, 10_000, 32),
+    (2, 1, 5, 3073, 32),
+    (6, 6, 31, 70_000, 1 << 31),
+    (24, 23, 3, 20_000, 8),
+    (3, 2, 17, 0, 1),
+    (3, 2, 17, 1, 1 << 17),
+    (3, 2, 17, 2, 1 << 17),
+    (2, 2, 12, 3071, 1 << 12),
+    (2, 2, 12, 3072, 1 << 12),
+]
+
+
+@pytest.mark.parametrize("V,m,bits,n,hi", SORT_ROWS_CASES)
+def test_sort_rows_matches_stable_lexsort(env, V, m, bits, n, hi):
+    g, torch = env
+    rng = np.random.default_rng(V * 1000 + m * 100 + bits + n)
+    cols = [rng.integers(0, hi, size=n, dtype=np.int64).astype(np.int32) for _ in range(V)]
+    d = [torch.from_numpy(c.copy()).cuda() for c in cols]
+    out = g.sort_rows(d, m, bits)
+    torch.cuda.synchronize()
+    # np.lexsort is stable and takes its primary key last
+    order = np.lexsort(cols[m - 1::-1]) if n else np.zeros(0, np.int64)
+    for v in range(V):
+        assert np.array_equal(out[v].cpu().numpy(), cols[v][order]), v
+
+
+def test_sort_rows_rejects_bad_arguments(env):
+    g, torch = env
+    c = [torch.zeros(4, dtype=torch.int32, device="cuda") for _ in range(2)]
+    for m, bits in ((3, 8), (0, 8), (1, 0), (1, 32)):
+        with pytest.raises(g.GsmatError) as e:
+            g.sort_rows(c, m, bits)
+        assert e.value.code == 1
