@@ -176,11 +176,61 @@ struct SinkRows {
     }
 };
 
-// out[j][i] = rest[j][perm[i]]: each thread keeps kGatherRows rows' loads of
-// a column in flight.
+// Gather of the non-key columns after the sort.  When consecutive output
+// rows come from scattered input rows, reading each column costs one 32-byte
+// sector per value; the columns are then first interleaved into records
+// rec[i] = (rest[0][i], ..., rest[n_rest-1][i]) of rw int4 words
+// (n_rest <= 4 * rw <= 8, zero padding), and the gather reads one sector per
+// row.  When the permutation keeps runs of consecutive rows (trailing plan
+// variables fan out inside each key group), the columns are read directly.
+//
+// *use_rec = 1 unless at least half of kLocalitySamples evenly spaced
+// positions i have |perm[i + 1] - perm[i]| <= 8 (same or next sector).
+constexpr int kLocalitySamples = 4096;
+__global__ void __launch_bounds__(256) perm_locality_kernel(const uint32_t *__restrict__ perm, int64_t n,
+                                                            int *__restrict__ use_rec) {
+    __shared__ int64_t tmp[9];
+    constexpr int kPer = kLocalitySamples / 256;
+    uint32_t a[kPer], b[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int64_t k = threadIdx.x + 256 * u;
+        const int64_t i = n > 1 ? k * (n - 2) / (kLocalitySamples - 1) : 0;
+        a[u] = i + 1 < n ? __ldg(perm + i) : 0u;
+        b[u] = i + 1 < n ? __ldg(perm + i + 1) : 0u;
+    }
+    int local = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+        const int64_t d = (int64_t)b[u] - (int64_t)a[u];
+        local += (n > 1 && d >= -8 && d <= 8) ? 1 : 0;
+    }
+    int64_t total;
+    block_exclusive_sum<256>((int64_t)local, tmp, &total);
+    if (threadIdx.x == 0) *use_rec = 2 * total < kLocalitySamples ? 1 : 0;
+}
+
+// Runs only when *use_rec is set (by perm_locality_kernel).
+constexpr int kMaxRecCols = 8;
+__global__ void __launch_bounds__(256) interleave_rest_kernel(Cols rest, int n_rest, int rw, int64_t n,
+                                                              const int *__restrict__ use_rec,
+                                                              int4 *__restrict__ rec) {
+    if (!*use_rec) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int x[kMaxRecCols];
+#pragma unroll
+        for (int j = 0; j < kMaxRecCols; ++j) x[j] = j < n_rest ? __ldg(rest.c[j] + i) : 0;
+        rec[i * rw] = make_int4(x[0], x[1], x[2], x[3]);
+        if (rw > 1) rec[i * rw + 1] = make_int4(x[4], x[5], x[6], x[7]);
+    }
+}
+
+// Each gather thread keeps kGatherRows rows' loads in flight.
 constexpr int kGatherRows = 4;
-__global__ void __launch_bounds__(256) gather_rest_kernel(Cols rest, OutCols out, int n_rest,
-                                                          const uint32_t *__restrict__ perm, int64_t n) {
+
+// out[j][i] = rest[j][perm[i]], column by column.
+__device__ __forceinline__ void gather_columns(const Cols &rest, const OutCols &out, int n_rest,
+                                               const uint32_t *__restrict__ perm, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += stride * kGatherRows) {
         uint32_t r[kGatherRows];
@@ -199,6 +249,101 @@ __global__ void __launch_bounds__(256) gather_rest_kernel(Cols rest, OutCols out
             }
         }
     }
+}
+
+// out[j][i] = field j of rec[perm[i]]; runs only when *use_rec is set (the
+// column gather runs otherwise, as its own kernel so that each keeps its
+// own register budget and occupancy).
+__global__ void __launch_bounds__(256) gather_rec_kernel(const int4 *__restrict__ rec, int rw,
+                                                         const int *__restrict__ use_rec, int n_rest, OutCols out,
+                                                         const uint32_t *__restrict__ perm, int64_t n) {
+    if (!*use_rec) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += stride * kGatherRows) {
+        int4 a[kGatherRows], b[kGatherRows];
+#pragma unroll
+        for (int u = 0; u < kGatherRows; ++u) {
+            const int64_t i = i0 + u * stride;
+            const uint32_t r = i < n ? __ldg(perm + i) : 0u;
+            a[u] = i < n ? __ldg(rec + (int64_t)r * rw) : make_int4(0, 0, 0, 0);
+            b[u] = (i < n && rw > 1) ? __ldg(rec + (int64_t)r * rw + 1) : make_int4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kGatherRows; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                const int x[kMaxRecCols] = {a[u].x, a[u].y, a[u].z, a[u].w, b[u].x, b[u].y, b[u].z, b[u].w};
+#pragma unroll
+                for (int j = 0; j < kMaxRecCols; ++j) {
+                    if (j < n_rest) out.c[j][i] = x[j];
+                }
+            }
+        }
+    }
+}
+
+// Reorder of a small table (n <= kSmallSortRows, the m key columns packed
+// in at most two 64-bit words) by one CTA: bitonic sort of (key, row) in
+// shared memory (the row breaks ties, so the order is the stable one), then
+// the output columns, key columns unpacked and the others gathered.
+constexpr int kSmallSortRows = 2048;
+constexpr int kSmallSortBlock = 1024;
+__global__ void __launch_bounds__(kSmallSortBlock) small_reorder_kernel(Cols cols, int V, int m, int k0, int bits,
+                                                                        int n, OutCols out) {
+    __shared__ unsigned long long s0[kSmallSortRows], s1[kSmallSortRows];
+    __shared__ uint16_t si[kSmallSortRows];
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += kSmallSortBlock) {
+        unsigned long long w0 = ~0ull, w1 = ~0ull;
+        if (i < n) {
+            w0 = 0;
+            w1 = 0;
+            for (int j = 0; j < k0; ++j) w0 = (w0 << bits) | (uint32_t)__ldg(cols.c[j] + i);
+            for (int j = k0; j < m; ++j) w1 = (w1 << bits) | (uint32_t)__ldg(cols.c[j] + i);
+        }
+        s0[i] = w0;
+        s1[i] = w1;
+        si[i] = (uint16_t)(i < n ? i : 0xffff);
+    }
+    __syncthreads();
+    for (int size = 2; size <= n2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += kSmallSortBlock) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long ai = s0[i], aj = s0[j], bi = s1[i], bj = s1[j];
+                    const uint16_t ii = si[i], ij = si[j];
+                    const bool gt = ai > aj || (ai == aj && (bi > bj || (bi == bj && ii > ij)));
+                    if (gt == up) {
+                        s0[i] = aj;
+                        s0[j] = ai;
+                        s1[i] = bj;
+                        s1[j] = bi;
+                        si[i] = ij;
+                        si[j] = ii;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const unsigned long long fmask = (1ull << bits) - 1;
+    for (int i = threadIdx.x; i < n; i += kSmallSortBlock) {
+        const int r = si[i];
+        for (int j = 0; j < k0; ++j) out.c[j][i] = (int32_t)((s0[i] >> ((k0 - 1 - j) * bits)) & fmask);
+        for (int j = k0; j < m; ++j) out.c[j][i] = (int32_t)((s1[i] >> ((m - 1 - j) * bits)) & fmask);
+        for (int j = m; j < V; ++j) out.c[j][i] = __ldg(cols.c[j] + r);
+    }
+}
+
+// The column gather; with use_rec given, runs only when *use_rec is clear.
+__global__ void __launch_bounds__(256) gather_rest_kernel(Cols rest, OutCols out, int n_rest,
+                                                          const uint32_t *__restrict__ perm, int64_t n,
+                                                          const int *__restrict__ use_rec) {
+    if (use_rec && *use_rec) return;
+    gather_columns(rest, out, n_rest, perm, n);
 }
 
 // Digit counts of every pass in one read of the keys: a CTA-wide shared
@@ -531,6 +676,13 @@ int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutC
     const int per_key = 64 / bits;
     const int n_chunks = (m + per_key - 1) / per_key;
     const int k0 = m < per_key ? m : per_key;
+    if (n <= kSmallSortRows && n_chunks <= 2) {
+        KernelTimer t("reorder_sort", st, (8.0 * V) * (double)n, (double)n);
+        small_reorder_kernel<<<1, kSmallSortBlock, 0, st>>>(cols, V, m, k0, bits, (int)n, out);
+        GS_LAUNCH_CHECK();
+        t.stop();
+        return GSMAT_OK;
+    }
     DevBuf ka, kb, va, vb, pa, pb;
     GS_TRY(ka.alloc(sizeof(uint64_t) * (size_t)n, st));
     GS_TRY(kb.alloc(sizeof(uint64_t) * (size_t)n, st));
@@ -559,6 +711,16 @@ int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutC
         algo += 4.0 * nc + in0 + outl + (n_pass > 1 ? 2.0 * e : 0.0) + 2.0 * e * (n_pass > 2 ? n_pass - 2 : 0);
     }
     KernelTimer t("reorder_sort", st, algo * (double)n, (double)n);
+    // the columns gathered after the sort, as records when they fit one
+    Cols rest;
+    OutCols ro;
+    memset(&rest, 0, sizeof(rest));
+    memset(&ro, 0, sizeof(ro));
+    for (int j = 0; j < n_rest; ++j) {
+        rest.c[j] = cols.c[k0 + j];
+        ro.c[j] = out.c[k0 + j];
+    }
+    const int rw = n_rest == 0 ? 0 : (n_rest <= 4 ? 1 : (n_rest <= kMaxRecCols ? 2 : 0));
     const uint32_t *perm_in = nullptr;
     const uint32_t *final_perm = nullptr;
     for (int ci = n_chunks - 1; ci >= 0; --ci) {
@@ -611,18 +773,24 @@ int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutC
         perm_in = pout;
     }
     if (n_rest > 0) {
-        Cols rest;
-        OutCols ro;
-        memset(&rest, 0, sizeof(rest));
-        memset(&ro, 0, sizeof(ro));
-        for (int j = 0; j < n_rest; ++j) {
-            rest.c[j] = cols.c[k0 + j];
-            ro.c[j] = out.c[k0 + j];
-        }
         int64_t g = (n + 256 * kGatherRows - 1) / (256 * kGatherRows);
         const int64_t cap = (int64_t)sm_count() * 8;
         if (g > cap) g = cap;
-        gather_rest_kernel<<<(unsigned)g, 256, 0, st>>>(rest, ro, n_rest, final_perm, n);
+        if (rw > 0) {
+            DevBuf rec, flag;
+            GS_TRY(rec.alloc(sizeof(int4) * (size_t)rw * (size_t)n, st));
+            GS_TRY(flag.alloc(sizeof(int), st));
+            perm_locality_kernel<<<1, 256, 0, st>>>(final_perm, n, flag.as<int>());
+            GS_LAUNCH_CHECK();
+            interleave_rest_kernel<<<grid_1d(n, 256), 256, 0, st>>>(rest, n_rest, rw, n, flag.as<int>(), rec.as<int4>());
+            GS_LAUNCH_CHECK();
+            gather_rec_kernel<<<(unsigned)g, 256, 0, st>>>(rec.as<int4>(), rw, flag.as<int>(), n_rest, ro, final_perm,
+                                                           n);
+            GS_LAUNCH_CHECK();
+            gather_rest_kernel<<<(unsigned)g, 256, 0, st>>>(rest, ro, n_rest, final_perm, n, flag.as<int>());
+        } else {
+            gather_rest_kernel<<<(unsigned)g, 256, 0, st>>>(rest, ro, n_rest, final_perm, n, nullptr);
+        }
         GS_LAUNCH_CHECK();
     }
     t.stop();

@@ -73,7 +73,10 @@ def test_scan_total_beyond_int32(env):
 # (V, m, bits, n, value range): single chunk with gathered columns; two and
 # three chunks; a one-pass chunk that is not the last one sorted (SrcRows ->
 # permutation) and a one-pass final chunk; tile edges; narrow value ranges
-# so that equal keys are common and stability decides the order.
+# so that equal keys are common and stability decides the order; both sides
+# of the one-CTA size limit (2048 rows, keys of up to two words); gathered
+# columns as one- and two-word records, as separate columns (more than
+# eight), and read in place when the permutation keeps runs (all keys equal).
 SORT_ROWS_CASES = [
     (3, 1, 20, 100_000, 1 << 20),
     (5, 4, 20, 300_001, 1 << 20),
@@ -88,6 +91,14 @@ SORT_ROWS_CASES = [
     (3, 2, 17, 2, 1 << 17),
     (2, 2, 12, 3071, 1 << 12),
     (2, 2, 12, 3072, 1 << 12),
+    (6, 6, 31, 5000, 1 << 31),
+    (10, 2, 20, 50_000, 1 << 20),
+    (12, 1, 20, 40_000, 1 << 20),
+    (7, 3, 20, 2048, 50),
+    (7, 3, 20, 2049, 50),
+    (6, 5, 20, 1500, 1 << 20),
+    (6, 6, 20, 2000, 4),
+    (5, 1, 20, 100_000, 1),
 ]
 
 
