@@ -158,6 +158,53 @@ __device__ __forceinline__ int2 row_range(const SideView &sv, const PredSide &ps
     return make_int2(0, 0);
 }
 
+// row_range for N values at once, with every lookup's loads in flight
+// together: the dense pointers' loads, or the binary searches advanced in
+// lockstep (one independent load per value per step).  ok[j] false: r[j] =
+// (0, 0).
+template <int N>
+__device__ __forceinline__ void row_ranges(const SideView &sv, const PredSide &ps, const int32_t (&x)[N],
+                                           const bool (&ok)[N], int2 (&r)[N]) {
+    if (ps.nnz == 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) r[j] = make_int2(0, 0);
+        return;
+    }
+    if (ps.dense_base >= 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const bool in = ok[j] && x[j] >= 0 && x[j] <= sv.max_entity;
+            const int32_t *rp = sv.dense + ps.dense_base + (in ? x[j] : 0);
+            r[j] = in ? make_int2(__ldg(rp), __ldg(rp + 1)) : make_int2(0, 0);
+        }
+        return;
+    }
+    const int32_t *ids = sv.rowid + ps.row_base;
+    int lo[N], hi[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        lo[j] = 0;
+        hi[j] = (ok[j] && x[j] >= 0) ? ps.nrows : 0;
+    }
+    for (int span = ps.nrows; span > 0; span >>= 1) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (lo[j] < hi[j]) {
+                const int mid = (lo[j] + hi[j]) >> 1;
+                if (__ldg(ids + mid) < x[j]) lo[j] = mid + 1; else hi[j] = mid;
+            }
+        }
+    }
+    int32_t at[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) at[j] = (ok[j] && x[j] >= 0 && lo[j] < ps.nrows) ? __ldg(ids + lo[j]) : -1;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int32_t *ro = sv.rowoff + ps.row_base + lo[j];
+        r[j] = (at[j] == x[j] && at[j] >= 0) ? make_int2(__ldg(ro), __ldg(ro + 1)) : make_int2(0, 0);
+    }
+}
+
 // Is v among the sorted entries val[first, last)?
 __device__ __forceinline__ bool sorted_contains(const int32_t *__restrict__ vals, int first, int last, int32_t v) {
     int lo = first, hi = last;

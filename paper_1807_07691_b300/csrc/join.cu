@@ -20,9 +20,13 @@ namespace {
 // count + scan
 
 constexpr int kCsBlock = 256;
-constexpr int kCsItems = 4;
+constexpr int kCsItems = 8;
 constexpr int kCsTile = kCsBlock * kCsItems;
 
+// Items are warp-striped (item j of lane l of warp w is row
+// tile * kCsTile + w * 32 * kCsItems + 32 j + l), so loads and stores are
+// coalesced; the tile's prefix runs in that order: a warp scan per j, the
+// warp's running total across j, then the warps' totals.
 __global__ void __launch_bounds__(kCsBlock) count_scan_kernel(SideView sv, PredSide ps,
                                                               const int32_t *__restrict__ x, int64_t n,
                                                               int64_t *__restrict__ off, int32_t *__restrict__ first,
@@ -31,34 +35,37 @@ __global__ void __launch_bounds__(kCsBlock) count_scan_kernel(SideView sv, PredS
     __shared__ int64_t scan_sm[kCsBlock / 32 + 1];
     __shared__ int64_t prefix_sm;
     const int tile = acquire_tile_id(ls, &tile_sm);
-    const int64_t i0 = (int64_t)tile * kCsTile + (int64_t)threadIdx.x * kCsItems;
-    int cnt[kCsItems];
-    int fst[kCsItems];
-    int64_t sum = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)tile * kCsTile + (int64_t)warp * (32 * kCsItems) + lane;
+    int32_t xv[kCsItems];
+    bool ok[kCsItems];
 #pragma unroll
     for (int j = 0; j < kCsItems; ++j) {
-        const int64_t i = i0 + j;
-        cnt[j] = 0;
-        fst[j] = 0;
-        if (i < n) {
-            const int2 r = row_range(sv, ps, __ldg(x + i));
-            cnt[j] = r.y - r.x;
-            fst[j] = r.x;
-        }
-        sum += cnt[j];
+        ok[j] = i0 + 32 * j < n;
+        xv[j] = ok[j] ? __ldg(x + i0 + 32 * j) : 0;
+    }
+    int2 rr[kCsItems];
+    row_ranges<kCsItems>(sv, ps, xv, ok, rr);
+    // exclusive prefix of every item inside its warp's part of the tile
+    int64_t ex[kCsItems];
+    int64_t wrun = 0;
+#pragma unroll
+    for (int j = 0; j < kCsItems; ++j) {
+        const int64_t c = rr[j].y - rr[j].x;
+        const int64_t inc = warp_inclusive_sum(c);
+        ex[j] = wrun + inc - c;
+        wrun += __shfl_sync(0xffffffffu, inc, 31);
     }
     int64_t tot;
-    const int64_t ex = block_exclusive_sum<kCsBlock>(sum, scan_sm, &tot);
+    const int64_t wex = block_exclusive_sum<kCsBlock>(lane == 0 ? wrun : 0, scan_sm, &tot);
+    const int64_t wbase = __shfl_sync(0xffffffffu, wex, 0);
     const int64_t pre = tile_lookback(ls, tile, tot, &prefix_sm);
-    int64_t run = pre + ex;
 #pragma unroll
     for (int j = 0; j < kCsItems; ++j) {
-        const int64_t i = i0 + j;
-        if (i < n) {
-            off[i] = run;
-            first[i] = fst[j];
+        if (ok[j]) {
+            off[i0 + 32 * j] = pre + wbase + ex[j];
+            first[i0 + 32 * j] = rr[j].x;
         }
-        run += cnt[j];
     }
     if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) {
         off[n] = pre + tot;

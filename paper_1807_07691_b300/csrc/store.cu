@@ -173,19 +173,53 @@ __global__ void pred_bounds_kernel(const int32_t *__restrict__ rowslot, const in
     }
 }
 
-// dense[x] = first entry of row x (or of the next non-empty row) for
-// x in [0, max_entity + 1].
-__global__ void dense_fill_kernel(const int32_t *__restrict__ rowid, const int32_t *__restrict__ rowoff, PredSide ps,
-                                  int32_t max_entity, int32_t *__restrict__ dense) {
-    const int64_t len = (int64_t)max_entity + 2;
-    const int32_t *ids = rowid + ps.row_base;
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < len; x += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = ps.nrows;
-        while (lo < hi) {
+// Dense row pointers of several predicates in one launch:
+// dense[dense_base + x] = first entry of row x (or of the next non-empty
+// row) for x in [0, max_entity + 1].  A warp fills kDenseChunk consecutive
+// x of one predicate: two binary searches bound the rows of the chunk, then
+// each lane searches its x inside that range and the writes are coalesced.
+struct DensePart {
+    int32_t row_base;
+    int32_t nrows;
+    int32_t end_entry;  // ent_base + nnz
+    int32_t _pad;
+    int64_t dense_base;
+    int64_t chunk0;     // first chunk of this predicate
+};
+constexpr int kDenseChunk = 256;
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *__restrict__ a, int lo, int hi, int64_t x) {
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void dense_fill_kernel(const int32_t *__restrict__ rowid, const int32_t *__restrict__ rowoff,
+                                  const DensePart *__restrict__ parts, int n_parts, int64_t n_chunks, int64_t len,
+                                  int32_t *__restrict__ dense) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
+        int lo = 0, hi = n_parts;  // last part whose chunk0 <= c
+        while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
-            if (ids[mid] < x) lo = mid + 1; else hi = mid;
+            if (parts[mid].chunk0 <= c) lo = mid; else hi = mid;
         }
-        dense[x] = (lo < ps.nrows) ? rowoff[ps.row_base + lo] : ps.ent_base + ps.nnz;
+        const DensePart P = parts[lo];
+        const int64_t x0 = (c - P.chunk0) * kDenseChunk;
+        const int32_t *ids = rowid + P.row_base;
+        const int r0 = lower_bound_i32(ids, 0, P.nrows, x0);
+        const int r1 = lower_bound_i32(ids, r0, P.nrows, x0 + kDenseChunk);
+#pragma unroll 4
+        for (int k = 0; k < kDenseChunk / 32; ++k) {
+            const int64_t x = x0 + lane + 32 * k;
+            if (x < len) {
+                const int r = lower_bound_i32(ids, r0, r1, x);
+                dense[P.dense_base + x] = r < P.nrows ? __ldg(rowoff + P.row_base + r) : P.end_entry;
+            }
+        }
     }
 }
 
@@ -267,12 +301,20 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
         ps.nrows = hb[(P + 1) + p + 1] - hb[(P + 1) + p];
         ps.dense_base = -1;
     }
-    // dense row pointers where the array costs at most 4x the entries
+    // Dense row pointers (max_entity + 2 words each) for the predicates with
+    // the most entries, while their total stays within 4x the side's entry
+    // bytes (16 bytes per entry); the others find rows by binary search.
     const int64_t len = (int64_t)S->max_entity + 2;
+    std::vector<int> by_nnz(P);
+    for (int p = 0; p < P; ++p) by_nnz[p] = p;
+    std::stable_sort(by_nnz.begin(), by_nnz.end(),
+                     [&](int a, int b) { return S->side[side][a].nnz > S->side[side][b].nnz; });
+    const int64_t budget = 16 * n;
     int64_t total = 0;
-    for (int p = 0; p < P; ++p) {
-        PredSide &ps = S->side[side][p];
-        if (S->max_entity >= 0 && len <= 4 * (int64_t)ps.nnz) {
+    if (S->max_entity >= 0) {
+        for (int p : by_nnz) {
+            PredSide &ps = S->side[side][p];
+            if (ps.nnz == 0 || (total + len) * 4 > budget) continue;
             ps.dense_base = total;
             total += len;
         }
@@ -280,15 +322,33 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     S->n_dense[side] = 0;
     if (total > 0) {
         GS_TRY(S->dense[side].alloc(sizeof(int32_t) * (size_t)total, st));
+        const int64_t per = (len + kDenseChunk - 1) / kDenseChunk;
+        std::vector<DensePart> parts;
         for (int p = 0; p < P; ++p) {
             const PredSide &ps = S->side[side][p];
             if (ps.dense_base < 0) continue;
-            S->n_dense[side]++;
-            dense_fill_kernel<<<grid_for(len), kThreads, 0, st>>>(S->rowid[side].as<int32_t>(),
-                                                                  S->rowoff[side].as<int32_t>(), ps, S->max_entity,
-                                                                  S->dense[side].as<int32_t>() + ps.dense_base);
-            GS_LAUNCH_CHECK();
+            DensePart d;
+            d.row_base = ps.row_base;
+            d.nrows = ps.nrows;
+            d.end_entry = ps.ent_base + ps.nnz;
+            d._pad = 0;
+            d.dense_base = ps.dense_base;
+            d.chunk0 = (int64_t)parts.size() * per;
+            parts.push_back(d);
         }
+        S->n_dense[side] = (int32_t)parts.size();
+        DevBuf d_parts;
+        GS_TRY(d_parts.alloc(sizeof(DensePart) * parts.size(), st));
+        GS_CUDA(cudaMemcpyAsync(d_parts.p, parts.data(), sizeof(DensePart) * parts.size(), cudaMemcpyHostToDevice, st));
+        const int64_t n_chunks = per * (int64_t)parts.size();
+        int64_t g = (n_chunks * 32 + kThreads - 1) / kThreads;
+        const int64_t cap = (int64_t)device_sm_count() * 16;
+        if (g > cap) g = cap;
+        dense_fill_kernel<<<(unsigned)g, kThreads, 0, st>>>(S->rowid[side].as<int32_t>(), S->rowoff[side].as<int32_t>(),
+                                                            d_parts.as<DensePart>(), (int)parts.size(), n_chunks, len,
+                                                            S->dense[side].as<int32_t>());
+        GS_LAUNCH_CHECK();
+        // the parts table is read by the kernel before the stream-ordered free
     }
     S->key[side] = std::move(key);
     S->val[side] = std::move(val);
