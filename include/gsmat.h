@@ -432,7 +432,7 @@ GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void);
 
 typedef struct {
     char name[32];         /* kernel family */
-    int64_t launches;
+    int64_t launches;      /* timed calls of the family (each may launch several kernels) */
     double total_ms;       /* sum of event-timed durations */
     double algo_bytes;     /* sum of algorithmic bytes moved (see docs per kernel) */
     double items;          /* sum of items processed (rows or keys) */
@@ -444,6 +444,10 @@ GSMAT_API int gsmat_profile_enable(int on);
 /* Copy up to cap kernel families into out; *n_out gets their count.
  * reset = 1 clears the counters after reading. */
 GSMAT_API int gsmat_profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset);
+
+/* Number of CUDA kernels the library has launched since it was loaded (all
+ * threads; monotonic).  Never fails. */
+GSMAT_API int64_t gsmat_launch_count(void);
 
 #ifdef __cplusplus
 }

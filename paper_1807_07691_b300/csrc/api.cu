@@ -29,6 +29,7 @@ const char *last_error();
 int set_allocator(gsmat_alloc_fn a, gsmat_free_fn f, void *ctx);
 int profile_enable(int on);
 int profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset);
+int64_t launch_count();
 }  // namespace gs
 
 using gs::set_error;
@@ -288,6 +289,8 @@ GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_o
 GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void) { return gs::exclusive_scan_i32_noalloc_max(); }
 
 GSMAT_API int gsmat_profile_enable(int on) { return gs::profile_enable(on); }
+
+GSMAT_API int64_t gsmat_launch_count(void) { return gs::launch_count(); }
 
 GSMAT_API int gsmat_profile_read(gsmat_kernel_profile *out, int32_t cap, int32_t *n_out, int reset) {
     return gs::profile_read(out, cap, n_out, reset);

@@ -38,7 +38,13 @@ void clear_error();
         }                       \
     } while (0)
 
-#define GS_LAUNCH_CHECK() GS_CUDA(cudaGetLastError())
+// After every kernel launch: counts it (gsmat_launch_count) and checks it.
+void note_launch();
+#define GS_LAUNCH_CHECK()      \
+    do {                       \
+        note_launch();         \
+        GS_CUDA(cudaGetLastError()); \
+    } while (0)
 
 // ---------------------------------------------------------------------------
 // device memory through the allocator hook

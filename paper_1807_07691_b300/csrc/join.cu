@@ -354,6 +354,7 @@ int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t 
                   (double)total);
     expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts,
                                                                                   cuts.as<int64_t>());
+    GS_LAUNCH_CHECK();
     expand_kernel<<<(unsigned)n_parts, kExBlock, 0, st>>>(a);
     GS_LAUNCH_CHECK();
     t.stop();

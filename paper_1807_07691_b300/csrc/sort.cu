@@ -24,8 +24,10 @@
 namespace gs {
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kWarps = kBlock / 32;
+constexpr int kBlock = 256;               // histogram kernel
+constexpr int kPassBlock = 256;           // pass kernel (a multiple of kBins)
+constexpr int kPassMinBlocks = 4;         // pass CTAs resident per SM (register budget)
+constexpr int kPassWarps = kPassBlock / 32;
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
 
@@ -378,25 +380,25 @@ __global__ void __launch_bounds__(kBlock) onesweep_histogram(Src src, int64_t n,
 }
 
 template <class K, bool HasVals, class Src, class Sink>
-__global__ void __launch_bounds__(kBlock, 4) onesweep_pass(Src src, Sink sink, int64_t n, int shift, int mask,
+__global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src src, Sink sink, int64_t n, int shift, int mask,
                                                        const uint32_t *__restrict__ hist_pass,
                                                        unsigned long long *__restrict__ desc,
                                                        unsigned int *__restrict__ tile_counter, uint32_t epoch,
                                                        int *__restrict__ err) {
     constexpr int ITEMS = SortTraits<K>::kItems;
-    constexpr int TILE = kBlock * ITEMS;
+    constexpr int TILE = kPassBlock * ITEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *skeys = reinterpret_cast<K *>(smem_raw);
     uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + TILE);
-    uint32_t *whist = svals + (HasVals ? TILE : 0);  // [kWarps][kBins]
-    uint32_t *tstart = whist + kWarps * kBins;
+    uint32_t *whist = svals + (HasVals ? TILE : 0);  // [kPassWarps][kBins]
+    uint32_t *tstart = whist + kPassWarps * kBins;
     uint32_t *gbase = tstart + kBins;
-    __shared__ int64_t scan_tmp[kWarps + 1];
+    __shared__ int64_t scan_tmp[kPassWarps + 1];
     __shared__ int tile_sm;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) tile_sm = (int)atomicAdd(tile_counter, 1u);
-    for (int i = threadIdx.x; i < kWarps * kBins; i += kBlock) whist[i] = 0;
+    for (int i = threadIdx.x; i < kPassWarps * kBins; i += kPassBlock) whist[i] = 0;
     __syncthreads();
     const int tile = tile_sm;
     const int64_t t0 = (int64_t)tile * TILE;
@@ -435,24 +437,29 @@ __global__ void __launch_bounds__(kBlock, 4) onesweep_pass(Src src, Sink sink, i
         __syncwarp();
     }
     __syncthreads();
-    // per digit (thread d): cross-warp prefix, tile count, tile start
+    // per digit (thread d < kBins): cross-warp prefix, tile count, tile start
     const int d = threadIdx.x;
+    const bool dig = d < kBins;
     uint32_t cnt = 0;
+    if (dig) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = whist[w * kBins + d];
-        whist[w * kBins + d] = cnt;
-        cnt += c;
+        for (int w = 0; w < kPassWarps; ++w) {
+            const uint32_t c = whist[w * kBins + d];
+            whist[w * kBins + d] = cnt;
+            cnt += c;
+        }
     }
     int64_t tot;
-    const int64_t ts = block_exclusive_sum<kBlock>((int64_t)cnt, scan_tmp, &tot);
-    tstart[d] = (uint32_t)ts;
+    const int64_t ts = block_exclusive_sum<kPassBlock>((int64_t)cnt, scan_tmp, &tot);
+    if (dig) tstart[d] = (uint32_t)ts;
     const uint32_t real = cnt - (d == kBins - 1 ? (uint32_t)(TILE - valid) : 0u);
     // global start of digit d in this pass (exclusive scan of the histogram)
-    const int64_t dbase = block_exclusive_sum<kBlock>((int64_t)__ldg(hist_pass + d), scan_tmp, &tot);
+    const int64_t dbase =
+        block_exclusive_sum<kPassBlock>(dig ? (int64_t)__ldg(hist_pass + d) : (int64_t)0, scan_tmp, &tot);
     // publish this tile's count of digit d, then look back for the earlier ones
     uint64_t excl = 0;
-    if (tile == 0) {
+    if (!dig) {
+    } else if (tile == 0) {
         atomicExch(desc + d, desc_pack(epoch, kDescPrefix, real));
     } else {
         atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescAggregate, real));
@@ -475,7 +482,7 @@ __global__ void __launch_bounds__(kBlock, 4) onesweep_pass(Src src, Sink sink, i
         }
         atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescPrefix, excl + real));
     }
-    gbase[d] = (uint32_t)(dbase + (int64_t)excl);
+    if (dig) gbase[d] = (uint32_t)(dbase + (int64_t)excl);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(kBlock, 4) onesweep_pass(Src src, Sink sink, i
         if (HasVals) svals[pos] = v[j];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < valid; i += kBlock) {
+    for (int i = threadIdx.x; i < valid; i += kPassBlock) {
         const K kk = skeys[i];
         const int dd = digit_of(kk, shift, mask);
         const uint32_t dst = gbase[dd] + ((uint32_t)i - tstart[dd]);
@@ -511,8 +518,8 @@ int sm_count() {
 
 template <class K, bool HasVals>
 int pass_smem_bytes() {
-    constexpr int TILE = kBlock * SortTraits<K>::kItems;
-    return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kWarps * kBins + 2 * kBins) * 4;
+    constexpr int TILE = kPassBlock * SortTraits<K>::kItems;
+    return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kPassWarps * kBins + 2 * kBins) * 4;
 }
 
 int current_device() {
@@ -533,9 +540,9 @@ int launch_pass(const Src &src, const Sink &sink, int64_t n, int shift, int widt
                                      cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
         done[dev] = true;
     }
-    constexpr int TILE = kBlock * SortTraits<K>::kItems;
+    constexpr int TILE = kPassBlock * SortTraits<K>::kItems;
     const int64_t ntiles = (n + TILE - 1) / TILE;
-    onesweep_pass<K, HasVals, Src, Sink><<<(unsigned)ntiles, kBlock, pass_smem_bytes<K, HasVals>(), st>>>(
+    onesweep_pass<K, HasVals, Src, Sink><<<(unsigned)ntiles, kPassBlock, pass_smem_bytes<K, HasVals>(), st>>>(
         src, sink, n, shift, (1 << width) - 1, hist_pass, desc, counter, epoch, err);
     GS_LAUNCH_CHECK();
     return GSMAT_OK;
@@ -583,7 +590,7 @@ template <class K, bool HasVals>
 int sort_passes(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word) {
     const int n_pass = (end_bit - begin_bit + 7) / 8;
     SortMeta meta;
-    GS_TRY(meta.make(n, n_pass, kBlock * SortTraits<K>::kItems, st, err_word));
+    GS_TRY(meta.make(n, n_pass, kPassBlock * SortTraits<K>::kItems, st, err_word));
     DevBuf alt_k, alt_v;
     GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
     if (HasVals) GS_TRY(alt_v.alloc(sizeof(uint32_t) * (size_t)n, st));
@@ -740,7 +747,7 @@ int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutC
         uint32_t *pout = ((n_chunks - 1 - ci) & 1) ? pb.as<uint32_t>() : pa.as<uint32_t>();
         const SinkPerm sink_perm{pout, src.idx_bits};
         SortMeta meta;
-        GS_TRY(meta.make(n, n_pass, kBlock * SortTraits<uint64_t>::kItems, st, err_word));
+        GS_TRY(meta.make(n, n_pass, kPassBlock * SortTraits<uint64_t>::kItems, st, err_word));
         GS_TRY((launch_histogram<uint64_t, SrcRows>(src, n, 0, key_bits, n_pass, meta.hist, st)));
         for (int p = 0; p < n_pass; ++p) {
             const int shift = src.idx_bits + 8 * p;

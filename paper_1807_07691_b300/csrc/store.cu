@@ -29,19 +29,59 @@ constexpr int kThreads = 256;
 
 unsigned grid_for(int64_t n) { return grid_1d(n, kThreads); }
 
-__global__ void init_ranges_kernel(int *r) {
-    r[0] = -1;         // max subject/object
-    r[1] = -1;         // max predicate
-    r[2] = INT32_MAX;  // min over all ids
+// ranges[0..3] = max subject/object, max predicate, min id, predicate
+// overflow flag; ranges[4..4 + kPredTable) = open-addressing set of the
+// predicates present (-1 = empty).  Each CTA first collects its predicates
+// in a shared-memory set (a plain read finds those already there, so the
+// loop issues almost no atomics), then inserts them into the global set.
+// More distinct predicates than a set holds set the flag; the distinct
+// predicates are then found by sorting.
+constexpr int kPredLocal = 1024;
+constexpr int kPredTable = 4096;
+constexpr int kRangesWords = 4 + kPredTable;
+
+__device__ __forceinline__ uint32_t pred_slot_hash(int32_t p) { return (uint32_t)p * 2654435761u; }
+
+// Inserts p into the set table[0..cap) (cap a power of two); false if full.
+__device__ __forceinline__ bool set_insert(int *table, int cap, int32_t p) {
+    uint32_t h = pred_slot_hash(p) & (uint32_t)(cap - 1);
+    for (int probe = 0; probe < cap; ++probe) {
+        const int v = *(volatile int *)(table + h);
+        if (v == p) return true;
+        if (v == -1) {
+            const int old = atomicCAS(table + h, -1, p);
+            if (old == -1 || old == p) return true;
+        }
+        h = (h + 1) & (uint32_t)(cap - 1);
+    }
+    return false;
 }
 
-__global__ void ranges_kernel(const int32_t *__restrict__ tri, int64_t n, int *r) {
+__global__ void init_ranges_kernel(int *r) {
+    for (int i = threadIdx.x; i < kRangesWords; i += blockDim.x) r[i] = i >= 4 ? -1 : 0;
+    if (threadIdx.x == 0) {
+        r[0] = -1;         // max subject/object
+        r[1] = -1;         // max predicate
+        r[2] = INT32_MAX;  // min over all ids
+    }
+}
+
+__global__ void __launch_bounds__(256) ranges_kernel(const int32_t *__restrict__ tri, int64_t n, int *r) {
+    __shared__ int lset[kPredLocal];
+    for (int i = threadIdx.x; i < kPredLocal; i += blockDim.x) lset[i] = -1;
+    __syncthreads();
     int mx_so = -1, mx_p = -1, mn = INT32_MAX;
+    bool over = false;
+    int32_t last = -1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int s = tri[3 * i], p = tri[3 * i + 1], o = tri[3 * i + 2];
         mx_so = max(mx_so, max(s, o));
         mx_p = max(mx_p, p);
         mn = min(mn, min(s, min(p, o)));
+        if (p >= 0 && p != last) {
+            over |= !set_insert(lset, kPredLocal, p);
+            last = p;
+        }
     }
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
@@ -49,10 +89,16 @@ __global__ void ranges_kernel(const int32_t *__restrict__ tri, int64_t n, int *r
         mx_p = max(mx_p, __shfl_xor_sync(0xffffffffu, mx_p, d));
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, d));
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPredLocal; i += blockDim.x) {
+        if (lset[i] >= 0) over |= !set_insert(r + 4, kPredTable, lset[i]);
+    }
+    over = __any_sync(0xffffffffu, over);
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&r[0], mx_so);
         atomicMax(&r[1], mx_p);
         atomicMin(&r[2], mn);
+        if (over) atomicExch(&r[3], 1);
     }
 }
 
@@ -223,9 +269,12 @@ __global__ void dense_fill_kernel(const int32_t *__restrict__ rowid, const int32
     }
 }
 
-// Sort rows (c, a, b) lexicographically; results into oa/ob/oc.
+// Sort rows (c, a, b) lexicographically; results into oa/ob/oc.  With
+// b_sorted the rows are already ascending in b among equal (c, a) (the
+// input is sorted by (c, b, a)), so a stable sort on (c, a) alone suffices
+// and b rides in the key's low bits unsorted.
 int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, int id_bits, int slot_bits,
-               int32_t *oa, int32_t *ob, int32_t *oc, cudaStream_t st, int *err) {
+               bool b_sorted, int32_t *oa, int32_t *ob, int32_t *oc, cudaStream_t st, int *err) {
     if (n == 0) return GSMAT_OK;
     const unsigned g = grid_for(n);
     if (slot_bits + 2 * id_bits <= 64) {
@@ -233,7 +282,8 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
         GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, st));
         pack_kernel<<<g, kThreads, 0, st>>>(a, b, c, n, id_bits, keys.as<uint64_t>());
         GS_LAUNCH_CHECK();
-        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, 0, slot_bits + 2 * id_bits, st, err));
+        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, n, b_sorted ? id_bits : 0, slot_bits + 2 * id_bits, st,
+                              err));
         unpack_kernel<<<g, kThreads, 0, st>>>(keys.as<uint64_t>(), n, id_bits, oa, ob, oc);
         GS_LAUNCH_CHECK();
         return GSMAT_OK;
@@ -243,6 +293,7 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
     GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)n, st));
     GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)n, st));
     iota_kernel<<<g, kThreads, 0, st>>>(perm.as<uint32_t>(), n);
+    GS_LAUNCH_CHECK();
     gather_key_kernel<<<g, kThreads, 0, st>>>(nullptr, b, 0, nullptr, n, keys.as<uint64_t>());
     GS_LAUNCH_CHECK();
     GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), n, 0, id_bits, st, err));
@@ -370,13 +421,15 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     int64_t *h = pinned_scratch(8);
     if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
     // 1. ranges
-    GS_TRY(ranges.alloc(sizeof(int) * 4, st));
-    init_ranges_kernel<<<1, 1, 0, st>>>(ranges.as<int>());
+    GS_TRY(ranges.alloc(sizeof(int) * kRangesWords, st));
+    init_ranges_kernel<<<1, 256, 0, st>>>(ranges.as<int>());
+    GS_LAUNCH_CHECK();
     if (n > 0) ranges_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, ranges.as<int>());
     GS_LAUNCH_CHECK();
-    GS_CUDA(cudaMemcpyAsync(h, ranges.p, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<int> hr_all(kRangesWords);
+    GS_CUDA(cudaMemcpyAsync(hr_all.data(), ranges.p, sizeof(int) * kRangesWords, cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
-    const int *hr = reinterpret_cast<const int *>(h);
+    const int *hr = hr_all.data();
     if (n > 0 && hr[2] < 0) return set_error(GSMAT_ERR_INVALID_ARG, "negative id in triples (min %d)", hr[2]);
     S->max_entity = n > 0 ? hr[0] : -1;
     S->max_pred = n > 0 ? hr[1] : -1;
@@ -391,7 +444,15 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
         return GSMAT_OK;
     }
     // 2. distinct predicates -> slots, hash index
-    {
+    if (!hr[3]) {
+        // from the set collected by the ranges pass, ascending
+        S->pred_ids.clear();
+        for (int w = 0; w < kPredTable; ++w) {
+            if (hr[4 + w] >= 0) S->pred_ids.push_back(hr[4 + w]);
+        }
+        std::sort(S->pred_ids.begin(), S->pred_ids.end());
+        S->n_pred = (int32_t)S->pred_ids.size();
+    } else {
         DevBuf pcol, pdist, cnt;
         GS_TRY(pcol.alloc(sizeof(uint32_t) * (size_t)n, st));
         GS_TRY(pdist.alloc(sizeof(int32_t) * (size_t)n, st));
@@ -445,7 +506,7 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     GS_TRY(s_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(o_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(slot_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(sort_rows3(s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>(), n, id_bits, slot_bits,
+    GS_TRY(sort_rows3(s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>(), n, id_bits, slot_bits, false,
                       s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(), st, err.as<int>()));
     // dedupe into the raw buffers (reused)
     GS_TRY(cnt.alloc(sizeof(int64_t), st));
@@ -467,12 +528,13 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     GS_CUDA(cudaMemcpyAsync(val0.p, o_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
     GS_CUDA(cudaMemcpyAsync(slot0.p, slot_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
     s_raw.release(); o_raw.release(); slot_raw.release();
-    // 4. side 1: sort the unique triples by (slot, o, s)
+    // 4. side 1: sort the unique triples by (slot, o, s); they are sorted by
+    // (slot, s, o), so a stable sort on (slot, o) keeps s ascending
     DevBuf key1, val1, slot1;
     GS_TRY(key1.alloc(sizeof(int32_t) * (size_t)nu, st));
     GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)nu, st));
     GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_TRY(sort_rows3(val0.as<int32_t>(), key0.as<int32_t>(), slot0.as<int32_t>(), nu, id_bits, slot_bits,
+    GS_TRY(sort_rows3(val0.as<int32_t>(), key0.as<int32_t>(), slot0.as<int32_t>(), nu, id_bits, slot_bits, true,
                       key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st, err.as<int>()));
     s_sorted.release(); o_sorted.release(); slot_sorted.release();
     // 5. rows, predicate bounds, dense row pointers

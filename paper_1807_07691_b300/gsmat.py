@@ -145,6 +145,7 @@ def _load():
         "gsmat_exclusive_scan_i32_noalloc_max": ([], i64),
         "gsmat_profile_enable": ([c_int], c_int),
         "gsmat_profile_read": ([vp, i32, P(i32), c_int], c_int),
+        "gsmat_launch_count": ([], i64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -600,6 +601,11 @@ def exclusive_scan_i32_noalloc_max() -> int:
 
 def profile_enable(on: bool = True):
     _check(_lib.gsmat_profile_enable(1 if on else 0))
+
+
+def launch_count() -> int:
+    """Kernels the library has launched since it was loaded."""
+    return int(_lib.gsmat_launch_count())
 
 
 def profile_read(reset: bool = False) -> dict:

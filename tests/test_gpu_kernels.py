@@ -123,3 +123,12 @@ def test_sort_rows_rejects_bad_arguments(env):
         with pytest.raises(g.GsmatError) as e:
             g.sort_rows(c, m, bits)
         assert e.value.code == 1
+
+
+def test_launch_count_counts_kernels(env):
+    g, torch = env
+    keys = torch.randint(0, 2**40, (100_000,), device="cuda", dtype=torch.int64)
+    c0 = g.launch_count()
+    g.radix_sort_u64(keys, None, 0, 40)
+    torch.cuda.synchronize()
+    assert g.launch_count() - c0 == 1 + 5  # digit histogram + five 8-bit passes

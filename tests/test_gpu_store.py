@@ -107,3 +107,15 @@ def test_ragged_sizes(gs):
     for n in (1, 2, 3, 1023, 1024, 1025, 3071, 3072, 3073, 4097):
         t = synth.small_random_graph(200, 3, n, seed=n)
         _check_store(gs, t)
+
+
+def test_many_distinct_predicates(gs):
+    # more distinct predicates than the build's hash sets hold (sort path),
+    # and a count that fits them (set path), with predicate ids spread wide
+    rng = np.random.default_rng(11)
+    for n_pred in (5000, 900):
+        n = 20_000
+        preds = rng.choice(2**30, size=n_pred, replace=False)
+        t = np.stack([rng.integers(0, 3000, n), preds[rng.integers(0, n_pred, n)], rng.integers(0, 3000, n)], 1)
+        S = _check_store(gs, t.astype(np.int32))
+        assert S.info()["n_predicates"] == len(np.unique(t[:, 1]))
