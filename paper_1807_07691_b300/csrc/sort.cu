@@ -536,8 +536,10 @@ int launch_pass(const Src &src, const Sink &sink, int64_t n, int shift, int widt
     if (!done[dev]) {
         GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      pass_smem_bytes<K, HasVals>()));
+        // the driver's own carveout: forcing the maximum shared memory left
+        // too little L1 for the passes that gather through a permutation
         GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared));
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutDefault));
         done[dev] = true;
     }
     constexpr int TILE = kPassBlock * SortTraits<K>::kItems;
