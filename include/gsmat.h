@@ -304,6 +304,10 @@ typedef struct {
                               requests (0: 120 GiB) */
     gsmat_batch_config batch; /* kernel shape and caps of every micro-batch (zeros: block 512,
                                  1 CTA/SM, arena up to 8 GiB sized from the estimates) */
+    int32_t batch_lone;    /* 0: a request admitted alone while nothing else is in flight runs
+                              on the plain path (as gsmat_query, on its slot's stream), which
+                              has the lower latency on an idle device; 1: micro-batch it too */
+    int32_t _pad;
 } gsmat_server_config;
 
 typedef struct {
@@ -315,6 +319,7 @@ typedef struct {
     int64_t queued;         /* now waiting for admission */
     int64_t in_flight;      /* micro-batches now on the device or being planned */
     int64_t in_flight_bytes;/* estimated bytes now admitted */
+    int64_t direct;         /* requests admitted alone and run on the plain path */
 } gsmat_server_stats_t;
 
 /* Start a server (two host threads) over a store, which must outlive it.
@@ -324,7 +329,9 @@ typedef struct {
  * unclaimed budget; a request larger than the whole budget runs alone.
  * Each micro-batch is planned and run as by gsmat_batch_prepare/execute on
  * its own stream, so micro-batches overlap on the device; a completion
- * thread finishes each as its device work ends. */
+ * thread finishes each as its device work ends.  A request admitted alone
+ * while nothing else is in flight runs on the plain path instead (see
+ * batch_lone). */
 GSMAT_API int gsmat_server_create(const gsmat_store *store, const gsmat_server_config *cfg, gsmat_server **out);
 
 /* Queue one BGP (copied; validated as gsmat_query) and return its ticket at

@@ -25,6 +25,7 @@
 
 #include "batch.cuh"
 #include "plan.h"
+#include "query.cuh"
 #include "store.cuh"
 
 namespace gs {
@@ -50,6 +51,12 @@ struct BatchHolder {
     }
 };
 
+// A result of the plain path (a request admitted alone).
+struct TableHolder {
+    gsmat_table *T = nullptr;
+    ~TableHolder() { delete T; }
+};
+
 enum { REQ_QUEUED = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_FAILED = 3 };
 
 struct Request {
@@ -60,8 +67,9 @@ struct Request {
     int state = REQ_QUEUED;
     int status = GSMAT_OK;
     Clock::time_point t_submit, t_done;
-    std::shared_ptr<BatchHolder> batch;
+    std::shared_ptr<BatchHolder> batch;  // result in a micro-batch ...
     int index = -1;
+    std::shared_ptr<TableHolder> table;  // ... or of the plain path
 };
 
 struct InFlight {
@@ -92,7 +100,18 @@ struct gsmat_server {
     bool stop = false;
     bool sched_done = false;  // the scheduler has exited (nothing more will be launched)
     gsmat_server_stats_t stats{};
-    std::thread sched, comp;
+    // the lone lane: one request at a time on the plain path, on its own
+    // stream and thread, while the scheduler keeps admitting micro-batches
+    cudaStream_t lone_stream = nullptr;
+    std::condition_variable cv_lone;
+    std::shared_ptr<Request> lone_req;  // handed over, not yet finished
+    double lone_bytes = 0;
+    // mean gap between submissions (exponentially weighted, microseconds):
+    // the lone lane serves only sparse arrivals, where the next request
+    // usually comes after the lone one has finished
+    double gap_us = 1e9;
+    Clock::time_point last_submit{};
+    std::thread sched, comp, lone;
 };
 
 namespace gs {
@@ -136,6 +155,50 @@ void fail_requests(gsmat_server *srv, std::vector<std::shared_ptr<Request>> &rs,
     }
 }
 
+// The lone lane: runs each handed-over request on the plain path (as
+// gsmat_query) on its own stream, then completes it.  The scheduler hands a
+// request over only when it was admitted alone while nothing else was on the
+// device, where the plain path's multi-CTA steps finish one query sooner
+// than a one-query micro-batch.
+constexpr double kLoneGapUs = 500.0;
+
+void lone_loop(gsmat_server *srv) {
+    cudaSetDevice(srv->device);
+    while (true) {
+        std::shared_ptr<Request> r;
+        double bytes = 0;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv_lone.wait(lk, [&] { return srv->sched_done || srv->lone_req != nullptr; });
+            if (!srv->lone_req) return;  // the scheduler is gone and nothing is pending
+            r = srv->lone_req;
+            bytes = srv->lone_bytes;
+        }
+        auto holder = std::make_shared<TableHolder>();
+        const int rc = query_run(srv->S, r->pats.data(), (int)r->pats.size(), r->n_vars, GSMAT_SORTED, srv->lone_stream,
+                                 &holder->T);
+        profile_flush();
+        const Clock::time_point now = Clock::now();
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->lone_req = nullptr;
+        srv->inflight_bytes -= bytes;
+        srv->finished_batches++;
+        r->t_done = now;
+        if (rc == GSMAT_OK) {
+            r->table = std::move(holder);
+            r->state = REQ_DONE;
+            srv->stats.completed++;
+            srv->stats.direct++;
+        } else {
+            r->state = REQ_FAILED;
+            r->status = rc;
+            srv->stats.failed++;
+        }
+        srv->cv_done.notify_all();
+        srv->cv_sched.notify_all();
+    }
+}
+
 void scheduler_loop(gsmat_server *srv) {
     cudaSetDevice(srv->device);
     while (true) {
@@ -154,6 +217,7 @@ void scheduler_loop(gsmat_server *srv) {
                 srv->sched_done = true;
                 srv->cv_done.notify_all();
                 srv->cv_comp.notify_all();
+                srv->cv_lone.notify_all();
                 return;
             }
             // admission: arrival order, under the budget; a request larger
@@ -161,7 +225,7 @@ void scheduler_loop(gsmat_server *srv) {
             while (!srv->queue.empty() && (int)take.size() < srv->cfg.max_batch) {
                 const double b = srv->queue.front()->est_bytes;
                 const bool fits = srv->inflight_bytes + bytes + b <= (double)srv->cfg.budget_bytes;
-                const bool alone = take.empty() && srv->inflight.empty() && srv->launching == 0;
+                const bool alone = take.empty() && srv->inflight.empty() && srv->launching == 0 && !srv->lone_req;
                 if (!fits && !alone) break;
                 take.push_back(srv->queue.front());
                 srv->queue.pop_front();
@@ -172,6 +236,16 @@ void scheduler_loop(gsmat_server *srv) {
                 // budget exhausted: wait for a micro-batch to finish
                 const uint64_t seen = srv->finished_batches;
                 srv->cv_sched.wait(lk, [&] { return srv->stop || srv->finished_batches != seen; });
+                continue;
+            }
+            if (!srv->cfg.batch_lone && take.size() == 1 && !srv->lone_req && srv->inflight.empty() &&
+                srv->launching == 0 && srv->gap_us > kLoneGapUs) {
+                // admitted alone on an idle device: the lone lane runs it
+                srv->inflight_bytes += bytes;
+                take[0]->state = REQ_RUNNING;
+                srv->lone_req = take[0];
+                srv->lone_bytes = bytes;
+                srv->cv_lone.notify_one();
                 continue;
             }
             srv->inflight_bytes += bytes;
@@ -237,7 +311,12 @@ void completion_loop(gsmat_server *srv) {
             }
         }
         if (!have) {
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            // a dedicated thread: wait 5 us by the clock, yielding, before
+            // the next look (a timed sleep adds the timer's slack, tens of
+            // microseconds, to every request's latency; the pause keeps the
+            // lock free for the submitters)
+            const Clock::time_point until = Clock::now() + std::chrono::microseconds(5);
+            while (Clock::now() < until) std::this_thread::yield();
             continue;
         }
         const int rc = batch_finish(job.holder->B);
@@ -297,7 +376,9 @@ int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_se
     }
     srv->cfg = c;
     cudaGetDevice(&srv->device);
-    if (cudaStreamCreateWithFlags(&srv->prep_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&srv->prep_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&srv->lone_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (srv->prep_stream) cudaStreamDestroy(srv->prep_stream);
         delete srv;
         return set_error(GSMAT_ERR_CUDA, "server stream");
     }
@@ -318,6 +399,7 @@ int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_se
     }
     srv->sched = std::thread(scheduler_loop, srv);
     srv->comp = std::thread(completion_loop, srv);
+    srv->lone = std::thread(lone_loop, srv);
     *out = srv;
     return GSMAT_OK;
 }
@@ -333,6 +415,11 @@ int server_submit(gsmat_server *srv, const gsmat_pattern *pats, int n_pats, int 
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return set_error(GSMAT_ERR_INVALID_ARG, "server is shutting down");
     r->ticket = srv->next_ticket++;
+    if (r->ticket > 1) {
+        const double gap = std::chrono::duration<double, std::micro>(r->t_submit - srv->last_submit).count();
+        srv->gap_us = srv->gap_us >= 1e9 ? gap : 0.875 * srv->gap_us + 0.125 * gap;
+    }
+    srv->last_submit = r->t_submit;
     srv->reqs[r->ticket] = r;
     srv->queue.push_back(r);
     srv->stats.submitted++;
@@ -367,19 +454,27 @@ int server_result(gsmat_server *srv, int64_t ticket, int64_t *rows, int32_t *col
     if (latency_us) {
         *latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
     }
+    if (r->table) {
+        if (rows) *rows = r->table->T->rows;
+        if (cols) *cols = r->table->T->ncols;
+        return GSMAT_OK;
+    }
     return batch_result_view(r->batch->B, r->index, rows, cols, nullptr);
 }
 
 int server_copy(gsmat_server *srv, int64_t ticket, int32_t *dst, int dst_on_device, cudaStream_t st) {
     std::shared_ptr<BatchHolder> holder;
+    std::shared_ptr<TableHolder> table;
     int index;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         auto r = find(srv, ticket);
         if (!r || r->state != REQ_DONE) return set_error(GSMAT_ERR_INVALID_ARG, "ticket %lld has no result", (long long)ticket);
         holder = r->batch;
+        table = r->table;
         index = r->index;
     }
+    if (table) return table_copy(table->T, dst, dst_on_device, st);
     return batch_copy(holder->B, index, dst, dst_on_device, st);
 }
 
@@ -420,9 +515,15 @@ void server_destroy(gsmat_server *srv) {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->sched_done = true;  // also when the scheduler never started
     }
-    // the completion thread drains what is in flight, then exits
+    // the completion thread and the lone lane drain what they hold, then exit
     srv->cv_comp.notify_all();
+    srv->cv_lone.notify_all();
     if (srv->comp.joinable()) srv->comp.join();
+    if (srv->lone.joinable()) srv->lone.join();
+    if (srv->lone_stream) {
+        cudaStreamSynchronize(srv->lone_stream);
+        cudaStreamDestroy(srv->lone_stream);
+    }
     srv->reqs.clear();
     for (BatchResources &r : srv->res) {
         if (r.st) cudaStreamSynchronize(r.st);

@@ -84,12 +84,12 @@ class BatchStats(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
-                ("batch", BatchConfig)]
+                ("batch", BatchConfig), ("batch_lone", ctypes.c_int32), ("_pad", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "batches", "fallbacks", "queued",
-                                              "in_flight", "in_flight_bytes")]
+                                              "in_flight", "in_flight_bytes", "direct")]
 
 
 class KernelProfile(ctypes.Structure):
@@ -471,11 +471,12 @@ class Server:
     """Continuous-batching server over a resident store (gsmat_server_*)."""
 
     def __init__(self, store: "Store", max_batch: int = 0, slots: int = 0, budget_bytes: int = 0,
-                 batch: dict | None = None):
+                 batch: dict | None = None, batch_lone: bool = False):
         c = ServerConfig()
         c.max_batch = max_batch
         c.slots = slots
         c.budget_bytes = budget_bytes
+        c.batch_lone = 1 if batch_lone else 0
         bc = _config(batch)
         if bc is not None:
             c.batch = bc

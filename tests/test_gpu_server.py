@@ -50,7 +50,7 @@ def _run(srv, items):
 
 def test_results_same_alone_and_in_the_mix(gs, tiny):
     S, items, alone = tiny
-    srv = gs.Server(S, max_batch=32, slots=4)
+    srv = gs.Server(S, max_batch=32, slots=4, batch_lone=True)
     tickets = _run(srv, items)
     for t, want in zip(tickets, alone):
         got = srv.to_numpy(t)
@@ -90,3 +90,24 @@ def test_close_with_pending_work(gs, tiny):
     for p, v in items:
         srv.submit(p, v)
     srv.close()  # finishes what is in flight, fails the rest, does not hang
+
+
+def test_lone_requests_take_the_plain_path(gs, tiny):
+    # sparse arrivals (2 ms apart), one at a time on an idle device: each
+    # runs as gsmat_query on the lone lane's stream, with the same result
+    import time
+
+    S, items, alone = tiny
+    srv = gs.Server(S)
+    for (p, v), want in list(zip(items, alone))[:20]:
+        time.sleep(0.002)
+        t = srv.submit(p, v)
+        assert srv.wait(t)
+        got = srv.to_numpy(t)
+        assert got.shape == want.shape and np.array_equal(got, want)
+        rows, cols, lat = srv.result(t)
+        assert rows == want.shape[0] and lat > 0
+        srv.release(t)
+    st = srv.stats()
+    assert st["direct"] == 20 and st["batches"] == 0 and st["completed"] == 20
+    srv.close()
