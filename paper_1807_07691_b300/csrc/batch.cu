@@ -378,34 +378,51 @@ __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs a) {
 // keys[g] = variables [vb, ve) of source row src = perm_in[g] (or g),
 // packed most significant first, with the source's segment index above
 // them when seg_shift >= 0; perm_out[g] = g when perm_in is null.
+// Segment of row g: the last s with start[s] <= g (start = the segments'
+// first rows, ascending; a compact array, cached, unlike the descriptors).
+__device__ __forceinline__ int seg_of(const int64_t *__restrict__ start, int n_segs, int64_t g) {
+    int lo = 0, hi = n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(start + mid) <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// idx_bits > 0: the source position rides in the key's low idx_bits bits
+// (key << idx_bits | src) and perm_out is not written.
 __global__ void seg_pack_kernel(const SegDesc *__restrict__ segs, int n_segs, int bits, int vb, int ve, int seg_shift,
-                                const uint32_t *__restrict__ perm_in, int64_t total, uint64_t *__restrict__ keys,
-                                uint32_t *__restrict__ perm_out) {
+                                int idx_bits, const uint32_t *__restrict__ perm_in, int64_t total,
+                                uint64_t *__restrict__ keys, uint32_t *__restrict__ perm_out) {
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t src = perm_in ? (int64_t)__ldg(perm_in + g) : g;
-        int lo = 0, hi = n_segs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].row_off <= src) lo = mid; else hi = mid - 1;
-        }
+        const int lo = seg_of(reinterpret_cast<const int64_t *>(segs + n_segs), n_segs, src);
         const SegDesc &s = segs[lo];
         const int64_t r = src - s.row_off;
         uint64_t key = 0;
         for (int v = vb; v < ve; ++v) key = (key << bits) | (uint32_t)__ldg(s.col[v] + r);
         if (seg_shift >= 0) key |= (uint64_t)lo << seg_shift;
-        keys[g] = key;
-        if (!perm_in) perm_out[g] = (uint32_t)g;
+        if (idx_bits > 0) {
+            keys[g] = (key << idx_bits) | (uint64_t)src;
+        } else {
+            keys[g] = key;
+            if (!perm_in) perm_out[g] = (uint32_t)g;
+        }
+    }
+}
+
+__global__ void key_low_bits_kernel(const uint64_t *__restrict__ keys, int idx_bits, int64_t total,
+                                    uint32_t *__restrict__ perm) {
+    const uint64_t mask = (1ull << idx_bits) - 1;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        perm[g] = (uint32_t)(__ldg(keys + g) & mask);
     }
 }
 
 __global__ void seg_gather_kernel(const SegDesc *__restrict__ segs, int n_segs, int64_t total,
                                   const uint32_t *__restrict__ perm) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = n_segs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (segs[mid].row_off <= p) lo = mid; else hi = mid - 1;
-        }
+        const int lo = seg_of(reinterpret_cast<const int64_t *>(segs + n_segs), n_segs, p);
         const SegDesc &s = segs[lo];
         const int64_t r = (perm ? (int64_t)__ldg(perm + p) : p) - s.row_off;  // source row (same segment)
         const int64_t i = p - s.row_off;                          // destination row
@@ -415,14 +432,21 @@ __global__ void seg_gather_kernel(const SegDesc *__restrict__ segs, int n_segs, 
 
 }  // namespace
 
-int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, const uint32_t *perm_in,
-                    int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st) {
+int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, int idx_bits,
+                    const uint32_t *perm_in, int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st) {
     if (total <= 0) return GSMAT_OK;
     KernelTimer t("seg_pack", st, (double)total * (12.0 + 4.0 * (ve - vb)), (double)total);
-    seg_pack_kernel<<<grid_1d(total, 256), 256, 0, st>>>(segs, n_segs, bits, vb, ve, seg_shift, perm_in, total, keys,
-                                                         perm_out);
+    seg_pack_kernel<<<grid_1d(total, 256), 256, 0, st>>>(segs, n_segs, bits, vb, ve, seg_shift, idx_bits, perm_in,
+                                                         total, keys, perm_out);
     GS_LAUNCH_CHECK();
     t.stop();
+    return GSMAT_OK;
+}
+
+int launch_key_low_bits(const uint64_t *keys, int idx_bits, int64_t total, uint32_t *perm, cudaStream_t st) {
+    if (total <= 0) return GSMAT_OK;
+    key_low_bits_kernel<<<grid_1d(total, 256), 256, 0, st>>>(keys, idx_bits, total, perm);
+    GS_LAUNCH_CHECK();
     return GSMAT_OK;
 }
 

@@ -73,6 +73,9 @@ struct BatchResources {
 // One result table of a segmented reorder: its rows are rows
 // [row_off, row_off + rows) of the concatenation; col[v] = the column of
 // variable v (variables 0..m-1 are the sort key); out = V columns of rows.
+// On the device an array of n_segs descriptors is followed by the int64
+// array of their row_off values (see upload_segs), which the kernels
+// search.
 struct SegDesc {
     int64_t row_off;
     int64_t rows;
@@ -81,8 +84,14 @@ struct SegDesc {
     const int32_t *col[32];
     int32_t *out;
 };
-int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, const uint32_t *perm_in,
-                    int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st);
+// keys[g] = the variables [vb, ve) of the row at source position src (g, or
+// perm_in[g]) packed `bits` each, with the segment index at seg_shift when
+// seg_shift >= 0; idx_bits > 0 appends src in the low idx_bits bits (and
+// perm_out is not written), else perm_out[g] = g when perm_in is null.
+int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, int idx_bits,
+                    const uint32_t *perm_in, int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st);
+// perm[g] = the low idx_bits bits of keys[g].
+int launch_key_low_bits(const uint64_t *keys, int idx_bits, int64_t total, uint32_t *perm, cudaStream_t st);
 // out rows of every segment from the rows perm[p] (a plain copy when perm
 // is null).
 int launch_seg_gather(const SegDesc *segs, int n_segs, int64_t total, const uint32_t *perm, cudaStream_t st);

@@ -332,6 +332,20 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
 // variables: a segmented least-significant-digit radix reorder whose last
 // (most significant) key holds the result's index above its first
 // variables, then one gather.
+// The descriptors followed by the int64 array of their first rows (what the
+// segmented kernels search), in one device buffer.
+int upload_segs(const std::vector<SegDesc> &segs, DevBuf &d, cudaStream_t st) {
+    const size_t n = segs.size();
+    std::vector<char> h(sizeof(SegDesc) * n + sizeof(int64_t) * n);
+    memcpy(h.data(), segs.data(), sizeof(SegDesc) * n);
+    int64_t *start = reinterpret_cast<int64_t *>(h.data() + sizeof(SegDesc) * n);
+    for (size_t k = 0; k < n; ++k) start[k] = segs[k].row_off;
+    GS_TRY(d.alloc(h.size(), st));
+    // a copy from pageable memory is staged before the call returns
+    GS_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+    return GSMAT_OK;
+}
+
 int reorder_group(gsmat_batch *B, const std::vector<int> &qs, int m, int bits) {
     const int seg_bits = std::max(1, bits_for((uint64_t)(qs.size() - 1)));
     std::vector<SegDesc> segs;
@@ -358,8 +372,7 @@ int reorder_group(gsmat_batch *B, const std::vector<int> &qs, int m, int bits) {
         w += d.rows * d.V;
     }
     DevBuf d_segs, keys, perm, err;
-    GS_TRY(d_segs.alloc(sizeof(SegDesc) * segs.size(), B->priv));
-    GS_CUDA(cudaMemcpyAsync(d_segs.p, segs.data(), sizeof(SegDesc) * segs.size(), cudaMemcpyHostToDevice, B->priv));
+    GS_TRY(upload_segs(segs, d_segs, B->priv));
     GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)total, B->priv));
     GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)total, B->priv));
     GS_TRY(err.alloc(sizeof(int), B->priv));
@@ -375,15 +388,26 @@ int reorder_group(gsmat_batch *B, const std::vector<int> &qs, int m, int bits) {
         e = b0;
     }
     chunks.push_back({0, h});
+    // a chunk whose key bits and the source position fit one 64-bit word
+    // sorts keys alone (8 bytes per row and pass instead of 12)
+    const int idx_bits = std::max(1, bits_for((uint64_t)(total - 1)));
     for (size_t c = 0; c < chunks.size(); ++c) {
         const int vb = chunks[c].first, ve = chunks[c].second;
         const bool last = c + 1 == chunks.size();
         const int kb = (ve - vb) * bits;
+        const int key_bits = last ? kb + seg_bits : kb;
+        const bool packed = key_bits + idx_bits <= 64;
         GS_TRY(launch_seg_pack(d_segs.as<SegDesc>(), (int)segs.size(), bits, vb, ve, last ? kb : -1,
-                               c == 0 ? nullptr : perm.as<uint32_t>(), total, keys.as<uint64_t>(), perm.as<uint32_t>(),
-                               B->priv));
-        GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), total, 0, last ? kb + seg_bits : kb, B->priv,
-                              err.as<int>()));
+                               packed ? idx_bits : 0, c == 0 ? nullptr : perm.as<uint32_t>(), total,
+                               keys.as<uint64_t>(), perm.as<uint32_t>(), B->priv));
+        if (packed) {
+            GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, total, idx_bits, idx_bits + key_bits, B->priv,
+                                  err.as<int>()));
+            GS_TRY(launch_key_low_bits(keys.as<uint64_t>(), idx_bits, total, perm.as<uint32_t>(), B->priv));
+        } else {
+            GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), total, 0, key_bits, B->priv,
+                                  err.as<int>()));
+        }
     }
     GS_TRY(launch_seg_gather(d_segs.as<SegDesc>(), (int)segs.size(), total, perm.as<uint32_t>(), B->priv));
     int herr = 0;
@@ -444,8 +468,7 @@ int compact_results(gsmat_batch *B) {
             w += d.rows * d.V;
         }
         DevBuf d_segs;
-        GS_TRY(d_segs.alloc(sizeof(SegDesc) * segs.size(), B->priv));
-        GS_CUDA(cudaMemcpyAsync(d_segs.p, segs.data(), sizeof(SegDesc) * segs.size(), cudaMemcpyHostToDevice, B->priv));
+        GS_TRY(upload_segs(segs, d_segs, B->priv));
         GS_TRY(launch_seg_gather(d_segs.as<SegDesc>(), (int)segs.size(), rows, nullptr, B->priv));
         GS_CUDA(cudaStreamSynchronize(B->priv));
         for (size_t k = 0; k < segs.size(); ++k) {
