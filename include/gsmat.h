@@ -190,6 +190,14 @@ GSMAT_API int gsmat_table_column(const gsmat_table *table, int32_t col, const in
  * dst_on_device = 0, device memory otherwise).  Synchronises `stream`. */
 GSMAT_API int gsmat_table_copy(const gsmat_table *table, int32_t *dst, int dst_on_device, gsmat_stream_t stream);
 
+/* As gsmat_table_copy, but only enqueues the copy on `stream` and returns:
+ * the table must stay alive and dst valid until `stream` has passed the
+ * copy (e.g. until the caller synchronises it), and dst should be pinned
+ * host memory for the copy to overlap other work.  Lets results of one
+ * query travel to the host while the next query computes (another stream). */
+GSMAT_API int gsmat_table_copy_async(const gsmat_table *table, int32_t *dst, int dst_on_device,
+                                     gsmat_stream_t stream);
+
 /* Per-query record: plan and per-step row counts. */
 #define GSMAT_MAX_PATTERNS 64
 typedef struct {

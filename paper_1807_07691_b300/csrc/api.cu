@@ -155,6 +155,12 @@ GSMAT_API int gsmat_table_copy(const gsmat_table *T, int32_t *dst, int dst_on_de
     return gs::table_copy(T, dst, dst_on_device, (cudaStream_t)stream);
 }
 
+GSMAT_API int gsmat_table_copy_async(const gsmat_table *T, int32_t *dst, int dst_on_device,
+                                     gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::table_copy(T, dst, dst_on_device, (cudaStream_t)stream, false);
+}
+
 GSMAT_API int gsmat_table_stats(const gsmat_table *T, gsmat_query_stats *stats) {
     gs::clear_error();
     if (!T || !stats) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");

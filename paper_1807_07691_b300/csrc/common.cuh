@@ -115,6 +115,12 @@ void profile_flush();
 // pinned host scratch for small device->host reads (one per host thread)
 
 int64_t *pinned_scratch(int n_words);
+// Device alias of a pointer into the calling thread's pinned scratch (null
+// outside it).
+void *pinned_scratch_device(const void *host_ptr);
+// h_dst[0..n) = the 8-byte words at d_src, written by a one-warp kernel on
+// `st` into the mapped scratch (h_dst must lie in it); synchronises `st`.
+int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device view of the store

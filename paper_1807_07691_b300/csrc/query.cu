@@ -84,8 +84,7 @@ struct Ctx {
 
     // Read the count word and the error word; synchronises the stream.
     int read_count(int64_t *count) {
-        GS_CUDA(cudaMemcpyAsync(h, qstat.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        GS_CUDA(cudaStreamSynchronize(st));
+        GS_TRY(read_words(qstat.p, h, 2, st));
         if (*reinterpret_cast<int *>(h + 1)) return set_error(GSMAT_ERR_DEVICE_CHECK, "a bounded wait expired");
         *count = h[0];
         return GSMAT_OK;
@@ -131,7 +130,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
     Ctx cx;
     cx.S = S;
     cx.st = st;
-    cx.h = pinned_scratch(4 + 4 * GSMAT_MAX_PATTERNS);
+    cx.h = pinned_scratch(4 + 8 * GSMAT_MAX_PATTERNS);
     if (!cx.h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
     GS_TRY(cx.qstat.alloc(4 * sizeof(int64_t), st));
     GS_CUDA(cudaMemsetAsync(cx.qstat.p, 0, 4 * sizeof(int64_t), st));
@@ -166,17 +165,16 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
     const int n_req = (int)req.size() / 3;
     std::vector<int32_t> rng(2 * (size_t)n_req);
     if (n_req > 0 && !absent) {
-        DevBuf d_req;
-        GS_TRY(d_req.alloc(sizeof(int32_t) * (req.size() + rng.size()), st));
+        // requests and row ranges pass through the mapped scratch: the
+        // kernel reads and writes it directly, no copy engine involved
         int32_t *hreq = reinterpret_cast<int32_t *>(cx.h + 4);
+        int32_t *hout = hreq + req.size();
         memcpy(hreq, req.data(), sizeof(int32_t) * req.size());
-        GS_CUDA(cudaMemcpyAsync(d_req.p, hreq, sizeof(int32_t) * req.size(), cudaMemcpyHostToDevice, st));
-        int32_t *d_out = d_req.as<int32_t>() + req.size();
-        GS_TRY(launch_const_lookup(S->view, S->pred_side_dev.as<PredSide>(), S->n_pred, d_req.as<int32_t>(), n_req,
-                                   d_out, st));
-        GS_CUDA(cudaMemcpyAsync(hreq, d_out, sizeof(int32_t) * rng.size(), cudaMemcpyDeviceToHost, st));
+        GS_TRY(launch_const_lookup(S->view, S->pred_side_dev.as<PredSide>(), S->n_pred,
+                                   static_cast<const int32_t *>(pinned_scratch_device(hreq)), n_req,
+                                   static_cast<int32_t *>(pinned_scratch_device(hout)), st));
         GS_CUDA(cudaStreamSynchronize(st));
-        memcpy(rng.data(), hreq, sizeof(int32_t) * rng.size());
+        memcpy(rng.data(), hout, sizeof(int32_t) * rng.size());
     }
     auto row_len = [&](int r) -> int64_t { return r < 0 ? 0 : (int64_t)rng[2 * r + 1] - rng[2 * r]; };
     for (int i = 0; i < n_pats; ++i) {
@@ -501,7 +499,7 @@ int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const in
     Ctx cx;
     cx.S = S;
     cx.st = st;
-    cx.h = pinned_scratch(4 + 4 * GSMAT_MAX_PATTERNS);
+    cx.h = pinned_scratch(4 + 8 * GSMAT_MAX_PATTERNS);
     if (!cx.h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
     GS_TRY(cx.qstat.alloc(4 * sizeof(int64_t), st));
     GS_CUDA(cudaMemsetAsync(cx.qstat.p, 0, 4 * sizeof(int64_t), st));
@@ -535,7 +533,7 @@ int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const in
     return GSMAT_OK;
 }
 
-int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st) {
+int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st, bool sync) {
     if (!T || (!dst && T->rows > 0 && T->ncols > 0)) return set_error(GSMAT_ERR_INVALID_ARG, "table or dst is NULL");
     const int64_t n = T->rows;
     const int k = T->ncols;
@@ -544,14 +542,14 @@ int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream
     for (int c = 0; c < kMaxCols; ++c) in.c[c] = c < k ? T->col[c] : nullptr;
     if (dst_on_device) {
         GS_TRY(launch_interleave(in, k, n, dst, st));
-        GS_CUDA(cudaStreamSynchronize(st));
+        if (sync) GS_CUDA(cudaStreamSynchronize(st));
         return GSMAT_OK;
     }
-    DevBuf tmp;
+    DevBuf tmp;  // freed in stream order after the copy
     GS_TRY(tmp.alloc(sizeof(int32_t) * (size_t)n * k, st));
     GS_TRY(launch_interleave(in, k, n, tmp.as<int32_t>(), st));
     GS_CUDA(cudaMemcpyAsync(dst, tmp.p, sizeof(int32_t) * (size_t)n * k, cudaMemcpyDeviceToHost, st));
-    GS_CUDA(cudaStreamSynchronize(st));
+    if (sync) GS_CUDA(cudaStreamSynchronize(st));
     return GSMAT_OK;
 }
 

@@ -16,7 +16,8 @@ namespace gs {
 
 int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
               gsmat_table **out);
-int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st);
+// sync = false: enqueue only (the caller keeps T alive until st passes it).
+int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st, bool sync = true);
 // Reorder a table given in plan column order (rows ascending in that order)
 // to variable order, rows ascending; the result owns its columns.
 int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const int32_t *plan_vars, int V, int64_t rows,

@@ -103,28 +103,60 @@ int set_allocator(gsmat_alloc_fn a, gsmat_free_fn f, void *ctx) {
 // ---------------------------------------------------------------------------
 // pinned host scratch
 
+// Mapped (device-addressable) pinned memory, one buffer per host thread, so
+// that kernels can read small inputs from it and write small results into
+// it without the copy engines (a small read-back queued behind a large
+// device-to-host copy on another stream would wait for that copy).
+struct ScratchHolder {
+    int64_t *p = nullptr;
+    int64_t *d = nullptr;
+    int cap = 0;
+    ~ScratchHolder() {
+        if (p) cudaFreeHost(p);
+    }
+};
+static thread_local ScratchHolder t_scratch;
+
 int64_t *pinned_scratch(int n_words) {
-    struct Holder {
-        int64_t *p = nullptr;
-        int cap = 0;
-        ~Holder() {
-            if (p) cudaFreeHost(p);
-        }
-    };
-    static thread_local Holder h;
+    ScratchHolder &h = t_scratch;
     if (h.cap < n_words) {
         if (h.p) cudaFreeHost(h.p);
-        h.p = nullptr;
+        h.p = h.d = nullptr;
         h.cap = 0;
-        int cap = n_words < 64 ? 64 : n_words;
-        if (cudaMallocHost((void **)&h.p, sizeof(int64_t) * (size_t)cap) != cudaSuccess) {
+        // one size for every use in practice (a re-allocation synchronises)
+        int cap = n_words < 1024 ? 1024 : n_words;
+        if (cudaHostAlloc((void **)&h.p, sizeof(int64_t) * (size_t)cap, cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess ||
+            cudaHostGetDevicePointer((void **)&h.d, h.p, 0) != cudaSuccess) {
             cudaGetLastError();
-            h.p = nullptr;
+            if (h.p) cudaFreeHost(h.p);
+            h.p = h.d = nullptr;
             return nullptr;
         }
         h.cap = cap;
     }
     return h.p;
+}
+
+void *pinned_scratch_device(const void *host_ptr) {
+    const ScratchHolder &h = t_scratch;
+    const char *hp = static_cast<const char *>(host_ptr);
+    const char *base = reinterpret_cast<const char *>(h.p);
+    if (!h.p || hp < base || hp >= base + sizeof(int64_t) * (size_t)h.cap) return nullptr;
+    return reinterpret_cast<char *>(h.d) + (hp - base);
+}
+
+__global__ void copy_words_kernel(const int64_t *__restrict__ src, int64_t *__restrict__ dst, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st) {
+    void *d_dst = pinned_scratch_device(h_dst);
+    if (!d_dst) return set_error(GSMAT_ERR_INVALID_ARG, "read_words: destination outside the pinned scratch");
+    copy_words_kernel<<<1, 32, 0, st>>>(static_cast<const int64_t *>(d_src), static_cast<int64_t *>(d_dst), n_words);
+    GS_LAUNCH_CHECK();
+    GS_CUDA(cudaStreamSynchronize(st));
+    return GSMAT_OK;
 }
 
 // ---------------------------------------------------------------------------

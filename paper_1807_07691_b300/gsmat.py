@@ -119,6 +119,7 @@ def _load():
         "gsmat_table_info": ([vp, P(i64), P(i32), vp], c_int),
         "gsmat_table_column": ([vp, i32, P(vp)], c_int),
         "gsmat_table_copy": ([vp, vp, c_int, vp], c_int),
+        "gsmat_table_copy_async": ([vp, vp, c_int, vp], c_int),
         "gsmat_table_stats": ([vp, P(QueryStats)], c_int),
         "gsmat_table_free": ([vp], None),
         "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
@@ -259,22 +260,24 @@ class Table:
             _check(_lib.gsmat_table_copy(self._h, out.ctypes.data, 0, _stream_ptr(stream)))
         return out
 
-    def copy_to(self, dst, stream=None):
+    def copy_to(self, dst, stream=None, sync: bool = True):
         """Copy the table row-major into dst: a host numpy array or a host
         (ideally pinned) / CUDA torch tensor of int32 with rows*cols
-        elements."""
+        elements.  sync=False only enqueues the copy on `stream`
+        (gsmat_table_copy_async): keep the table and dst alive until the
+        stream has passed it."""
         rows, cols = self.shape
         if rows == 0 or cols == 0:
             return dst
+        fn = _lib.gsmat_table_copy if sync else _lib.gsmat_table_copy_async
         if hasattr(dst, "data_ptr"):
             if dst.numel() < rows * cols:
                 raise ValueError("destination too small")
-            _check(_lib.gsmat_table_copy(self._h, ctypes.c_void_p(dst.data_ptr()), 1 if dst.is_cuda else 0,
-                                         _stream_ptr(stream)))
+            _check(fn(self._h, ctypes.c_void_p(dst.data_ptr()), 1 if dst.is_cuda else 0, _stream_ptr(stream)))
         else:
             if dst.size < rows * cols or dst.dtype != np.int32 or not dst.flags.c_contiguous:
                 raise ValueError("destination must be a contiguous int32 array of rows*cols elements")
-            _check(_lib.gsmat_table_copy(self._h, dst.ctypes.data, 0, _stream_ptr(stream)))
+            _check(fn(self._h, dst.ctypes.data, 0, _stream_ptr(stream)))
         return dst
 
     def to_torch(self, stream=None):

@@ -87,6 +87,26 @@ def test_tiny_rerun_is_identical(gs, tiny):
         assert np.array_equal(a, b)
 
 
+def test_async_copy_on_another_stream(gs, tiny):
+    import torch
+
+    t, ix, S, qs = tiny
+    side = torch.cuda.Stream()
+    held, outs = [], []
+    for q in qs:
+        T = S.query(q)
+        rows, cols = T.shape
+        h = torch.empty(max(1, rows * cols), dtype=torch.int32).pin_memory()
+        T.copy_to(h, stream=side, sync=False)
+        held.append(T)
+        outs.append((h, rows, cols))
+    side.synchronize()
+    for q, T, (h, rows, cols) in zip(qs, held, outs):
+        got = h[: rows * cols].numpy().reshape(rows, cols)
+        assert np.array_equal(got, ix.query(q)), q.name
+        T.free()
+
+
 @pytest.mark.parametrize("seed", range(60))
 def test_random_bgps_small_graphs(gs, seed):
     rng = np.random.default_rng(1000 + seed)
