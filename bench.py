@@ -264,6 +264,9 @@ def run_gsmat(args):
         batched, bq = run_batched(args, gs, torch, d_tri, stream)
         if not args.no_served:
             served = run_served(args, gs, torch, d_tri, stream, bq)
+    served_large = None
+    if args.served_graph == "large" and rank == 0:
+        served_large = run_served_large(args, gs, torch, stream)
 
     if rank != 0:
         if ws > 1:
@@ -334,6 +337,8 @@ def run_gsmat(args):
         out["batched"] = batched
     if served is not None:
         out["served"] = served
+    if served_large is not None:
+        out["served_large"] = served_large
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(triples, queries, budget_s=args.cpu_budget)
     if ws > 1:
@@ -425,7 +430,7 @@ def _spin_until(t):
             time.sleep(d - 1e-4)
 
 
-def run_served(args, gs, torch, d_tri, stream, bq):
+def run_served(args, gs, torch, d_tri, stream, bq, workload=None):
     """Open-loop Poisson arrivals drawn from the batched mix, served by
     continuous batching (gsmat_server) and, for comparison, by the plain
     path one query at a time (FIFO).  Latency = completion - arrival."""
@@ -433,7 +438,7 @@ def run_served(args, gs, torch, d_tri, stream, bq):
     marsh = [gs.Server.marshal(q) for q in bq]
     marsh_plain = [gs.Store.marshal(q) for q in bq]
     rng = np.random.default_rng(7691 + 4)
-    out = {"workload": f"Poisson arrivals over {len(bq)} batched-mix BGPs (medium graph, resident store)",
+    out = {"workload": workload or f"Poisson arrivals over {len(bq)} batched-mix BGPs (medium graph, resident store)",
            "seconds_per_rate": args.served_seconds, "rates": []}
     for rate in args.served_rates:
         n = max(1, int(rate * args.served_seconds))
@@ -555,6 +560,26 @@ def run_reference(args):
     }
 
 
+def run_served_large(args, gs, torch, stream):
+    """The served measurement over the large graph (3x10^8 triples resident
+    on the device) with its own anchored 2-8-pattern mix."""
+    import synth
+
+    t0 = time.time()
+    tri = synth.make_graph("large")
+    qs = synth.make_large_served_queries(tri, n_queries=args.served_large_n)
+    gen_s = time.time() - t0
+    d_tri = torch.from_numpy(tri).cuda()
+    del tri
+    out = run_served(args, gs, torch, d_tri, stream, qs,
+                     workload=f"Poisson arrivals over {len(qs)} anchored BGPs of 2-8 patterns, star:chain:snowflake "
+                              "4:3:2 (large graph, 3x10^8 triples, resident store)")
+    out["generation_s"] = round(gen_s, 1)
+    del d_tri
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_micro(args):
     """One library primitive on a synthetic input larger than L2, timed with
     CUDA events (for kernel-level measurements and ncu captures)."""
@@ -643,6 +668,9 @@ def main():
     ap.add_argument("--served-rates", type=float, nargs="+", default=[1000, 5000, 20000])
     ap.add_argument("--served-max-batch", type=int, default=1024)
     ap.add_argument("--served-slots", type=int, default=4)
+    ap.add_argument("--served-graph", choices=["medium", "large"], default="medium",
+                    help="large: also serve an anchored mix over the large graph (generation takes minutes)")
+    ap.add_argument("--served-large-n", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
     if args.micro:

@@ -14,7 +14,8 @@ reproduced.
 """
 
 from .graphs import CONFIGS, GraphConfig, make_graph, graph_stats, small_random_graph
-from .queries import BGP, make_queries, make_batched_queries, make_large_queries, bgp_row_bound
+from .queries import (BGP, bgp_row_bound, make_batched_queries, make_large_queries, make_large_served_queries,
+                      make_queries)
 
 __all__ = [
     "CONFIGS",
@@ -26,5 +27,6 @@ __all__ = [
     "make_queries",
     "make_batched_queries",
     "make_large_queries",
+    "make_large_served_queries",
     "bgp_row_bound",
 ]

@@ -802,3 +802,35 @@ def make_large_queries(triples: np.ndarray | None = None, seed: int | None = Non
         bgp.count = exact  # exact result rows (stars, chains) or None
         out.append(bgp)
     return out
+
+
+def make_large_served_queries(triples: np.ndarray | None = None, n_queries: int = 2048, seed: int | None = None,
+                              limit: float = 1e6, n_entities: int | None = None):
+    """Served mix over the large graph: 2-8 patterns, shapes
+    star:chain:snowflake = 4:3:2, each anchored at one constant whose row is
+    short, every plan prefix bounded by ``limit`` rows (uneven selectivity:
+    bounds from a few rows up to the limit).  The batched mix's 4-cycles are
+    left out: closing a cycle needs a walk-count search that the sparse
+    frontier sampler does not do."""
+    cfg = CONFIGS["large"]
+    if triples is None:
+        triples = make_graph(cfg)
+    seed = cfg.query_seed + 1 if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed))
+    adj = _LargeAdjacency(triples, cfg.n_entities if n_entities is None else n_entities)
+    shapes = ("star",) * 4 + ("chain",) * 3 + ("snowflake",) * 2
+    out = []
+    for qi in range(n_queries):
+        shape = shapes[qi % len(shapes)]
+        if shape == "star":
+            n_pat = int(rng.integers(2, 9))
+        elif shape == "chain":
+            n_pat = int(rng.integers(2, 7))
+        else:
+            n_pat = int(rng.integers(4, 9))
+        pats, n_vars, bound, exact = _large_one(adj, rng, shape, n_pat, limit, max_anchor_deg=2000)
+        bgp = BGP(pats, n_vars, shape, f"large-s{qi:04d}-{shape}{len(pats)}")
+        bgp.bound = bound
+        bgp.count = exact
+        out.append(bgp)
+    return out
