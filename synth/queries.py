@@ -719,6 +719,7 @@ def _large_one(adj, rng, shape, n_pat, limit, max_anchor_deg, min_bound=0.0):
             if shape == "snowflake":
                 n_sub = n_pat - n_arms
                 next_var = n_arms
+                arm_prod = {}  # arm -> per candidate, product of max(1, sub-degree) over its sub-patterns
                 for j in range(n_sub):
                     a = j % n_arms
                     y = arms[a][1]
@@ -728,11 +729,14 @@ def _large_one(adj, rng, shape, n_pat, limit, max_anchor_deg, min_bound=0.0):
                     pb = int(yp[rng.integers(yp.size)])
                     pats.append((a, pb, next_var, True, True))
                     next_var += 1
-                    # bound for the arm: sum over its candidates of max(1, deg)
+                    # bound for the arm: sum over its candidates y of the
+                    # product, over the arm's sub-patterns, of max(1, deg(y))
+                    # (an arm with two sub-patterns multiplies their degrees)
                     ys = os_[ps == arms[a][0]].astype(np.int64)
                     lo, hi = adj.s_ptr[ys], adj.s_ptr[ys + 1]
                     degs = np.array([np.sum(adj.out_p[l:h] == pb) for l, h in zip(lo, hi)], dtype=np.float64)
-                    factors[a] = float(np.maximum(degs, 1.0).sum()) if factors[a] > 0 else 0.0
+                    arm_prod[a] = arm_prod.get(a, np.ones(ys.size)) * np.maximum(degs, 1.0)
+                    factors[a] = float(arm_prod[a].sum()) if factors[a] > 0 else 0.0
                 if len(pats) != n_pat:
                     continue
             bound = float(np.prod(factors))

@@ -284,3 +284,18 @@ def test_plan_first_pattern_has_smallest_key():
         order = planner.plan_order(pats, keys)
         assert keys[order[0]] == min(keys)
         assert order[0] == keys.index(min(keys))
+
+
+def test_large_served_mix_counts_match_the_oracle():
+    # the anchored sampler's exact counts (stars, chains) on the tiny graph
+    t = synth.make_graph("tiny")
+    qs = synth.make_large_served_queries(t, n_queries=36, n_entities=10_000, limit=2e5)
+    ix = oracle.OracleIndex(t)
+    shapes = {q.shape for q in qs}
+    assert shapes == {"star", "chain", "snowflake"}
+    for q in qs:
+        assert 2 <= len(q.patterns) <= 8
+        got = ix.query(q, row_limit=5_000_000)
+        assert got.shape[0] <= q.bound + 1e-6, q.name
+        if q.count is not None:
+            assert got.shape[0] == int(q.count), q.name
