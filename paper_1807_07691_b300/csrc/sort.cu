@@ -35,12 +35,18 @@ template <class K>
 struct SortTraits;
 template <>
 struct SortTraits<uint64_t> {
-    static constexpr int kItems = 12;
+    static constexpr int kItems = 12;         // keys per thread with a payload
+    static constexpr int kItemsKeysOnly = 16; // and without
 };
 template <>
 struct SortTraits<uint32_t> {
     static constexpr int kItems = 16;
+    static constexpr int kItemsKeysOnly = 16;
 };
+template <class K, bool HasVals>
+__host__ __device__ constexpr int items_per_thread() {
+    return HasVals ? SortTraits<K>::kItems : SortTraits<K>::kItemsKeysOnly;
+}
 
 template <class K>
 __device__ __forceinline__ int digit_of(K k, int shift, int mask) {
@@ -385,7 +391,7 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
                                                        unsigned long long *__restrict__ desc,
                                                        unsigned int *__restrict__ tile_counter, uint32_t epoch,
                                                        int *__restrict__ err) {
-    constexpr int ITEMS = SortTraits<K>::kItems;
+    constexpr int ITEMS = items_per_thread<K, HasVals>();
     constexpr int TILE = kPassBlock * ITEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *skeys = reinterpret_cast<K *>(smem_raw);
@@ -518,7 +524,7 @@ int sm_count() {
 
 template <class K, bool HasVals>
 int pass_smem_bytes() {
-    constexpr int TILE = kPassBlock * SortTraits<K>::kItems;
+    constexpr int TILE = kPassBlock * items_per_thread<K, HasVals>();
     return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kPassWarps * kBins + 2 * kBins) * 4;
 }
 
@@ -542,7 +548,7 @@ int launch_pass(const Src &src, const Sink &sink, int64_t n, int shift, int widt
                                      cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutDefault));
         done[dev] = true;
     }
-    constexpr int TILE = kPassBlock * SortTraits<K>::kItems;
+    constexpr int TILE = kPassBlock * items_per_thread<K, HasVals>();
     const int64_t ntiles = (n + TILE - 1) / TILE;
     onesweep_pass<K, HasVals, Src, Sink><<<(unsigned)ntiles, kPassBlock, pass_smem_bytes<K, HasVals>(), st>>>(
         src, sink, n, shift, (1 << width) - 1, hist_pass, desc, counter, epoch, err);
@@ -592,7 +598,7 @@ template <class K, bool HasVals>
 int sort_passes(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word) {
     const int n_pass = (end_bit - begin_bit + 7) / 8;
     SortMeta meta;
-    GS_TRY(meta.make(n, n_pass, kPassBlock * SortTraits<K>::kItems, st, err_word));
+    GS_TRY(meta.make(n, n_pass, kPassBlock * items_per_thread<K, HasVals>(), st, err_word));
     DevBuf alt_k, alt_v;
     GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
     if (HasVals) GS_TRY(alt_v.alloc(sizeof(uint32_t) * (size_t)n, st));
@@ -749,7 +755,9 @@ int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutC
         uint32_t *pout = ((n_chunks - 1 - ci) & 1) ? pb.as<uint32_t>() : pa.as<uint32_t>();
         const SinkPerm sink_perm{pout, src.idx_bits};
         SortMeta meta;
-        GS_TRY(meta.make(n, n_pass, kPassBlock * SortTraits<uint64_t>::kItems, st, err_word));
+        GS_TRY(meta.make(n, n_pass,
+                         kPassBlock * (packed ? items_per_thread<uint64_t, false>() : items_per_thread<uint64_t, true>()),
+                         st, err_word));
         GS_TRY((launch_histogram<uint64_t, SrcRows>(src, n, 0, key_bits, n_pass, meta.hist, st)));
         for (int p = 0; p < n_pass; ++p) {
             const int shift = src.idx_bits + 8 * p;
