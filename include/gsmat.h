@@ -410,7 +410,12 @@ GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n
  * 1 <= m <= V <= 32, 1 <= bits <= 31, 0 <= n < 2^32; d_out must not alias
  * d_cols.  Scratch comes from the allocator hook.  Does not synchronise. */
 GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bits, int64_t n,
-                              int32_t *const *d_out, gsmat_stream_t stream);
+                              int32_t *const *d_out, uint32_t flags, gsmat_stream_t stream);
+/* flags of gsmat_sort_rows: how the other V - m columns reach d_out when
+ * they fit one 64-bit payload, the key one word, and n > 2048 (0: chosen by
+ * size) */
+#define GSMAT_SORT_CARRY 1u  /* carried through the passes beside the key */
+#define GSMAT_SORT_GATHER 2u /* gathered through the sorted row index */
 
 /* Exclusive prefix sum of n int32 counts (each >= 0) into d_out[0..n]
  * (int64; d_out[n] = total), single pass with decoupled look-back over

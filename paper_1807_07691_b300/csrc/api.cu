@@ -268,8 +268,9 @@ GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n
 }
 
 GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bits, int64_t n,
-                              int32_t *const *d_out, gsmat_stream_t stream) {
+                              int32_t *const *d_out, uint32_t flags, gsmat_stream_t stream) {
     gs::clear_error();
+    if (flags > GSMAT_SORT_GATHER) return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     if (V < 1 || V > gs::kMaxCols || !d_cols || !d_out) return set_error(GSMAT_ERR_INVALID_ARG, "bad columns");
     gs::Cols in;
     gs::OutCols out;
@@ -278,7 +279,9 @@ GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bi
         out.c[v] = v < V ? d_out[v] : nullptr;
         if (v < V && n > 0 && (!in.c[v] || !out.c[v])) return set_error(GSMAT_ERR_INVALID_ARG, "column %d is NULL", v);
     }
-    return gs::reorder_rows(in, V, m, bits, n, out, (cudaStream_t)stream, nullptr);
+    const int mode = flags == GSMAT_SORT_CARRY ? gs::kReorderCarry
+                     : flags == GSMAT_SORT_GATHER ? gs::kReorderGather : gs::kReorderAuto;
+    return gs::reorder_rows(in, V, m, bits, n, out, (cudaStream_t)stream, nullptr, mode);
 }
 
 GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int64_t n, gsmat_stream_t stream) {

@@ -70,8 +70,12 @@ int launch_const_lookup(const StoreView &sv, const PredSide *d_sides, int n_pred
 // the variables `bits` bits each, as many per 64-bit key as fit; wider
 // orders sort chunk by chunk, least significant first.  *err_word is set if a
 // bounded wait expired (may be null).
+// mode: how the non-key columns reach the output when both ways apply
+// (they fit one 64-bit payload, one key chunk, more than 2048 rows):
+// carried through the passes, gathered after the sort, or chosen by size.
+enum { kReorderAuto = 0, kReorderCarry = 1, kReorderGather = 2 };
 int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutCols &out, cudaStream_t st,
-                 int *err_word);
+                 int *err_word, int mode = kReorderAuto);
 // dst[i * k + c] = in[c][i] (row-major interleave).
 int launch_interleave(const Cols &in, int k, int64_t n, int32_t *dst, cudaStream_t st);
 // out[c][i] = in[c][i] (copy k columns).

@@ -43,9 +43,11 @@ struct SortTraits<uint32_t> {
     static constexpr int kItems = 16;
     static constexpr int kItemsKeysOnly = 16;
 };
-template <class K, bool HasVals>
+// A 64-bit payload (packed column values carried through the passes)
+// needs more registers and shared memory per key: 10 keys per thread.
+template <class K, bool HasVals, class V = uint32_t>
 __host__ __device__ constexpr int items_per_thread() {
-    return HasVals ? SortTraits<K>::kItems : SortTraits<K>::kItemsKeysOnly;
+    return HasVals ? (sizeof(V) == 8 ? 10 : SortTraits<K>::kItems) : SortTraits<K>::kItemsKeysOnly;
 }
 
 template <class K>
@@ -62,24 +64,22 @@ __device__ __forceinline__ unsigned long long desc_pack(uint32_t epoch, uint64_t
     return ((unsigned long long)epoch << 56) | (state << 54) | value;
 }
 
-// Key sources and sinks of a pass.  A source yields the key and payload of
-// input position i; a sink stores the sorted key and payload at position dst.
 // Key sources and sinks of a pass.  A source loads a thread's ITEMS keys and
 // payloads of a tile (input positions t0 + base + 32 j, those below `valid`);
 // a sink stores a sorted key and payload at position dst.
-template <class K, bool HasVals>
+template <class K, bool HasVals, class V = uint32_t>
 struct SrcArray {
+    using Val = V;
     const K *keys;
-    const uint32_t *vals;
+    const V *vals;
     template <int ITEMS>
-    __device__ __forceinline__ void load_tile(int64_t t0, int base, int valid, K (&k)[ITEMS],
-                                              uint32_t (&v)[ITEMS]) const {
+    __device__ __forceinline__ void load_tile(int64_t t0, int base, int valid, K (&k)[ITEMS], V (&v)[ITEMS]) const {
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
             const int idx = base + 32 * j;
             if (idx < valid) {
                 k[j] = keys[t0 + idx];
-                v[j] = HasVals ? vals[t0 + idx] : 0u;
+                v[j] = HasVals ? vals[t0 + idx] : V(0);
             }
         }
     }
@@ -100,6 +100,7 @@ struct SrcArray {
 // instead of a separate payload (fields << idx_bits | r), so a pass moves 8
 // bytes per row instead of 12; the passes then sort bits from idx_bits up.
 struct SrcRows {
+    using Val = uint32_t;
     const int32_t *c[kMaxCols];
     const uint32_t *perm;
     int nc;
@@ -148,13 +149,76 @@ struct SrcRows {
     }
 };
 
-template <class K, bool HasVals>
+template <class K, bool HasVals, class V = uint32_t>
 struct SinkArray {
     K *keys;
-    uint32_t *vals;
-    __device__ __forceinline__ void store(uint32_t dst, K k, uint32_t v) const {
+    V *vals;
+    __device__ __forceinline__ void store(uint32_t dst, K k, V v) const {
         keys[dst] = k;
         if (HasVals) vals[dst] = v;
+    }
+};
+
+// Rows whose non-key columns travel with the key: key = the fields of
+// columns c[0..nc-1], payload = the fields of columns c[nc..nc+nr-1] (nr *
+// bits <= 64), both most significant first, `bits` each; rows in order.
+struct SrcRowsWide {
+    using Val = uint64_t;
+    const int32_t *c[kMaxCols];
+    int nc;
+    int nr;
+    int bits;
+    template <int ITEMS>
+    __device__ __forceinline__ void load_tile(int64_t t0, int base, int valid, uint64_t (&k)[ITEMS],
+                                              uint64_t (&v)[ITEMS]) const {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            k[j] = 0;
+            v[j] = 0;
+        }
+        for (int cc = 0; cc < nc + nr; ++cc) {
+            const int32_t *col = c[cc];
+            uint32_t x[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) x[j] = base + 32 * j < valid ? (uint32_t)__ldg(col + t0 + base + 32 * j) : 0u;
+            if (cc < nc) {
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) k[j] = (k[j] << bits) | x[j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) v[j] = (v[j] << bits) | x[j];
+            }
+        }
+    }
+    template <int H>
+    __device__ __forceinline__ void hist_keys(int64_t base, int stride, int64_t n, uint64_t (&k)[H]) const {
+#pragma unroll
+        for (int j = 0; j < H; ++j) k[j] = 0;
+        for (int cc = 0; cc < nc; ++cc) {
+            const int32_t *col = c[cc];
+            uint32_t x[H];
+#pragma unroll
+            for (int j = 0; j < H; ++j) {
+                const int64_t i = base + (int64_t)stride * j;
+                x[j] = i < n ? (uint32_t)__ldg(col + i) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < H; ++j) k[j] = (k[j] << bits) | x[j];
+        }
+    }
+};
+
+// The sorted table from key and payload alone: out[0..nc-1] from the key,
+// out[nc..nc+nr-1] from the payload.
+struct SinkRowsWide {
+    int32_t *out[kMaxCols];
+    int nc;
+    int nr;
+    int bits;
+    __device__ __forceinline__ void store(uint32_t dst, uint64_t k, uint64_t v) const {
+        const uint64_t fmask = (1ull << bits) - 1;
+        for (int j = 0; j < nc; ++j) out[j][dst] = (int32_t)((k >> ((nc - 1 - j) * bits)) & fmask);
+        for (int j = 0; j < nr; ++j) out[nc + j][dst] = (int32_t)((v >> ((nr - 1 - j) * bits)) & fmask);
     }
 };
 
@@ -391,12 +455,13 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
                                                        unsigned long long *__restrict__ desc,
                                                        unsigned int *__restrict__ tile_counter, uint32_t epoch,
                                                        int *__restrict__ err) {
-    constexpr int ITEMS = items_per_thread<K, HasVals>();
+    using V = typename Src::Val;
+    constexpr int ITEMS = items_per_thread<K, HasVals, V>();
     constexpr int TILE = kPassBlock * ITEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *skeys = reinterpret_cast<K *>(smem_raw);
-    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + TILE);
-    uint32_t *whist = svals + (HasVals ? TILE : 0);  // [kPassWarps][kBins]
+    V *svals = reinterpret_cast<V *>(skeys + TILE);
+    uint32_t *whist = reinterpret_cast<uint32_t *>(svals + (HasVals ? TILE : 0));  // [kPassWarps][kBins]
     uint32_t *tstart = whist + kPassWarps * kBins;
     uint32_t *gbase = tstart + kBins;
     __shared__ int64_t scan_tmp[kPassWarps + 1];
@@ -413,7 +478,7 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
     uint32_t *wh = whist + warp * kBins;
 
     K k[ITEMS];
-    uint32_t v[ITEMS];
+    V v[ITEMS];
     uint32_t dr[ITEMS];  // rank within the warp << 8 | digit
     // warp-striped: stable order inside the tile is (warp, j, lane)
     src.template load_tile<ITEMS>(t0, warp * (32 * ITEMS) + lane, valid, k, v);
@@ -424,7 +489,7 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
             dr[j] = (uint32_t)digit_of(k[j], shift, mask);
         } else {
             k[j] = ~K(0);
-            v[j] = 0u;
+            v[j] = V(0);
             dr[j] = kBins - 1;  // padding ranks last in the last bucket
         }
     }
@@ -502,7 +567,7 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
         const K kk = skeys[i];
         const int dd = digit_of(kk, shift, mask);
         const uint32_t dst = gbase[dd] + ((uint32_t)i - tstart[dd]);
-        sink.store(dst, kk, HasVals ? svals[i] : 0u);
+        sink.store(dst, kk, HasVals ? svals[i] : V(0));
     }
 }
 
@@ -522,10 +587,10 @@ int sm_count() {
     return cached[dev];
 }
 
-template <class K, bool HasVals>
+template <class K, bool HasVals, class V>
 int pass_smem_bytes() {
-    constexpr int TILE = kPassBlock * items_per_thread<K, HasVals>();
-    return TILE * (int)sizeof(K) + (HasVals ? TILE * 4 : 0) + (kPassWarps * kBins + 2 * kBins) * 4;
+    constexpr int TILE = kPassBlock * items_per_thread<K, HasVals, V>();
+    return TILE * (int)sizeof(K) + (HasVals ? TILE * (int)sizeof(V) : 0) + (kPassWarps * kBins + 2 * kBins) * 4;
 }
 
 int current_device() {
@@ -537,20 +602,21 @@ int current_device() {
 template <class K, bool HasVals, class Src, class Sink>
 int launch_pass(const Src &src, const Sink &sink, int64_t n, int shift, int width, const uint32_t *hist_pass,
                 unsigned long long *desc, unsigned int *counter, uint32_t epoch, int *err, cudaStream_t st) {
+    using V = typename Src::Val;
     static bool done[64] = {false};
     const int dev = current_device();
     if (!done[dev]) {
         GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     pass_smem_bytes<K, HasVals>()));
+                                     pass_smem_bytes<K, HasVals, V>()));
         // the driver's own carveout: forcing the maximum shared memory left
         // too little L1 for the passes that gather through a permutation
         GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutDefault));
         done[dev] = true;
     }
-    constexpr int TILE = kPassBlock * items_per_thread<K, HasVals>();
+    constexpr int TILE = kPassBlock * items_per_thread<K, HasVals, V>();
     const int64_t ntiles = (n + TILE - 1) / TILE;
-    onesweep_pass<K, HasVals, Src, Sink><<<(unsigned)ntiles, kPassBlock, pass_smem_bytes<K, HasVals>(), st>>>(
+    onesweep_pass<K, HasVals, Src, Sink><<<(unsigned)ntiles, kPassBlock, pass_smem_bytes<K, HasVals, V>(), st>>>(
         src, sink, n, shift, (1 << width) - 1, hist_pass, desc, counter, epoch, err);
     GS_LAUNCH_CHECK();
     return GSMAT_OK;
@@ -681,8 +747,79 @@ int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
     return radix_sort_impl<uint32_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u32", err_word);
 }
 
-int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutCols &out, cudaStream_t st,
+namespace {
+
+constexpr double kWideMinRestBytes = 256.0 * (1 << 20);
+
+// Single-chunk reorder whose n_rest non-key columns fit one 64-bit payload:
+// they travel through the passes with the key, so the sorted table comes
+// out of the last pass whole (no permutation, no gather).
+int reorder_wide(const Cols &cols, int V, int m, int bits, int64_t n, const OutCols &out, cudaStream_t st,
                  int *err_word) {
+    using SA = SrcArray<uint64_t, true, uint64_t>;
+    using KA = SinkArray<uint64_t, true, uint64_t>;
+    const int n_rest = V - m;
+    const int key_bits = m * bits;
+    const int n_pass = (key_bits + 7) / 8;
+    SrcRowsWide src;
+    SinkRowsWide sink;
+    memset(&src, 0, sizeof(src));
+    memset(&sink, 0, sizeof(sink));
+    for (int v = 0; v < V; ++v) {
+        src.c[v] = cols.c[v];
+        sink.out[v] = out.c[v];
+    }
+    src.nc = sink.nc = m;
+    src.nr = sink.nr = n_rest;
+    src.bits = sink.bits = bits;
+    // algorithmic bytes: histogram 4m, first pass reads 4V, each pass
+    // boundary writes and reads 16 (key + payload), last pass writes 4V
+    const double algo = 4.0 * m + 8.0 * V + 32.0 * (n_pass - 1);
+    KernelTimer t("reorder_sort", st, algo * (double)n, (double)n);
+    DevBuf ka, kb, va, vb;
+    GS_TRY(ka.alloc(sizeof(uint64_t) * (size_t)n, st));
+    GS_TRY(va.alloc(sizeof(uint64_t) * (size_t)n, st));
+    if (n_pass > 2) {
+        GS_TRY(kb.alloc(sizeof(uint64_t) * (size_t)n, st));
+        GS_TRY(vb.alloc(sizeof(uint64_t) * (size_t)n, st));
+    }
+    SortMeta meta;
+    GS_TRY(meta.make(n, n_pass, kPassBlock * items_per_thread<uint64_t, true, uint64_t>(), st, err_word));
+    GS_TRY((launch_histogram<uint64_t, SrcRowsWide>(src, n, 0, key_bits, n_pass, meta.hist, st)));
+    for (int p = 0; p < n_pass; ++p) {
+        const int shift = 8 * p;
+        const int width = key_bits - shift < 8 ? key_bits - shift : 8;
+        // pass p writes buffer set p & 1 and reads set (p - 1) & 1
+        uint64_t *dk = (p & 1) ? kb.as<uint64_t>() : ka.as<uint64_t>();
+        uint64_t *dv = (p & 1) ? vb.as<uint64_t>() : va.as<uint64_t>();
+        const SA arr{(p & 1) ? ka.as<uint64_t>() : kb.as<uint64_t>(), (p & 1) ? va.as<uint64_t>() : vb.as<uint64_t>()};
+        const KA to{dk, dv};
+        const bool first = p == 0, last = p == n_pass - 1;
+        const uint32_t *hp = meta.hist + p * kBins;
+        unsigned int *ctr = meta.counters + p;
+        const uint32_t ep = (uint32_t)(p + 1);
+        if (first && last) {
+            GS_TRY((launch_pass<uint64_t, true, SrcRowsWide, SinkRowsWide>(src, sink, n, shift, width, hp, meta.desc,
+                                                                          ctr, ep, meta.err, st)));
+        } else if (first) {
+            GS_TRY((launch_pass<uint64_t, true, SrcRowsWide, KA>(src, to, n, shift, width, hp, meta.desc, ctr, ep,
+                                                                meta.err, st)));
+        } else if (last) {
+            GS_TRY((launch_pass<uint64_t, true, SA, SinkRowsWide>(arr, sink, n, shift, width, hp, meta.desc, ctr, ep,
+                                                                 meta.err, st)));
+        } else {
+            GS_TRY((launch_pass<uint64_t, true, SA, KA>(arr, to, n, shift, width, hp, meta.desc, ctr, ep, meta.err,
+                                                       st)));
+        }
+    }
+    t.stop();
+    return GSMAT_OK;
+}
+
+}  // namespace
+
+int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutCols &out, cudaStream_t st,
+                 int *err_word, int mode) {
     if (V < 1 || V > kMaxCols || m < 1 || m > V || bits < 1 || bits > 31 || n < 0) {
         return set_error(GSMAT_ERR_INVALID_ARG, "reorder: V=%d m=%d bits=%d n=%lld", V, m, bits, (long long)n);
     }
@@ -691,6 +828,19 @@ int reorder_rows(const Cols &cols, int V, int m, int bits, int64_t n, const OutC
     const int per_key = 64 / bits;
     const int n_chunks = (m + per_key - 1) / per_key;
     const int k0 = m < per_key ? m : per_key;
+    // Carrying the non-key columns costs 8 more bytes per row each way per
+    // pass; a gather after the sort costs one random access per row, cheap
+    // while the gathered columns stay in L2 (126 MB).  Carry them when they
+    // fit 64 bits, the key needs at most five passes and the columns are
+    // well beyond L2 (measured: 62 M rows x 3 columns, 5 passes, 11 % faster;
+    // 12 M x 3 and 18 M x 2 with 8 passes, slower).
+    const int n_pass_key = (m * bits + 7) / 8;
+    const bool can_carry = n > kSmallSortRows && n_chunks == 1 && V > m && (V - m) * bits <= 64;
+    const bool carry = mode == kReorderCarry ||
+                       (mode == kReorderAuto && n_pass_key <= 5 && (double)n * (V - m) * 4.0 > kWideMinRestBytes);
+    if (can_carry && carry) {
+        return reorder_wide(cols, V, m, bits, n, out, st, err_word);
+    }
     if (n <= kSmallSortRows && n_chunks <= 2) {
         KernelTimer t("reorder_sort", st, (8.0 * V) * (double)n, (double)n);
         small_reorder_kernel<<<1, kSmallSortBlock, 0, st>>>(cols, V, m, k0, bits, (int)n, out);

@@ -140,7 +140,7 @@ def _load():
         "gsmat_server_stats": ([vp, vp], c_int),
         "gsmat_server_destroy": ([vp], None),
         "gsmat_radix_sort_u64": ([vp, vp, i64, c_int, c_int, vp], c_int),
-        "gsmat_sort_rows": ([vp, c_int, c_int, c_int, i64, vp, vp], c_int),
+        "gsmat_sort_rows": ([vp, c_int, c_int, c_int, i64, vp, u32, vp], c_int),
         "gsmat_exclusive_scan_i32": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc_max": ([], i64),
@@ -573,16 +573,20 @@ def radix_sort_u64(keys, vals=None, begin_bit: int = 0, end_bit: int = 64, strea
                                      keys.numel(), begin_bit, end_bit, _stream_ptr(stream)))
 
 
-def sort_rows(cols, m: int, bits: int, out=None, stream=None):
+SORT_CARRY, SORT_GATHER = 1, 2
+
+
+def sort_rows(cols, m: int, bits: int, out=None, stream=None, flags: int = 0):
     """Stable lexicographic reorder of the rows of V int32 CUDA columns by
-    the first m; returns (or fills) V new columns."""
+    the first m; returns (or fills) V new columns.  flags: SORT_CARRY /
+    SORT_GATHER force how the other columns travel (0: by size)."""
     V = len(cols)
     if out is None:
         out = [c.new_empty(c.shape) for c in cols]
     n = cols[0].numel() if V else 0
     src = (ctypes.c_void_p * max(V, 1))(*[c.data_ptr() for c in cols])
     dst = (ctypes.c_void_p * max(V, 1))(*[c.data_ptr() for c in out])
-    _check(_lib.gsmat_sort_rows(src, V, m, bits, n, dst, _stream_ptr(stream)))
+    _check(_lib.gsmat_sort_rows(src, V, m, bits, n, dst, flags, _stream_ptr(stream)))
     return out
 
 

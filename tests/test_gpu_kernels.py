@@ -76,7 +76,8 @@ def test_scan_total_beyond_int32(env):
 # so that equal keys are common and stability decides the order; both sides
 # of the one-CTA size limit (2048 rows, keys of up to two words); gathered
 # columns as one- and two-word records, as separate columns (more than
-# eight), and read in place when the permutation keeps runs (all keys equal).
+# eight), and read in place when the permutation keeps runs (all keys equal);
+# non-key columns that fit 64 bits carried through the passes as a payload.
 SORT_ROWS_CASES = [
     (3, 1, 20, 100_000, 1 << 20),
     (5, 4, 20, 300_001, 1 << 20),
@@ -99,16 +100,21 @@ SORT_ROWS_CASES = [
     (6, 5, 20, 1500, 1 << 20),
     (6, 6, 20, 2000, 4),
     (5, 1, 20, 100_000, 1),
+    (5, 2, 20, 300_001, 1 << 20),
+    (5, 3, 20, 100_000, 7),
+    (4, 1, 21, 70_000, 1 << 21),
+    (3, 2, 31, 10_000, 1 << 31),
 ]
 
 
+@pytest.mark.parametrize("flags", [0, 1, 2])  # by size, carried, gathered
 @pytest.mark.parametrize("V,m,bits,n,hi", SORT_ROWS_CASES)
-def test_sort_rows_matches_stable_lexsort(env, V, m, bits, n, hi):
+def test_sort_rows_matches_stable_lexsort(env, V, m, bits, n, hi, flags):
     g, torch = env
     rng = np.random.default_rng(V * 1000 + m * 100 + bits + n)
     cols = [rng.integers(0, hi, size=n, dtype=np.int64).astype(np.int32) for _ in range(V)]
     d = [torch.from_numpy(c.copy()).cuda() for c in cols]
-    out = g.sort_rows(d, m, bits)
+    out = g.sort_rows(d, m, bits, flags=flags)
     torch.cuda.synchronize()
     # np.lexsort is stable and takes its primary key last
     order = np.lexsort(cols[m - 1::-1]) if n else np.zeros(0, np.int64)
@@ -119,9 +125,9 @@ def test_sort_rows_matches_stable_lexsort(env, V, m, bits, n, hi):
 def test_sort_rows_rejects_bad_arguments(env):
     g, torch = env
     c = [torch.zeros(4, dtype=torch.int32, device="cuda") for _ in range(2)]
-    for m, bits in ((3, 8), (0, 8), (1, 0), (1, 32)):
+    for m, bits, flags in ((3, 8, 0), (0, 8, 0), (1, 0, 0), (1, 32, 0), (1, 8, 3)):
         with pytest.raises(g.GsmatError) as e:
-            g.sort_rows(c, m, bits)
+            g.sort_rows(c, m, bits, flags=flags)
         assert e.value.code == 1
 
 
