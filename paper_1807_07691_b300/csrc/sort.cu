@@ -1,4 +1,5 @@
-// Stable LSD radix sort of 32/64-bit keys with an optional 32-bit payload.
+// Stable LSD radix sort of 32/64-bit keys with an optional 32- or 64-bit
+// payload.
 //
 // Used by the store builder (sorting the triple set by (p, s, o) and
 // (p, o, s), which lays out every predicate's matrix M_h of Sec. 5.3 row by
@@ -15,9 +16,13 @@
 //
 // The canonical reorder of a result table (reorder_rows) runs the same passes
 // with the ends fused: the first pass packs each row's key from the table's
-// columns itself (payload = row index), and the last pass writes the sorted
-// table's columns directly (key fields unpacked, other columns gathered
-// through the payload), so no key array is packed or unpacked separately.
+// columns itself and the last pass writes the sorted table's columns
+// directly, so no key array is packed or unpacked separately.  The other
+// columns reach the output one of three ways: carried through the passes as
+// a packed 64-bit payload (when they fit it and are large), or gathered
+// after the sort through the row index (the payload, or the key's low bits
+// when index and key fit one word), column by column or as interleaved
+// records.  Tables of at most 2048 rows are sorted by one CTA instead.
 #include "common.cuh"
 #include "join.cuh"
 
