@@ -119,7 +119,8 @@ int64_t *pinned_scratch(int n_words);
 // outside it).
 void *pinned_scratch_device(const void *host_ptr);
 // h_dst[0..n) = the 8-byte words at d_src, written by a one-warp kernel on
-// `st` into the mapped scratch (h_dst must lie in it); synchronises `st`.
+// `st` into the mapped scratch (h_dst[0..n] must lie in it: h_dst[n] takes a
+// completion tag); returns once `st` has reached the copy.
 int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

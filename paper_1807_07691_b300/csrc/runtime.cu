@@ -146,16 +146,46 @@ void *pinned_scratch_device(const void *host_ptr) {
     return reinterpret_cast<char *>(h.d) + (hp - base);
 }
 
-__global__ void copy_words_kernel(const int64_t *__restrict__ src, int64_t *__restrict__ dst, int n) {
+// dst[0..n) = src[0..n), then (after a system-scope fence) dst[n] = tag.
+__global__ void copy_words_kernel(const int64_t *__restrict__ src, int64_t *__restrict__ dst, int n, int64_t tag) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        __threadfence_system();
+        *(volatile int64_t *)(dst + n) = tag;
+    }
 }
 
+// The copy kernel is the last work on the stream, so once its tag is in
+// host memory everything before it has finished: the host spins on the tag
+// (faster to wake than a stream synchronisation), asking the stream every
+// 1024 spins so that an error or a lost tag ends the wait.
 int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st) {
     void *d_dst = pinned_scratch_device(h_dst);
-    if (!d_dst) return set_error(GSMAT_ERR_INVALID_ARG, "read_words: destination outside the pinned scratch");
-    copy_words_kernel<<<1, 32, 0, st>>>(static_cast<const int64_t *>(d_src), static_cast<int64_t *>(d_dst), n_words);
+    if (!d_dst || !pinned_scratch_device(h_dst + n_words)) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "read_words: destination outside the pinned scratch");
+    }
+    static thread_local int64_t seq = 0;
+    const int64_t want = ++seq;
+    volatile int64_t *tag = h_dst + n_words;
+    *tag = 0;
+    copy_words_kernel<<<1, 32, 0, st>>>(static_cast<const int64_t *>(d_src), static_cast<int64_t *>(d_dst), n_words,
+                                        want);
     GS_LAUNCH_CHECK();
-    GS_CUDA(cudaStreamSynchronize(st));
+    for (uint64_t spin = 1; *tag != want; ++spin) {
+        if ((spin & 1023) == 0) {
+            const cudaError_t q = cudaStreamQuery(st);
+            if (q == cudaSuccess) {
+                if (*tag == want) break;
+                return set_error(GSMAT_ERR_CUDA, "read_words: stream idle but the read-back tag is missing");
+            }
+            if (q != cudaErrorNotReady) return set_error(GSMAT_ERR_CUDA, "read_words: %s", cudaGetErrorString(q));
+        }
+#if defined(__x86_64__)
+        __builtin_ia32_pause();
+#endif
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
     return GSMAT_OK;
 }
 
