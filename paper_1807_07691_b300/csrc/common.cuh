@@ -122,6 +122,11 @@ void *pinned_scratch_device(const void *host_ptr);
 // `st` into the mapped scratch (h_dst[0..n] must lie in it: h_dst[n] takes a
 // completion tag); returns once `st` has reached the copy.
 int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st);
+// Returns once `st` has finished its work so far (as cudaStreamSynchronize,
+// woken by a completion tag the stream writes into the mapped scratch's word
+// kScratchTagWord, which no other use of the scratch touches).
+constexpr int kScratchTagWord = 1023;
+int wait_stream(cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device view of the store

@@ -173,7 +173,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         GS_TRY(launch_const_lookup(S->view, S->pred_side_dev.as<PredSide>(), S->n_pred,
                                    static_cast<const int32_t *>(pinned_scratch_device(hreq)), n_req,
                                    static_cast<int32_t *>(pinned_scratch_device(hout)), st));
-        GS_CUDA(cudaStreamSynchronize(st));
+        GS_TRY(wait_stream(st));
         memcpy(rng.data(), hout, sizeof(int32_t) * rng.size());
     }
     auto row_len = [&](int r) -> int64_t { return r < 0 ? 0 : (int64_t)rng[2 * r + 1] - rng[2 * r]; };
@@ -470,6 +470,10 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         T->col[c] = fin.col[c];
     }
     T->storage = std::move(fin.buf);
+    // wait for the reorder or copy, whose bounded waits report into the same
+    // error word (the earlier returns follow a read of the last step's count)
+    int64_t unused = 0;
+    GS_TRY(cx.read_count(&unused));
     return GSMAT_OK;
 }
 
@@ -480,9 +484,10 @@ int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n
     if (!S || !out) return set_error(GSMAT_ERR_INVALID_ARG, "store or out is NULL");
     *out = nullptr;
     gsmat_table *T = new gsmat_table();
-    int rc = run(S, pats, n_pats, n_vars, flags, st, T);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (rc == GSMAT_OK && e != cudaSuccess) rc = set_error(GSMAT_ERR_CUDA, "query: %s", cudaGetErrorString(e));
+    // on success run() has waited for its last device work (its final read
+    // of the error word); a failed call drains what it enqueued
+    const int rc = run(S, pats, n_pats, n_vars, flags, st, T);
+    if (rc != GSMAT_OK) cudaStreamSynchronize(st);
     profile_flush();
     if (rc != GSMAT_OK) {
         delete T;
@@ -521,12 +526,12 @@ int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const in
     }
     T->storage = std::move(fin.buf);
     T->stats.result_rows = fin.rows;
-    GS_CUDA(cudaMemcpyAsync(cx.h, cx.qstat.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess || *reinterpret_cast<int *>(cx.h + 1)) {
+    int64_t unused = 0;
+    const int rc = cx.read_count(&unused);  // waits for the reorder, checks its bounded waits
+    if (rc != GSMAT_OK) {
+        cudaStreamSynchronize(st);
         delete T;
-        return e != cudaSuccess ? set_error(GSMAT_ERR_CUDA, "reorder: %s", cudaGetErrorString(e))
-                                : set_error(GSMAT_ERR_DEVICE_CHECK, "reorder: a bounded wait expired");
+        return rc;
     }
     T->storage.st = nullptr;
     *out = T;

@@ -160,26 +160,15 @@ __global__ void copy_words_kernel(const int64_t *__restrict__ src, int64_t *__re
 // host memory everything before it has finished: the host spins on the tag
 // (faster to wake than a stream synchronisation), asking the stream every
 // 1024 spins so that an error or a lost tag ends the wait.
-int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st) {
-    void *d_dst = pinned_scratch_device(h_dst);
-    if (!d_dst || !pinned_scratch_device(h_dst + n_words)) {
-        return set_error(GSMAT_ERR_INVALID_ARG, "read_words: destination outside the pinned scratch");
-    }
-    static thread_local int64_t seq = 0;
-    const int64_t want = ++seq;
-    volatile int64_t *tag = h_dst + n_words;
-    *tag = 0;
-    copy_words_kernel<<<1, 32, 0, st>>>(static_cast<const int64_t *>(d_src), static_cast<int64_t *>(d_dst), n_words,
-                                        want);
-    GS_LAUNCH_CHECK();
+static int spin_on_tag(volatile int64_t *tag, int64_t want, cudaStream_t st) {
     for (uint64_t spin = 1; *tag != want; ++spin) {
         if ((spin & 1023) == 0) {
             const cudaError_t q = cudaStreamQuery(st);
             if (q == cudaSuccess) {
                 if (*tag == want) break;
-                return set_error(GSMAT_ERR_CUDA, "read_words: stream idle but the read-back tag is missing");
+                return set_error(GSMAT_ERR_CUDA, "stream idle but the completion tag is missing");
             }
-            if (q != cudaErrorNotReady) return set_error(GSMAT_ERR_CUDA, "read_words: %s", cudaGetErrorString(q));
+            if (q != cudaErrorNotReady) return set_error(GSMAT_ERR_CUDA, "stream wait: %s", cudaGetErrorString(q));
         }
 #if defined(__x86_64__)
         __builtin_ia32_pause();
@@ -187,6 +176,34 @@ int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st) 
     }
     std::atomic_thread_fence(std::memory_order_acquire);
     return GSMAT_OK;
+}
+
+static thread_local int64_t t_tag_seq = 0;
+
+int read_words(const void *d_src, int64_t *h_dst, int n_words, cudaStream_t st) {
+    void *d_dst = pinned_scratch_device(h_dst);
+    if (!d_dst || !pinned_scratch_device(h_dst + n_words)) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "read_words: destination outside the pinned scratch");
+    }
+    const int64_t want = ++t_tag_seq;
+    volatile int64_t *tag = h_dst + n_words;
+    *tag = 0;
+    copy_words_kernel<<<1, 32, 0, st>>>(static_cast<const int64_t *>(d_src), static_cast<int64_t *>(d_dst), n_words,
+                                        want);
+    GS_LAUNCH_CHECK();
+    return spin_on_tag(tag, want, st);
+}
+
+int wait_stream(cudaStream_t st) {
+    int64_t *h = pinned_scratch(kScratchTagWord + 1);
+    if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    const int64_t want = ++t_tag_seq;
+    volatile int64_t *tag = h + kScratchTagWord;
+    *tag = 0;
+    copy_words_kernel<<<1, 32, 0, st>>>(nullptr, static_cast<int64_t *>(pinned_scratch_device(h + kScratchTagWord)), 0,
+                                        want);
+    GS_LAUNCH_CHECK();
+    return spin_on_tag(tag, want, st);
 }
 
 // ---------------------------------------------------------------------------
