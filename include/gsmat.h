@@ -396,7 +396,9 @@ GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, cons
 /* Stable LSD radix sort of n uint64 keys on bits [begin_bit, end_bit),
  * 8 bits per pass, with an optional uint32 payload (d_vals may be NULL).
  * d_keys / d_vals are device arrays, sorted in place.  0 <= n < 2^32.
- * Scratch comes from the allocator hook.  Does not synchronise. */
+ * Scratch comes from the allocator hook.  Does not synchronise, so a
+ * bounded wait that expires inside (a predecessor tile that never publishes
+ * its counts) is not reported: the output is then unspecified. */
 GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int begin_bit, int end_bit,
                                    gsmat_stream_t stream);
 
@@ -408,7 +410,8 @@ GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n
  * significant first, each chunk being 8-bit onesweep passes whose first pass
  * packs the keys from the columns and whose last pass writes d_out.
  * 1 <= m <= V <= 32, 1 <= bits <= 31, 0 <= n < 2^32; d_out must not alias
- * d_cols.  Scratch comes from the allocator hook.  Does not synchronise. */
+ * d_cols.  Scratch comes from the allocator hook.  Does not synchronise, so a
+ * bounded wait that expires inside is not reported (output unspecified). */
 GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bits, int64_t n,
                               int32_t *const *d_out, uint32_t flags, gsmat_stream_t stream);
 /* flags of gsmat_sort_rows: how the other V - m columns reach d_out when
@@ -420,7 +423,8 @@ GSMAT_API int gsmat_sort_rows(const int32_t *const *d_cols, int V, int m, int bi
 /* Exclusive prefix sum of n int32 counts (each >= 0) into d_out[0..n]
  * (int64; d_out[n] = total), single pass with decoupled look-back over
  * tiles.  Scratch (tile descriptors) comes from the allocator hook.
- * Does not synchronise. */
+ * Does not synchronise, so a bounded wait that expires inside is not
+ * reported (output unspecified). */
 GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int64_t n, gsmat_stream_t stream);
 
 /* The same exclusive prefix sum, for callers that cannot allocate device
