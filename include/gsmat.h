@@ -244,6 +244,10 @@ typedef struct {
     int32_t compact_results; /* 1: after each run, copy the results into one right-sized
                                 buffer and release the arena (results then outlive the
                                 arena's reuse; costs one copy of the result rows) */
+    int32_t reorder_mode; /* results above 2048 rows: how their non-key columns reach the
+                             reordered output when they fit a 64-bit payload (0: by size,
+                             GSMAT_SORT_CARRY or GSMAT_SORT_GATHER as for gsmat_sort_rows) */
+    int32_t _pad;
 } gsmat_batch_config;
 
 typedef struct {

@@ -411,6 +411,42 @@ __global__ void seg_pack_kernel(const SegDesc *__restrict__ segs, int n_segs, in
     }
 }
 
+// Carried columns: keys[g] = (segment << kb) | the key variables [0, m) of
+// row g (`bits` each), pay[g] = the segment's other variables [m, V) packed
+// the same way (rows in segment order, before the sort).
+__global__ void seg_pack_wide_kernel(const SegDesc *__restrict__ segs, int n_segs, int bits, int m, int kb,
+                                     int64_t total, uint64_t *__restrict__ keys, uint64_t *__restrict__ pay) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int lo = seg_of(reinterpret_cast<const int64_t *>(segs + n_segs), n_segs, g);
+        const SegDesc &s = segs[lo];
+        const int64_t r = g - s.row_off;
+        uint64_t key = 0, p = 0;
+        for (int v = 0; v < m; ++v) key = (key << bits) | (uint32_t)__ldg(s.col[v] + r);
+        for (int v = m; v < s.V; ++v) p = (p << bits) | (uint32_t)__ldg(s.col[v] + r);
+        keys[g] = ((uint64_t)lo << kb) | key;
+        pay[g] = p;
+    }
+}
+
+// The sorted rows of every segment from the carried key and payload (the
+// segment index is the key's most significant field, so each segment keeps
+// its positions).
+__global__ void seg_unpack_wide_kernel(const SegDesc *__restrict__ segs, int n_segs, int bits, int m, int64_t total,
+                                       const uint64_t *__restrict__ keys, const uint64_t *__restrict__ pay) {
+    const uint64_t fmask = (1ull << bits) - 1;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int lo = seg_of(reinterpret_cast<const int64_t *>(segs + n_segs), n_segs, g);
+        const SegDesc &s = segs[lo];
+        const int64_t i = g - s.row_off;
+        const uint64_t key = __ldg(keys + g), p = __ldg(pay + g);
+        for (int v = 0; v < m; ++v) s.out[(size_t)v * s.rows + i] = (int32_t)((key >> ((m - 1 - v) * bits)) & fmask);
+        const int nr = s.V - m;
+        for (int v = m; v < s.V; ++v) {
+            s.out[(size_t)v * s.rows + i] = (int32_t)((p >> ((nr - 1 - (v - m)) * bits)) & fmask);
+        }
+    }
+}
+
 __global__ void key_low_bits_kernel(const uint64_t *__restrict__ keys, int idx_bits, int64_t total,
                                     uint32_t *__restrict__ perm) {
     const uint64_t mask = (1ull << idx_bits) - 1;
@@ -440,6 +476,22 @@ int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, i
                                                          total, keys, perm_out);
     GS_LAUNCH_CHECK();
     t.stop();
+    return GSMAT_OK;
+}
+
+int launch_seg_pack_wide(const SegDesc *segs, int n_segs, int bits, int m, int kb, int64_t total, uint64_t *keys,
+                         uint64_t *pay, cudaStream_t st) {
+    if (total <= 0) return GSMAT_OK;
+    seg_pack_wide_kernel<<<grid_1d(total, 256), 256, 0, st>>>(segs, n_segs, bits, m, kb, total, keys, pay);
+    GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+int launch_seg_unpack_wide(const SegDesc *segs, int n_segs, int bits, int m, int64_t total, const uint64_t *keys,
+                           const uint64_t *pay, cudaStream_t st) {
+    if (total <= 0) return GSMAT_OK;
+    seg_unpack_wide_kernel<<<grid_1d(total, 256), 256, 0, st>>>(segs, n_segs, bits, m, total, keys, pay);
+    GS_LAUNCH_CHECK();
     return GSMAT_OK;
 }
 

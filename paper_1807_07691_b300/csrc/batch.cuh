@@ -90,6 +90,13 @@ struct SegDesc {
 // perm_out is not written), else perm_out[g] = g when perm_in is null.
 int launch_seg_pack(const SegDesc *segs, int n_segs, int bits, int vb, int ve, int seg_shift, int idx_bits,
                     const uint32_t *perm_in, int64_t total, uint64_t *keys, uint32_t *perm_out, cudaStream_t st);
+// Carried columns of a segmented reorder: keys = (segment << kb) | the
+// variables [0, m); pay = the segment's variables [m, V); and back into each
+// segment's out after the sort.
+int launch_seg_pack_wide(const SegDesc *segs, int n_segs, int bits, int m, int kb, int64_t total, uint64_t *keys,
+                         uint64_t *pay, cudaStream_t st);
+int launch_seg_unpack_wide(const SegDesc *segs, int n_segs, int bits, int m, int64_t total, const uint64_t *keys,
+                           const uint64_t *pay, cudaStream_t st);
 // perm[g] = the low idx_bits bits of keys[g].
 int launch_key_low_bits(const uint64_t *keys, int idx_bits, int64_t total, uint32_t *perm, cudaStream_t st);
 // out rows of every segment from the rows perm[p] (a plain copy when perm

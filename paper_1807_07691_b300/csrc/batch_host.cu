@@ -94,6 +94,10 @@ int resolve_config(const gsmat_batch_config *in, gsmat_batch_config *out) {
         c.use_graph = in->use_graph;
         c.compact_results = in->compact_results;
         if (c.compact_results) c.use_graph = 0;  // the arena is re-allocated per run
+        c.reorder_mode = in->reorder_mode;
+    }
+    if (c.reorder_mode < 0 || c.reorder_mode > (int)GSMAT_SORT_GATHER) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "bad batch reorder_mode %d", c.reorder_mode);
     }
     if (c.block != 128 && c.block != 256 && c.block != 512) {
         return set_error(GSMAT_ERR_INVALID_ARG, "batch block must be 128, 256 or 512 (got %d)", c.block);
@@ -373,43 +377,66 @@ int reorder_group(gsmat_batch *B, const std::vector<int> &qs, int m, int bits) {
     }
     DevBuf d_segs, keys, perm, err;
     GS_TRY(upload_segs(segs, d_segs, B->priv));
-    GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)total, B->priv));
-    GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)total, B->priv));
     GS_TRY(err.alloc(sizeof(int), B->priv));
     GS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), B->priv));
-    // chunks: head [0, h) shares the key with the segment index; the tail
-    // [h, m) in chunks of per_key variables, sorted first
-    const int per_key = 64 / bits;
-    const int h = std::min(m, (64 - seg_bits) / bits);
-    std::vector<std::pair<int, int>> chunks;  // least significant first
-    for (int e = m; e > h;) {
-        const int b0 = std::max(h, e - per_key);
-        chunks.push_back({b0, e});
-        e = b0;
-    }
-    chunks.push_back({0, h});
-    // a chunk whose key bits and the source position fit one 64-bit word
-    // sorts keys alone (8 bytes per row and pass instead of 12)
-    const int idx_bits = std::max(1, bits_for((uint64_t)(total - 1)));
-    for (size_t c = 0; c < chunks.size(); ++c) {
-        const int vb = chunks[c].first, ve = chunks[c].second;
-        const bool last = c + 1 == chunks.size();
-        const int kb = (ve - vb) * bits;
-        const int key_bits = last ? kb + seg_bits : kb;
-        const bool packed = key_bits + idx_bits <= 64;
-        GS_TRY(launch_seg_pack(d_segs.as<SegDesc>(), (int)segs.size(), bits, vb, ve, last ? kb : -1,
-                               packed ? idx_bits : 0, c == 0 ? nullptr : perm.as<uint32_t>(), total,
-                               keys.as<uint64_t>(), perm.as<uint32_t>(), B->priv));
-        if (packed) {
-            GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, total, idx_bits, idx_bits + key_bits, B->priv,
-                                  err.as<int>()));
-            GS_TRY(launch_key_low_bits(keys.as<uint64_t>(), idx_bits, total, perm.as<uint32_t>(), B->priv));
-        } else {
-            GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), total, 0, key_bits, B->priv,
-                                  err.as<int>()));
+    // The other variables travel with the key when they fit 64 bits, the
+    // key (with the segment index) one word of at most five passes, and the
+    // rows are well beyond L2 (as the plain reorder decides): no gather.
+    int max_rest = 0;
+    for (const SegDesc &d : segs) max_rest = std::max(max_rest, d.V - m);
+    const int kb_all = m * bits;
+    const int n_pass_all = (kb_all + seg_bits + 7) / 8;
+    const bool can_carry = kb_all + seg_bits <= 64 && max_rest > 0 && max_rest * bits <= 64;
+    const int mode = B->cfg.reorder_mode;
+    const bool carry = mode == GSMAT_SORT_CARRY ||
+                       (mode == 0 && n_pass_all <= 5 && (double)total * max_rest * 4.0 > 256.0 * (1 << 20));
+    if (can_carry && carry) {
+        DevBuf pay;
+        GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)total, B->priv));
+        GS_TRY(pay.alloc(sizeof(uint64_t) * (size_t)total, B->priv));
+        GS_TRY(launch_seg_pack_wide(d_segs.as<SegDesc>(), (int)segs.size(), bits, m, kb_all, total,
+                                    keys.as<uint64_t>(), pay.as<uint64_t>(), B->priv));
+        GS_TRY(radix_sort_u64_wide(keys.as<uint64_t>(), pay.as<uint64_t>(), total, 0, kb_all + seg_bits, B->priv,
+                                   err.as<int>()));
+        GS_TRY(launch_seg_unpack_wide(d_segs.as<SegDesc>(), (int)segs.size(), bits, m, total, keys.as<uint64_t>(),
+                                      pay.as<uint64_t>(), B->priv));
+    } else {
+        GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)total, B->priv));
+        GS_TRY(perm.alloc(sizeof(uint32_t) * (size_t)total, B->priv));
+        // chunks: head [0, h) shares the key with the segment index; the tail
+        // [h, m) in chunks of per_key variables, sorted first
+        const int per_key = 64 / bits;
+        const int h = std::min(m, (64 - seg_bits) / bits);
+        std::vector<std::pair<int, int>> chunks;  // least significant first
+        for (int e = m; e > h;) {
+            const int b0 = std::max(h, e - per_key);
+            chunks.push_back({b0, e});
+            e = b0;
         }
+        chunks.push_back({0, h});
+        // a chunk whose key bits and the source position fit one 64-bit word
+        // sorts keys alone (8 bytes per row and pass instead of 12)
+        const int idx_bits = std::max(1, bits_for((uint64_t)(total - 1)));
+        for (size_t c = 0; c < chunks.size(); ++c) {
+            const int vb = chunks[c].first, ve = chunks[c].second;
+            const bool last = c + 1 == chunks.size();
+            const int kb = (ve - vb) * bits;
+            const int key_bits = last ? kb + seg_bits : kb;
+            const bool packed = key_bits + idx_bits <= 64;
+            GS_TRY(launch_seg_pack(d_segs.as<SegDesc>(), (int)segs.size(), bits, vb, ve, last ? kb : -1,
+                                   packed ? idx_bits : 0, c == 0 ? nullptr : perm.as<uint32_t>(), total,
+                                   keys.as<uint64_t>(), perm.as<uint32_t>(), B->priv));
+            if (packed) {
+                GS_TRY(radix_sort_u64(keys.as<uint64_t>(), nullptr, total, idx_bits, idx_bits + key_bits, B->priv,
+                                      err.as<int>()));
+                GS_TRY(launch_key_low_bits(keys.as<uint64_t>(), idx_bits, total, perm.as<uint32_t>(), B->priv));
+            } else {
+                GS_TRY(radix_sort_u64(keys.as<uint64_t>(), perm.as<uint32_t>(), total, 0, key_bits, B->priv,
+                                      err.as<int>()));
+            }
+        }
+        GS_TRY(launch_seg_gather(d_segs.as<SegDesc>(), (int)segs.size(), total, perm.as<uint32_t>(), B->priv));
     }
-    GS_TRY(launch_seg_gather(d_segs.as<SegDesc>(), (int)segs.size(), total, perm.as<uint32_t>(), B->priv));
     int herr = 0;
     GS_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, B->priv));
     GS_CUDA(cudaStreamSynchronize(B->priv));

@@ -391,6 +391,9 @@ int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
                    int *err_word = nullptr);
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
                    int *err_word = nullptr);
+// As radix_sort_u64 with a 64-bit payload (required).
+int radix_sort_u64_wide(uint64_t *keys, uint64_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
+                        int *err_word = nullptr);
 // Exclusive scan of int32 counts into int64[n+1]; *err_word (device int) is
 // set if a bounded wait expired (may be null).
 int exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st, int *err_word);

@@ -665,30 +665,31 @@ struct SortMeta {
     }
 };
 
-template <class K, bool HasVals>
-int sort_passes(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word) {
+template <class K, bool HasVals, class V = uint32_t>
+int sort_passes(K *keys, V *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word) {
+    using SA = SrcArray<K, HasVals, V>;
+    using KA = SinkArray<K, HasVals, V>;
     const int n_pass = (end_bit - begin_bit + 7) / 8;
     SortMeta meta;
-    GS_TRY(meta.make(n, n_pass, kPassBlock * items_per_thread<K, HasVals>(), st, err_word));
+    GS_TRY(meta.make(n, n_pass, kPassBlock * items_per_thread<K, HasVals, V>(), st, err_word));
     DevBuf alt_k, alt_v;
     GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
-    if (HasVals) GS_TRY(alt_v.alloc(sizeof(uint32_t) * (size_t)n, st));
-    GS_TRY((launch_histogram<K, SrcArray<K, HasVals>>(SrcArray<K, HasVals>{keys, vals}, n, begin_bit, end_bit, n_pass,
-                                                     meta.hist, st)));
+    if (HasVals) GS_TRY(alt_v.alloc(sizeof(V) * (size_t)n, st));
+    GS_TRY((launch_histogram<K, SA>(SA{keys, vals}, n, begin_bit, end_bit, n_pass, meta.hist, st)));
     K *src_k = keys, *dst_k = alt_k.as<K>();
-    uint32_t *src_v = vals, *dst_v = alt_v.as<uint32_t>();
+    V *src_v = vals, *dst_v = alt_v.as<V>();
     for (int p = 0; p < n_pass; ++p) {
         const int shift = begin_bit + 8 * p;
         const int width = end_bit - shift < 8 ? end_bit - shift : 8;
-        GS_TRY((launch_pass<K, HasVals, SrcArray<K, HasVals>, SinkArray<K, HasVals>>(
-            SrcArray<K, HasVals>{src_k, src_v}, SinkArray<K, HasVals>{dst_k, dst_v}, n, shift, width,
-            meta.hist + p * kBins, meta.desc, meta.counters + p, (uint32_t)(p + 1), meta.err, st)));
+        GS_TRY((launch_pass<K, HasVals, SA, KA>(SA{src_k, src_v}, KA{dst_k, dst_v}, n, shift, width,
+                                               meta.hist + p * kBins, meta.desc, meta.counters + p, (uint32_t)(p + 1),
+                                               meta.err, st)));
         K *tk = src_k; src_k = dst_k; dst_k = tk;
-        uint32_t *tv = src_v; src_v = dst_v; dst_v = tv;
+        V *tv = src_v; src_v = dst_v; dst_v = tv;
     }
     if (src_k != keys) {
         GS_CUDA(cudaMemcpyAsync(keys, src_k, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        if (HasVals) GS_CUDA(cudaMemcpyAsync(vals, src_v, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+        if (HasVals) GS_CUDA(cudaMemcpyAsync(vals, src_v, sizeof(V) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     }
     return GSMAT_OK;
 }
@@ -705,7 +706,8 @@ int radix_sort_impl(K *keys, uint32_t *vals, int64_t n, int begin_bit, int end_b
     const int n_pass = (end_bit - begin_bit + 7) / 8;
     KernelTimer t(timer_name, st, (double)n * (2.0 * sizeof(K) + (vals ? 8.0 : 0.0)) * n_pass, (double)n);
     const int rc = vals ? sort_passes<K, true>(keys, vals, n, begin_bit, end_bit, st, err_word)
-                        : sort_passes<K, false>(keys, nullptr, n, begin_bit, end_bit, st, err_word);
+                        : sort_passes<K, false>(keys, static_cast<uint32_t *>(nullptr), n, begin_bit, end_bit, st,
+                                                err_word);
     if (rc != GSMAT_OK) return rc;
     t.stop();
     return GSMAT_OK;
@@ -750,6 +752,20 @@ int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
                    int *err_word) {
     return radix_sort_impl<uint32_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u32", err_word);
+}
+
+int radix_sort_u64_wide(uint64_t *keys, uint64_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
+                        int *err_word) {
+    if (n < 0 || begin_bit < 0 || end_bit > 64 || begin_bit > end_bit || !vals) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "radix sort: bad arguments");
+    }
+    if (n <= 1 || begin_bit == end_bit) return GSMAT_OK;
+    if (n > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "radix sort: n = %lld >= 2^32", (long long)n);
+    const int n_pass = (end_bit - begin_bit + 7) / 8;
+    KernelTimer t("radix_sort_u64", st, (double)n * 32.0 * n_pass, (double)n);
+    GS_TRY((sort_passes<uint64_t, true, uint64_t>(keys, vals, n, begin_bit, end_bit, st, err_word)));
+    t.stop();
+    return GSMAT_OK;
 }
 
 namespace {

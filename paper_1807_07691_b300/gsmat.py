@@ -72,7 +72,8 @@ class BGPStruct(ctypes.Structure):
 
 class BatchConfig(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
-                ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("compact_results", ctypes.c_int32)]
+                ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("compact_results", ctypes.c_int32),
+                ("reorder_mode", ctypes.c_int32), ("_pad", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -400,6 +401,7 @@ def _config(cfg):
     c.max_rows = int(cfg.get("max_rows", 0))
     c.use_graph = int(cfg.get("use_graph", 1))
     c.compact_results = int(cfg.get("compact_results", 0))
+    c.reorder_mode = int(cfg.get("reorder_mode", 0))
     return c
 
 

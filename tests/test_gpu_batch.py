@@ -141,15 +141,16 @@ def test_batch_autotune(gs, tiny):
         assert np.array_equal(B.to_numpy(i), ix.query(q))
 
 
-def test_batched_mix_on_medium_matches_plain_path(gs):
+@pytest.mark.parametrize("reorder_mode", [0, 1, 2])  # by size, carried, gathered
+def test_batched_mix_on_medium_matches_plain_path(gs, reorder_mode):
     import torch
 
     t = synth.make_graph("medium")
     qs = synth.make_batched_queries(512)
     S = gs.Store(torch.from_numpy(np.array(t, copy=True)).cuda())
-    B = gs.Batch(S, qs).execute()
+    B = gs.Batch(S, qs, config={"reorder_mode": reorder_mode}).execute()
     st = B.stats()
-    assert st["n_in_kernel"] > 0.5 * len(qs)
+    assert st["n_in_kernel"] > 0.5 * len(qs) and st["n_reordered"] > 0
     for i, q in enumerate(qs):
         a = B.to_numpy(i)
         b = S.query(q).to_numpy()
