@@ -38,7 +38,7 @@ static std::mutex g_alloc_mu;
 static gsmat_alloc_fn g_alloc = nullptr;
 static gsmat_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
-static bool g_pool_configured[64] = {false};
+static bool g_pool_configured[64] = {false};  // guarded by g_alloc_mu
 
 static void configure_default_pool() {
     int dev = 0;
@@ -216,7 +216,7 @@ struct ProfAgg {
 
 static std::mutex g_prof_mu;
 static std::map<std::string, ProfAgg> g_prof;
-static volatile bool g_prof_on = false;
+static std::atomic<bool> g_prof_on{false};
 
 struct PendingTimer {
     const char *name;
@@ -240,11 +240,11 @@ static cudaEvent_t get_event() {
     return e;
 }
 
-bool profile_on() { return g_prof_on; }
+bool profile_on() { return g_prof_on.load(std::memory_order_relaxed); }
 
 KernelTimer::KernelTimer(const char *n, cudaStream_t s, double algo_bytes, double n_items)
     : name(n), st(s), bytes(algo_bytes), items(n_items) {
-    if (!g_prof_on) return;
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
     a = get_event();
     b = get_event();
     if (!a || !b) {
@@ -286,7 +286,7 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int profile_enable(int on) {
-    g_prof_on = on != 0;
+    g_prof_on.store(on != 0, std::memory_order_relaxed);
     return GSMAT_OK;
 }
 

@@ -23,6 +23,8 @@
 // after the sort through the row index (the payload, or the key's low bits
 // when index and key fit one word), column by column or as interleaved
 // records.  Tables of at most 2048 rows are sorted by one CTA instead.
+#include <atomic>
+
 #include "common.cuh"
 #include "join.cuh"
 
@@ -577,19 +579,19 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
 }
 
 int sm_count() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) dev = 0;
-    if (!cached[dev]) {
-        int v = 0;
+    int v = cached[dev].load(std::memory_order_acquire);
+    if (!v) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
             cudaGetLastError();
             v = 148;
         }
-        cached[dev] = v;
+        cached[dev].store(v, std::memory_order_release);
     }
-    return cached[dev];
+    return v;
 }
 
 template <class K, bool HasVals, class V>
@@ -608,16 +610,16 @@ template <class K, bool HasVals, class Src, class Sink>
 int launch_pass(const Src &src, const Sink &sink, int64_t n, int shift, int width, const uint32_t *hist_pass,
                 unsigned long long *desc, unsigned int *counter, uint32_t epoch, int *err, cudaStream_t st) {
     using V = typename Src::Val;
-    static bool done[64] = {false};
+    static std::atomic<bool> done[64];  // attributes set (once per device; setting them twice is harmless)
     const int dev = current_device();
-    if (!done[dev]) {
+    if (!done[dev].load(std::memory_order_acquire)) {
         GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      pass_smem_bytes<K, HasVals, V>()));
         // the driver's own carveout: forcing the maximum shared memory left
         // too little L1 for the passes that gather through a permutation
         GS_CUDA(cudaFuncSetAttribute(onesweep_pass<K, HasVals, Src, Sink>,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutDefault));
-        done[dev] = true;
+        done[dev].store(true, std::memory_order_release);
     }
     constexpr int TILE = kPassBlock * items_per_thread<K, HasVals, V>();
     const int64_t ntiles = (n + TILE - 1) / TILE;
