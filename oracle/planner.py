@@ -29,9 +29,24 @@ multiplies the running estimate by
   EXPAND  from a bound variable end   nnz / (non-zero rows on that side)
   FILTER  (both ends bound/constant)  min(1, nnz / (nr_s * nr_o))
 and the cost is the sum of the running estimates over all steps.
+
+Cost-based variant (the planner that Thm. 2 motivates; Alg. 1 only
+approaches its minimum greedily): over all *connected* orders of a BGP of at
+most 8 patterns -- orders in which every step after the first takes a
+pattern sharing a variable with the patterns taken so far, unless no
+remaining pattern does -- take one of least cost.  Readings: the cost is
+accumulated step by step in fp64 (the argmin is a decision taken in
+floating point, so the summation order is fixed); among equal costs the
+order that comes first when orders are compared as sequences of positions
+in the stable key order wins (Alg. 1's order is the first connected order
+in that comparison, so it wins any tie it is part of); above 8 patterns the
+variant is Alg. 1.  Written here as the definition: every permutation,
+filtered, costed, first minimum.
 """
 
 from __future__ import annotations
+
+import itertools
 
 STEP_CROSS = 0
 STEP_EXPAND_S = 1  # subject end known, object end a new variable (CSR side)
@@ -114,6 +129,46 @@ def estimate(patterns, order, keys, stats) -> tuple:
         kinds.append(kind)
         bound |= pattern_vars(pat)
     return per_step, sum(per_step), kinds
+
+
+def is_connected_order(patterns, order) -> bool:
+    """Every step shares a variable with the steps before it, unless no
+    remaining pattern does (then a Cartesian product is unavoidable)."""
+    seen = set(pattern_vars(patterns[order[0]]))
+    for k in range(1, len(order)):
+        vs = pattern_vars(patterns[order[k]])
+        if not (vs & seen):
+            rest = order[k:]
+            if any(pattern_vars(patterns[j]) & seen for j in rest):
+                return False
+        seen |= vs
+    return True
+
+
+def order_cost(patterns, order, keys, stats) -> float:
+    """Sum of the running estimates, accumulated in step order in fp64."""
+    per_step, _, _ = estimate(patterns, order, keys, stats)
+    total = 0.0
+    for e in per_step:
+        total = total + e
+    return total
+
+
+def cost_plan_order(patterns, keys, stats, max_patterns: int = 8) -> list:
+    """Least-cost connected order (see the module docstring); Alg. 1's order
+    for BGPs of more than ``max_patterns`` patterns."""
+    n = len(patterns)
+    if n > max_patterns:
+        return plan_order(patterns, keys)
+    L = sorted(range(n), key=lambda i: (keys[i], i))
+    best_cost, best = None, None
+    for perm in itertools.permutations(L):  # lexicographic in key positions
+        if not is_connected_order(patterns, perm):
+            continue
+        c = order_cost(patterns, perm, keys, stats)
+        if best_cost is None or c < best_cost:
+            best_cost, best = c, list(perm)
+    return best
 
 
 def upper_bound_sum(sizes) -> int:

@@ -286,6 +286,104 @@ def test_plan_first_pattern_has_smallest_key():
         assert order[0] == keys.index(min(keys))
 
 
+# --------------------------------------------------------------------------
+# Cost-based planner variant (Thm. 2 motivates minimising the accumulated
+# estimate; Alg. 1 approaches it greedily)
+
+
+def _chain_abc():
+    # ?x A ?y . ?y B ?z . ?z C ?w -- A is the smallest matrix, but all of its
+    # 100 entries point at one object, whose row in B holds 150 entries
+    pats = [(0, 1, 1, 1, 1), (1, 2, 2, 1, 1), (2, 3, 3, 1, 1)]
+    stats = [dict(nnz=100, nr_s=100, nr_o=1), dict(nnz=150, nr_s=1, nr_o=150), dict(nnz=200, nr_s=200, nr_o=200)]
+    keys = [100, 150, 200]
+    return pats, keys, stats
+
+
+def test_cost_plan_worked_chain():
+    """Costs written out by hand for every connected order of the chain
+    A-B-C (running estimates: CROSS -> key, EXPAND -> nnz / nr of the bound
+    side):
+      A,B,C: 100, 100*150/1, *200/200        -> 100 + 15000 + 15000 = 30100
+      B,A,C: 150, 150*100/1, *200/200        -> 150 + 15000 + 15000 = 30150
+      B,C,A: 150, 150*200/200, *100/1        -> 150 + 150 + 15000   = 15300
+      C,B,A: 200, 200*150/150, *100/1        -> 200 + 200 + 20000   = 20400
+    (A,C,B and C,A,B join two patterns that share nothing while B connects)."""
+    pats, keys, stats = _chain_abc()
+    assert planner.plan_order(pats, keys) == [0, 1, 2]
+    assert planner.order_cost(pats, [0, 1, 2], keys, stats) == 30100.0
+    order = planner.cost_plan_order(pats, keys, stats)
+    assert order == [1, 2, 0]
+    per_step, _, kinds = planner.estimate(pats, order, keys, stats)
+    assert per_step == [150.0, 150.0, 15000.0]
+    assert kinds == [planner.STEP_CROSS, planner.STEP_EXPAND_S, planner.STEP_EXPAND_O]
+    assert planner.order_cost(pats, order, keys, stats) == 15300.0
+    assert not planner.is_connected_order(pats, [0, 2, 1])
+    assert planner.is_connected_order(pats, [2, 1, 0])
+
+
+def test_cost_plan_tie_keeps_alg1_order():
+    """Two patterns of key 4 (nnz 4 over 2 rows on each side) sharing ?y:
+    either order costs 4 + 4*2 = 12, so the stable key order (Alg. 1's) is
+    kept; with the keys swapped the other order is Alg. 1's and is kept."""
+    pats = [(0, 1, 1, 1, 1), (1, 2, 2, 1, 1)]
+    st = [dict(nnz=4, nr_s=2, nr_o=2)] * 2
+    assert planner.order_cost(pats, [0, 1], [4, 4], st) == planner.order_cost(pats, [1, 0], [4, 4], st) == 12.0
+    assert planner.cost_plan_order(pats, [4, 4], st) == [0, 1]
+    assert planner.cost_plan_order(pats, [5, 4], st) == [1, 0] == planner.plan_order(pats, [5, 4])
+
+
+def test_cost_plan_disconnected_bgp_takes_a_cartesian_step():
+    # {?x A ?y} and {?z B ?w} share nothing: both orders are connected in the
+    # sense above; costs 3 + 3*7 = 24 (A first) and 7 + 7*3 = 28 (B first)
+    pats = [(0, 1, 1, 1, 1), (2, 2, 3, 1, 1)]
+    st = [dict(nnz=3, nr_s=3, nr_o=3), dict(nnz=7, nr_s=7, nr_o=7)]
+    assert planner.is_connected_order(pats, [1, 0])
+    assert planner.cost_plan_order(pats, [3, 7], st) == [0, 1]
+    assert planner.order_cost(pats, [0, 1], [3, 7], st) == 24.0
+
+
+def test_cost_plan_never_costs_more_than_alg1_and_stays_connected():
+    rng = np.random.default_rng(11)
+    improved = 0
+    for _ in range(120):
+        n = int(rng.integers(1, 7))
+        pats = [(int(rng.integers(4)), int(rng.integers(3)), int(rng.integers(4)), 1, int(rng.random() < 0.9))
+                for _ in range(n)]
+        keys = rng.integers(1, 1000, size=n).tolist()
+        stats = [dict(nnz=int(rng.integers(1, 5000)), nr_s=int(rng.integers(1, 100)), nr_o=int(rng.integers(1, 100)))
+                 for _ in range(n)]
+        g = planner.plan_order(pats, keys)
+        c = planner.cost_plan_order(pats, keys, stats)
+        assert sorted(c) == list(range(n))
+        assert planner.is_connected_order(pats, c) and planner.is_connected_order(pats, g)
+        gc, cc = planner.order_cost(pats, g, keys, stats), planner.order_cost(pats, c, keys, stats)
+        assert cc <= gc
+        improved += cc < gc
+    assert improved > 10
+
+
+def test_cost_plan_above_eight_patterns_is_alg1():
+    pats = [(i, 1, i + 1, 1, 1) for i in range(9)]
+    keys = list(range(9, 0, -1))
+    st = [dict(nnz=10, nr_s=5, nr_o=5)] * 9
+    assert planner.cost_plan_order(pats, keys, st) == planner.plan_order(pats, keys)
+
+
+def test_cost_plan_result_is_the_same_relation(tiny):
+    """The plan changes the order of the joins, never the relation (Sec. 6.1):
+    the oracle evaluated in the cost plan's order gives the same rows."""
+    t, ix, qs = tiny
+    st = storage.statistics(t)
+    for q in qs:
+        stats = [st[p[1]] for p in q.patterns]
+        keys = [s["nnz"] for s in stats]
+        order = planner.cost_plan_order(q.patterns, keys, stats)
+        want = ix.query(q.patterns, q.n_vars)
+        got = ix.query([q.patterns[i] for i in order], q.n_vars)
+        assert np.array_equal(got, want)
+
+
 def test_large_served_mix_counts_match_the_oracle():
     # the anchored sampler's exact counts (stars, chains) on the tiny graph
     t = synth.make_graph("tiny")
