@@ -160,12 +160,19 @@ typedef struct {
 #define GSMAT_COUNT_ONLY 2u   /* compute the row count only; the table has no columns */
 #define GSMAT_NO_INTERSECT 4u /* join strictly one pattern per step (Alg. 2 as printed): no
                                  fusion of an expand with a later filter into an intersection */
+#define GSMAT_PLAN_COST 8u    /* plan by least estimated cost instead of Alg. 1's greedy choice
+                                 (see gsmat_plan_cost); the result is the same */
+
+/* Largest BGP that the cost-based planner searches exhaustively (larger
+ * BGPs keep Alg. 1's order). */
+#define GSMAT_PLAN_COST_MAX 8
 
 /* Evaluate a BGP.
  *  pats, n_pats   host array of 1 <= n_pats <= 64 patterns.
  *  n_vars         0 <= n_vars <= 32; every variable 0..n_vars-1 must occur.
  * The plan is Alg. 1 (connected minimal upper bound) with the
- * intermediate-size estimate of Sec. 6.2; each step is one SM-based join
+ * intermediate-size estimate of Sec. 6.2 (with GSMAT_PLAN_COST, the
+ * connected order of least estimated cost, gsmat_plan_cost); each step is one SM-based join
  * (Alg. 3) of the running relation with the next pattern's matrix:
  * a gather-expand along the pattern's CSR or CSC rows when one end is bound,
  * a membership filter with prefix-sum compaction when both ends are bound,
@@ -247,7 +254,8 @@ typedef struct {
     int32_t reorder_mode; /* results above 2048 rows: how their non-key columns reach the
                              reordered output when they fit a 64-bit payload (0: by size,
                              GSMAT_SORT_CARRY or GSMAT_SORT_GATHER as for gsmat_sort_rows) */
-    int32_t _pad;
+    int32_t plan_cost;    /* 0: plan every query by Alg. 1; 1: by least estimated cost, as
+                             GSMAT_PLAN_COST (the results are the same) */
 } gsmat_batch_config;
 
 typedef struct {
@@ -263,7 +271,8 @@ typedef struct {
 } gsmat_batch_stats_t;
 
 /* Plan a batch of n >= 1 BGPs against a store and prepare its device run.
- * Each query is planned by Alg. 1 (Sec. 6.2) into a step program; all
+ * Each query is planned by Alg. 1 (Sec. 6.2; by least estimated cost when
+ * cfg->plan_cost) into a step program; all
  * programs are uploaded together; the device work (queue and arena reset,
  * the persistent kernel, the copy of result descriptors) is captured as a
  * CUDA graph when cfg->use_graph (cfg may be NULL: defaults).  Validation
@@ -392,6 +401,21 @@ GSMAT_API void gsmat_server_destroy(gsmat_server *srv);
 GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
                          const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out,
                          double *est_out);
+
+/* Cost-based variant (Thm. 2 makes the accumulated estimate the quantity a
+ * plan should keep small; Alg. 1 only approximates its minimum greedily).
+ * Same arguments and outputs as gsmat_plan.  Among the connected orders --
+ * orders in which every step takes a pattern sharing a variable with the
+ * patterns before it, unless no remaining pattern does -- returns one whose
+ * cost (sum of the running estimates, computed as gsmat_plan computes them)
+ * is least; among equal costs, the one that comes first when orders are
+ * compared as sequences of positions in the stable key order, so Alg. 1's
+ * order (itself connected) is kept on a tie.  Exhaustive with pruning for
+ * n_pats <= GSMAT_PLAN_COST_MAX (at most 8! orders), Alg. 1 above that.
+ * Never costs more than gsmat_plan's order.  Errors as gsmat_plan. */
+GSMAT_API int gsmat_plan_cost(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
+                              const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out,
+                              double *est_out);
 
 /* ------------------------------------------------------------------------ */
 /* Device primitives used by the store builder and the join (exported so     */

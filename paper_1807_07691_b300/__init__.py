@@ -8,7 +8,8 @@ library raises ImportError then.
 """
 
 _BINDING_NAMES = {
-    "COUNT_ONLY", "NO_INTERSECT", "PLAN_ORDER", "SORTED", "GsmatError", "Store", "Table", "Batch", "batch_autotune",
+    "COUNT_ONLY", "NO_INTERSECT", "PLAN_COST", "PLAN_COST_MAX", "PLAN_ORDER", "SORTED", "GsmatError", "Store",
+    "Table", "Batch", "batch_autotune",
     "Server", "exclusive_scan_i32", "exclusive_scan_i32_noalloc", "exclusive_scan_i32_noalloc_max",
     "header_functions", "launch_count", "lib", "plan", "profile_enable", "profile_read", "radix_sort_u64", "sort_rows",
     "SORT_CARRY", "SORT_GATHER", "use_torch_allocator",

@@ -260,6 +260,15 @@ GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, cons
     return gs::plan_bgp(pats, n_pats, keys, stats, order_out, kinds_out, est_out);
 }
 
+GSMAT_API int gsmat_plan_cost(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
+                              const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out,
+                              double *est_out) {
+    gs::clear_error();
+    GS_TRY(gs::validate_bgp(pats, n_pats, n_vars));
+    if (!keys || !stats || !order_out) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    return gs::plan_bgp_cost(pats, n_pats, keys, stats, order_out, kinds_out, est_out);
+}
+
 GSMAT_API int gsmat_radix_sort_u64(uint64_t *d_keys, uint32_t *d_vals, int64_t n, int begin_bit, int end_bit,
                                    gsmat_stream_t stream) {
     gs::clear_error();

@@ -95,6 +95,10 @@ int resolve_config(const gsmat_batch_config *in, gsmat_batch_config *out) {
         c.compact_results = in->compact_results;
         if (c.compact_results) c.use_graph = 0;  // the arena is re-allocated per run
         c.reorder_mode = in->reorder_mode;
+        c.plan_cost = in->plan_cost;
+    }
+    if (c.plan_cost != 0 && c.plan_cost != 1) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "bad batch plan_cost %d (0 or 1)", c.plan_cost);
     }
     if (c.reorder_mode < 0 || c.reorder_mode > (int)GSMAT_SORT_GATHER) {
         return set_error(GSMAT_ERR_INVALID_ARG, "bad batch reorder_mode %d", c.reorder_mode);
@@ -255,7 +259,8 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
             else keys[k] = st[k].nnz;
         }
         std::vector<int32_t> order(np), kinds(np);
-        GS_TRY(plan_bgp(P, np, keys.data(), st.data(), order.data(), kinds.data(), nullptr));
+        GS_TRY((B->cfg.plan_cost ? plan_bgp_cost : plan_bgp)(P, np, keys.data(), st.data(), order.data(),
+                                                             kinds.data(), nullptr));
         BQuery &Q = B->hq[i];
         memset(&Q, 0, sizeof(Q));
         Q.step0 = (int32_t)B->hs.size();
@@ -586,7 +591,8 @@ int finish(gsmat_batch *B) {
             B->path[i] = 2;
             s.n_reordered++;
         } else {
-            GS_TRY(query_run(B->S, B->pats[i].data(), (int)B->pats[i].size(), B->hq[i].n_vars, GSMAT_SORTED, B->priv,
+            GS_TRY(query_run(B->S, B->pats[i].data(), (int)B->pats[i].size(), B->hq[i].n_vars,
+                             B->cfg.plan_cost ? GSMAT_PLAN_COST : GSMAT_SORTED, B->priv,
                              &B->owned[i]));
             B->path[i] = 1;
             s.n_fallback++;

@@ -14,6 +14,15 @@
 // side (EXPAND from a variable), or by min(1, nnz / (nr_s * nr_o)) (FILTER);
 // the cost is the sum of the running estimates, the quantity Thm. 1 and
 // Thm. 2 bound.
+//
+// Alg. 1 is greedy: it fixes the first pattern by its statistic alone and
+// never revisits a choice.  The cost-based variant keeps the estimate and
+// the connectivity rule but minimises the cost itself: over every connected
+// order of a BGP of at most kCostPlanMax patterns (each step takes a
+// pattern sharing a variable with those taken, unless none remains that
+// does), it returns one of least cost; among equal costs, the one whose
+// sequence of positions in the key order is smallest, which makes Alg. 1's
+// order the winner of any tie it is part of.
 #include <string.h>
 
 #include <algorithm>
@@ -30,6 +39,15 @@ uint64_t vars_of(const gsmat_pattern &p) {
     if (p.s_var) m |= uint64_t(1) << p.s;
     if (p.o_var) m |= uint64_t(1) << p.o;
     return m;
+}
+
+// Running-estimate factor of a pattern taken as a step of the given kind.
+double step_factor(const gsmat_pattern &p, int kind, int64_t key, const gsmat_pred_stats &st) {
+    const double nnz = (double)st.nnz, nr_s = (double)st.nr_s, nr_o = (double)st.nr_o;
+    if (kind == GSMAT_STEP_CROSS) return (double)key;
+    if (kind == GSMAT_STEP_FILTER) return (nr_s > 0 && nr_o > 0) ? std::min(1.0, nnz / (nr_s * nr_o)) : 0.0;
+    if (kind == GSMAT_STEP_EXPAND_S) return !p.s_var ? (double)key : (nr_s > 0 ? nnz / nr_s : 0.0);
+    return !p.o_var ? (double)key : (nr_o > 0 ? nnz / nr_o : 0.0);
 }
 
 }  // namespace
@@ -71,21 +89,98 @@ int plan_bgp(const gsmat_pattern *pats, int n, const int64_t *keys, const gsmat_
         const int i = order[step];
         const gsmat_pattern &p = pats[i];
         const int kind = step_kind(p, bound);
-        const double nnz = (double)stats[i].nnz, nr_s = (double)stats[i].nr_s, nr_o = (double)stats[i].nr_o;
-        double f;
-        if (kind == GSMAT_STEP_CROSS) {
-            f = (double)keys[i];
-        } else if (kind == GSMAT_STEP_FILTER) {
-            f = (nr_s > 0 && nr_o > 0) ? std::min(1.0, nnz / (nr_s * nr_o)) : 0.0;
-        } else if (kind == GSMAT_STEP_EXPAND_S) {
-            f = !p.s_var ? (double)keys[i] : (nr_s > 0 ? nnz / nr_s : 0.0);
-        } else {
-            f = !p.o_var ? (double)keys[i] : (nr_o > 0 ? nnz / nr_o : 0.0);
-        }
-        e = e * f;
+        e = e * step_factor(p, kind, keys[i], stats[i]);
         if (kinds) kinds[step] = kind;
         if (est) est[step] = e;
         bound |= vars_of(p);
+    }
+    return GSMAT_OK;
+}
+
+namespace {
+
+// Depth-first search over the connected orders (an order is connected when
+// each step takes a pattern sharing a variable with those already taken,
+// unless no remaining pattern does), branching on the remaining patterns in
+// the key order of Alg. 1, so the first complete order reached is Alg. 1's.
+// An order replaces the best one only when its cost is strictly smaller;
+// since every running estimate is >= 0, a prefix whose partial sum already
+// reaches the best cost cannot lead to a strictly smaller one and is cut.
+struct CostSearch {
+    const gsmat_pattern *pats;
+    const int64_t *keys;
+    const gsmat_pred_stats *stats;
+    int n;
+    int L[kCostPlanMax];        // pattern indices in key order
+    uint64_t vm[kCostPlanMax];  // variables of L[t]
+    int cur[kCostPlanMax];
+    int best_order[kCostPlanMax];
+    double best;
+
+    void run(int depth, unsigned taken, uint64_t bound, double e, double partial) {
+        if (depth == n) {
+            if (partial < best) {
+                best = partial;
+                for (int d = 0; d < n; ++d) best_order[d] = cur[d];
+            }
+            return;
+        }
+        bool connected = false;
+        if (depth > 0) {
+            for (int t = 0; t < n && !connected; ++t) connected = !((taken >> t) & 1) && (vm[t] & bound);
+        }
+        for (int t = 0; t < n; ++t) {
+            if ((taken >> t) & 1) continue;
+            if (connected && !(vm[t] & bound)) continue;
+            const int i = L[t];
+            const double e2 = e * step_factor(pats[i], step_kind(pats[i], bound), keys[i], stats[i]);
+            const double p2 = partial + e2;
+            if (!(p2 < best)) continue;
+            cur[depth] = i;
+            run(depth + 1, taken | (1u << t), bound | vm[t], e2, p2);
+        }
+    }
+};
+
+}  // namespace
+
+int plan_bgp_cost(const gsmat_pattern *pats, int n, const int64_t *keys, const gsmat_pred_stats *stats,
+                  int32_t *order, int32_t *kinds, double *est) {
+    std::vector<double> greedy_est(n);
+    const int rc = plan_bgp(pats, n, keys, stats, order, kinds, greedy_est.data());
+    if (rc != GSMAT_OK) return rc;
+    if (n > kCostPlanMax) {
+        if (est) memcpy(est, greedy_est.data(), sizeof(double) * (size_t)n);
+        return GSMAT_OK;
+    }
+    CostSearch cs;
+    cs.pats = pats;
+    cs.keys = keys;
+    cs.stats = stats;
+    cs.n = n;
+    for (int i = 0; i < n; ++i) cs.L[i] = i;
+    std::stable_sort(cs.L, cs.L + n, [&](int a, int b) { return keys[a] < keys[b]; });
+    for (int t = 0; t < n; ++t) cs.vm[t] = vars_of(pats[cs.L[t]]);
+    // Alg. 1's order is the first connected order of the search: start from
+    // it, so that it wins every tie and bounds the search from the outset
+    double greedy_cost = 0.0;
+    for (int d = 0; d < n; ++d) {
+        greedy_cost += greedy_est[d];
+        cs.best_order[d] = order[d];
+    }
+    cs.best = greedy_cost;
+    cs.run(0, 0u, 0, 1.0, 0.0);
+    // kinds and running estimates of the chosen order
+    uint64_t bound = 0;
+    double e = 1.0;
+    for (int d = 0; d < n; ++d) {
+        const int i = cs.best_order[d];
+        const int kind = step_kind(pats[i], bound);
+        e = e * step_factor(pats[i], kind, keys[i], stats[i]);
+        order[d] = i;
+        if (kinds) kinds[d] = kind;
+        if (est) est[d] = e;
+        bound |= vars_of(pats[i]);
     }
     return GSMAT_OK;
 }

@@ -16,6 +16,15 @@ int step_kind(const gsmat_pattern &p, uint64_t bound);
 int plan_bgp(const gsmat_pattern *pats, int n, const int64_t *keys, const gsmat_pred_stats *stats, int32_t *order,
              int32_t *kinds, double *est);
 
+// Largest BGP the cost-based variant searches exhaustively.
+constexpr int kCostPlanMax = GSMAT_PLAN_COST_MAX;
+
+// Cost-based variant: the connected order of least estimated cost (sum of
+// the running estimates), Alg. 1's order on ties; Alg. 1 above
+// kCostPlanMax patterns.  Same outputs as plan_bgp.
+int plan_bgp_cost(const gsmat_pattern *pats, int n, const int64_t *keys, const gsmat_pred_stats *stats,
+                  int32_t *order, int32_t *kinds, double *est);
+
 // Shape checks shared by gsmat_plan and gsmat_query.
 int validate_bgp(const gsmat_pattern *pats, int n_pats, int n_vars);
 

@@ -124,7 +124,7 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
 int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
         gsmat_table *T) {
     GS_TRY(validate_bgp(pats, n_pats, n_vars));
-    if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY | GSMAT_NO_INTERSECT)) {
+    if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY | GSMAT_NO_INTERSECT | GSMAT_PLAN_COST)) {
         return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     }
     Ctx cx;
@@ -193,7 +193,8 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
     gsmat_query_stats &qs = T->stats;
     memset(&qs, 0, sizeof(qs));
     qs.n_steps = n_pats;
-    GS_TRY(plan_bgp(pats, n_pats, keys.data(), stats.data(), qs.order, qs.kind, qs.est_rows));
+    GS_TRY(((flags & GSMAT_PLAN_COST) ? plan_bgp_cost : plan_bgp)(pats, n_pats, keys.data(), stats.data(), qs.order,
+                                                                   qs.kind, qs.est_rows));
     for (int s = 0; s < n_pats; ++s) {
         qs.est_cost += qs.est_rows[s];
         qs.rows[s] = -1;

@@ -120,7 +120,7 @@ namespace {
 // Estimated device bytes of one request: the plan's accumulated estimate
 // (Sec. 6.2) with constant rows taken at their predicate's average row size,
 // times the widest row, for tables and their temporaries.
-double estimate_bytes(const gsmat_store *S, const gsmat_pattern *pats, int n, int n_vars) {
+double estimate_bytes(const gsmat_store *S, const gsmat_pattern *pats, int n, int n_vars, bool plan_cost) {
     std::vector<int64_t> keys(n);
     std::vector<gsmat_pred_stats> st(n);
     for (int i = 0; i < n; ++i) {
@@ -139,7 +139,10 @@ double estimate_bytes(const gsmat_store *S, const gsmat_pattern *pats, int n, in
     }
     std::vector<int32_t> order(n), kinds(n);
     std::vector<double> est(n);
-    if (plan_bgp(pats, n, keys.data(), st.data(), order.data(), kinds.data(), est.data()) != GSMAT_OK) return 1e12;
+    if ((plan_cost ? plan_bgp_cost : plan_bgp)(pats, n, keys.data(), st.data(), order.data(), kinds.data(),
+                                               est.data()) != GSMAT_OK) {
+        return 1e12;
+    }
     double total = 0;
     for (double e : est) total += e;
     return 4096.0 + total * 4.0 * std::max(1, n_vars) * 2.0;
@@ -175,8 +178,9 @@ void lone_loop(gsmat_server *srv) {
             bytes = srv->lone_bytes;
         }
         auto holder = std::make_shared<TableHolder>();
-        const int rc = query_run(srv->S, r->pats.data(), (int)r->pats.size(), r->n_vars, GSMAT_SORTED, srv->lone_stream,
-                                 &holder->T);
+        const uint32_t flags = srv->cfg.batch.plan_cost ? GSMAT_PLAN_COST : GSMAT_SORTED;
+        const int rc =
+            query_run(srv->S, r->pats.data(), (int)r->pats.size(), r->n_vars, flags, srv->lone_stream, &holder->T);
         profile_flush();
         const Clock::time_point now = Clock::now();
         std::lock_guard<std::mutex> lk(srv->mu);
@@ -374,6 +378,10 @@ int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_se
         delete srv;
         return set_error(GSMAT_ERR_INVALID_ARG, "server slots or max_batch out of range");
     }
+    if (c.batch.plan_cost != 0 && c.batch.plan_cost != 1) {
+        delete srv;
+        return set_error(GSMAT_ERR_INVALID_ARG, "bad batch plan_cost %d (0 or 1)", c.batch.plan_cost);
+    }
     srv->cfg = c;
     cudaGetDevice(&srv->device);
     if (cudaStreamCreateWithFlags(&srv->prep_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -410,7 +418,7 @@ int server_submit(gsmat_server *srv, const gsmat_pattern *pats, int n_pats, int 
     auto r = std::make_shared<Request>();
     r->pats.assign(pats, pats + n_pats);
     r->n_vars = n_vars;
-    r->est_bytes = estimate_bytes(srv->S, pats, n_pats, n_vars);
+    r->est_bytes = estimate_bytes(srv->S, pats, n_pats, n_vars, srv->cfg.batch.plan_cost != 0);
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return set_error(GSMAT_ERR_INVALID_ARG, "server is shutting down");

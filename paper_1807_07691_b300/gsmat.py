@@ -29,6 +29,8 @@ SORTED = 0
 PLAN_ORDER = 1
 COUNT_ONLY = 2
 NO_INTERSECT = 4
+PLAN_COST = 8
+PLAN_COST_MAX = 8
 
 STEP_CROSS, STEP_EXPAND_S, STEP_EXPAND_O, STEP_FILTER = 0, 1, 2, 3
 MAX_PATTERNS = 64
@@ -73,7 +75,7 @@ class BGPStruct(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
                 ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("compact_results", ctypes.c_int32),
-                ("reorder_mode", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+                ("reorder_mode", ctypes.c_int32), ("plan_cost", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -124,6 +126,7 @@ def _load():
         "gsmat_table_stats": ([vp, P(QueryStats)], c_int),
         "gsmat_table_free": ([vp], None),
         "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
+        "gsmat_plan_cost": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
         "gsmat_batch_prepare": ([vp, vp, i32, vp, vp, P(vp)], c_int),
         "gsmat_batch_execute": ([vp, vp], c_int),
         "gsmat_batch_result": ([vp, i32, P(i64), P(i32), P(i32)], c_int),
@@ -402,6 +405,7 @@ def _config(cfg):
     c.use_graph = int(cfg.get("use_graph", 1))
     c.compact_results = int(cfg.get("compact_results", 0))
     c.reorder_mode = int(cfg.get("reorder_mode", 0))
+    c.plan_cost = int(cfg.get("plan_cost", 0))
     return c
 
 
@@ -548,12 +552,13 @@ def batch_autotune(store: "Store", bgps, base: dict | None = None, stream=None) 
     _check(_lib.gsmat_batch_autotune(store.handle, arr, len(bgps), ctypes.byref(cfg) if cfg else None,
                                      _stream_ptr(stream), ctypes.byref(best)))
     return {"block": best.block, "ctas_per_sm": best.ctas_per_sm, "arena_bytes": best.arena_bytes,
-            "max_rows": best.max_rows, "use_graph": best.use_graph}
+            "max_rows": best.max_rows, "use_graph": best.use_graph, "plan_cost": best.plan_cost}
 
 
-def plan(bgp, keys, stats, n_vars=None):
-    """Host planner (Alg. 1): (order, kinds, est) for given per-pattern keys
-    and predicate statistics (list of dicts with nnz, nr_s, nr_o)."""
+def plan(bgp, keys, stats, n_vars=None, cost: bool = False):
+    """Host planner (Alg. 1; with ``cost``, the least-cost connected order of
+    gsmat_plan_cost): (order, kinds, est) for given per-pattern keys and
+    predicate statistics (list of dicts with nnz, nr_s, nr_o)."""
     pats, n, nv = _patterns(bgp)
     n_vars = nv if n_vars is None else n_vars
     k = np.ascontiguousarray(np.asarray(keys, dtype=np.int64))
@@ -563,8 +568,8 @@ def plan(bgp, keys, stats, n_vars=None):
     order = np.zeros(n, np.int32)
     kinds = np.zeros(n, np.int32)
     est = np.zeros(n, np.float64)
-    _check(_lib.gsmat_plan(pats, n, int(n_vars), k.ctypes.data, st, order.ctypes.data, kinds.ctypes.data,
-                           est.ctypes.data))
+    fn = _lib.gsmat_plan_cost if cost else _lib.gsmat_plan
+    _check(fn(pats, n, int(n_vars), k.ctypes.data, st, order.ctypes.data, kinds.ctypes.data, est.ctypes.data))
     return order.tolist(), kinds.tolist(), est.tolist()
 
 

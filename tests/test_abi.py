@@ -91,6 +91,50 @@ def test_plan_matches_oracle_planner(gs, seed):
     assert np.allclose(est, o_est, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("seed", range(40))
+def test_cost_plan_matches_oracle(gs, seed):
+    """gsmat_plan_cost = the oracle's least-cost connected order, bit for bit
+    (the argmin is taken in fp64 on both sides, step-order sums)."""
+    rng = np.random.default_rng(1000 + seed)
+    pats, nv, keys, stats = _random_case(rng)
+    order, kinds, est = gs.plan(pats, keys, stats, n_vars=nv, cost=True)
+    o_order = oplan.cost_plan_order(pats, keys, stats)
+    assert order == o_order
+    o_est, _, o_kinds = oplan.estimate(pats, o_order, keys, stats)
+    assert kinds == o_kinds
+    assert est == o_est
+
+
+def test_cost_plan_worked_chain_and_limits(gs):
+    # the chain A-B-C of the oracle's worked example: Alg. 1 costs 30100,
+    # the least-cost connected order (B, C, A) 15300
+    pats = [(0, 1, 1, 1, 1), (1, 2, 2, 1, 1), (2, 3, 3, 1, 1)]
+    stats = [dict(nnz=100, nr_s=100, nr_o=1), dict(nnz=150, nr_s=1, nr_o=150), dict(nnz=200, nr_s=200, nr_o=200)]
+    keys = [100, 150, 200]
+    assert gs.plan(pats, keys, stats, n_vars=4)[0] == [0, 1, 2]
+    order, kinds, est = gs.plan(pats, keys, stats, n_vars=4, cost=True)
+    assert order == [1, 2, 0] and est == [150.0, 150.0, 15000.0]
+    # above GSMAT_PLAN_COST_MAX patterns: Alg. 1
+    n = gs.PLAN_COST_MAX + 1
+    chain = [(i, 1, i + 1, 1, 1) for i in range(n)]
+    k = list(range(n, 0, -1))
+    st = [dict(nnz=10, nr_s=5, nr_o=5)] * n
+    assert gs.plan(chain, k, st, n_vars=n + 1, cost=True) == gs.plan(chain, k, st, n_vars=n + 1)
+    with pytest.raises(gs.GsmatError) as e:
+        gs.plan([(0, 5, 1, 1, 1)], [1], [dict(nnz=1, nr_s=1, nr_o=1)], n_vars=3, cost=True)
+    assert e.value.code == 1
+
+
+def test_cost_plan_on_tiny_workload(gs):
+    t = synth.make_graph("tiny")
+    st = storage.statistics(t)
+    for q in synth.make_queries("tiny", t):
+        stats = [st[p[1]] for p in q.patterns]
+        keys = [s["nnz"] for s in stats]
+        order, kinds, est = gs.plan(q, keys, stats, cost=True)
+        assert order == oplan.cost_plan_order(q.patterns, keys, stats)
+
+
 def test_plan_on_tiny_workload(gs):
     t = synth.make_graph("tiny")
     st = storage.statistics(t)

@@ -141,14 +141,29 @@ def test_batch_autotune(gs, tiny):
         assert np.array_equal(B.to_numpy(i), ix.query(q))
 
 
-@pytest.mark.parametrize("reorder_mode", [0, 1, 2])  # by size, carried, gathered
-def test_batched_mix_on_medium_matches_plain_path(gs, reorder_mode):
+def test_batch_cost_plan(gs, tiny):
+    t, ix, S, qs = tiny
+    items = [(q.patterns, q.n_vars) for q in qs] + _mixed_bgps(t, 80, 21)
+    items = [it for it in items if _small(ix, it)]
+    B = gs.Batch(S, [p for p, _ in items], n_vars_list=[v for _, v in items], config={"plan_cost": 1}).execute()
+    _check_all(B, items, ix)
+    # a row cap that sends the large ones to the plain path, planned the same way
+    B = gs.Batch(S, [p for p, _ in items], n_vars_list=[v for _, v in items],
+                 config={"plan_cost": 1, "max_rows": 100}).execute()
+    _check_all(B, items, ix)
+    with pytest.raises(gs.GsmatError) as e:
+        gs.Batch(S, qs, config={"plan_cost": 2})
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("reorder_mode,plan_cost", [(0, 0), (1, 0), (2, 0), (0, 1)])
+def test_batched_mix_on_medium_matches_plain_path(gs, reorder_mode, plan_cost):
     import torch
 
     t = synth.make_graph("medium")
     qs = synth.make_batched_queries(512)
     S = gs.Store(torch.from_numpy(np.array(t, copy=True)).cuda())
-    B = gs.Batch(S, qs, config={"reorder_mode": reorder_mode}).execute()
+    B = gs.Batch(S, qs, config={"reorder_mode": reorder_mode, "plan_cost": plan_cost}).execute()
     st = B.stats()
     assert st["n_in_kernel"] > 0.5 * len(qs) and st["n_reordered"] > 0
     for i, q in enumerate(qs):

@@ -4,7 +4,9 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle.planner as oplan
 import synth
+from oracle import storage
 from tests.helpers import golden, is_sorted_unique, random_bgp
 
 pytestmark = pytest.mark.gpu
@@ -222,3 +224,75 @@ def test_cycles_use_intersect_expand(gs, tiny):
         assert S.query(pats, V, flags=gs.COUNT_ONLY).shape[0] == want.shape[0]
         n_isect += 4 in T.stats()["kind"]
     assert n_isect > 10
+
+
+def _plan_inputs(t, pats):
+    """Per-pattern keys and predicate statistics as the query computes them:
+    nnz for a pattern without constants, the constant's row size otherwise
+    (the smaller row with two constants), zeros for an absent predicate."""
+    u = storage.unique_triples(t).astype(np.int64)
+    st = storage.statistics(t)
+    keys, stats = [], []
+    for (s, p, o, sv, ov) in [tuple(x[:5]) for x in pats]:
+        if p not in st:
+            keys.append(0)
+            stats.append(dict(nnz=0, nr_s=0, nr_o=0))
+            continue
+        stats.append(st[p])
+        rs = int(np.sum((u[:, 1] == p) & (u[:, 0] == s))) if not sv else None
+        ro = int(np.sum((u[:, 1] == p) & (u[:, 2] == o))) if not ov else None
+        if rs is not None and ro is not None:
+            keys.append(min(rs, ro))
+        elif rs is not None:
+            keys.append(rs)
+        elif ro is not None:
+            keys.append(ro)
+        else:
+            keys.append(st[p]["nnz"])
+    return keys, stats
+
+
+def test_cost_plan_same_relation_and_plan(gs, tiny):
+    """GSMAT_PLAN_COST: the same relation as the oracle's, by the plan that
+    gsmat_plan_cost gives for the store's statistics, never estimated to cost
+    more than Alg. 1's."""
+    t, ix, S, qs = tiny
+    rng = np.random.default_rng(5)
+    items = [(q.patterns, q.n_vars) for q in qs]
+    while len(items) < 60:
+        pats, V = random_bgp(rng, t, n_vars_max=5, n_pats_max=6, p_const=0.3)
+        try:
+            ix.query(pats, V, row_limit=2_000_000)
+        except oracle.OracleError:
+            continue
+        items.append((pats, V))
+    changed = 0
+    for pats, V in items:
+        want = ix.query(pats, V)
+        T = S.query(pats, V, flags=gs.PLAN_COST)
+        assert np.array_equal(T.to_numpy(), want), pats
+        st = T.stats()
+        keys, stats = _plan_inputs(t, pats)
+        if all(s["nnz"] > 0 for s in stats):  # (an absent predicate: empty, whatever the plan)
+            order, kinds, est = gs.plan(pats, keys, stats, n_vars=V, cost=True)
+            assert st["order"] == order == oplan.cost_plan_order(pats, keys, stats)
+        g = S.query(pats, V).stats()
+        assert st["est_cost"] <= g["est_cost"]
+        changed += st["order"] != g["order"]
+        assert S.query(pats, V, flags=gs.PLAN_COST | gs.COUNT_ONLY).shape == (want.shape[0], 0)
+        P = S.query(pats, V, flags=gs.PLAN_COST | gs.PLAN_ORDER)
+        ref = want[:, P.col_vars]
+        ref = ref[np.lexsort(ref.T[::-1])] if len(ref) else ref
+        assert np.array_equal(P.to_numpy(), ref)
+    assert changed > 0
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_cost_plan_random_small_graphs(gs, seed):
+    rng = np.random.default_rng(5000 + seed)
+    t = synth.small_random_graph(int(rng.integers(3, 12)), 3, int(rng.integers(1, 80)), seed=seed,
+                                 pred_ids=np.array([3, 77, 123456]))
+    pats, V = random_bgp(rng, t, n_vars_max=5, n_pats_max=7)
+    want = oracle.oracle_query(t, pats, V)
+    got = gs.Store(t).query(pats, V, flags=gs.PLAN_COST).to_numpy()
+    assert got.shape == want.shape and np.array_equal(got, want)

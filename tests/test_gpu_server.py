@@ -63,6 +63,20 @@ def test_results_same_alone_and_in_the_mix(gs, tiny):
     srv.close()
 
 
+def test_cost_plan_server(gs, tiny):
+    # micro-batches, the lone lane and the admission estimate all plan by cost
+    S, items, alone = tiny
+    srv = gs.Server(S, max_batch=16, slots=2, batch={"plan_cost": 1})
+    tickets = _run(srv, items)
+    for t, want in zip(tickets, alone):
+        assert np.array_equal(srv.to_numpy(t), want)
+        srv.release(t)
+    assert srv.stats()["failed"] == 0
+    srv.close()
+    with pytest.raises(gs.GsmatError):
+        gs.Server(S, batch={"plan_cost": 3})
+
+
 def test_tight_budget_and_concurrent_submitters(gs, tiny):
     S, items, alone = tiny
     srv = gs.Server(S, max_batch=8, slots=2, budget_bytes=1 << 20)
