@@ -260,8 +260,11 @@ def run_gsmat(args):
 
     batched = None
     served = None
+    planner = None
     if not args.no_batched:
-        batched, bq = run_batched(args, gs, torch, d_tri, stream)
+        batched, bq, tuned = run_batched(args, gs, torch, d_tri, stream)
+        if not args.no_planner:
+            planner = run_planner(args, gs, torch, d_tri, stream, queries, bq, tuned)
         if not args.no_served:
             served = run_served(args, gs, torch, d_tri, stream, bq)
     served_large = None
@@ -328,6 +331,8 @@ def run_gsmat(args):
     }
     if batched is not None:
         out["batched"] = batched
+    if planner is not None:
+        out["planner"] = planner
     if served is not None:
         out["served"] = served
     if served_large is not None:
@@ -411,7 +416,76 @@ def run_batched(args, gs, torch, d_tri, stream):
     }
     B.free()
     S.free()
-    return out, bq
+    return out, bq, tuned
+
+
+def run_planner(args, gs, torch, d_tri, stream, queries, bq, tuned):
+    """Alg. 1 against the cost-based variant (GSMAT_PLAN_COST): the medium
+    workload one query at a time with the store resident (three passes each,
+    the median), and the batched mix as one prepared batch; per variant the
+    device time, the intermediate rows the plans produce and the planner's
+    estimated cost."""
+    S = gs.Store(d_tri, stream=stream)
+    marsh = [gs.Store.marshal(q) for q in queries]
+
+    def plain(flags):
+        ms, inter, est, orders = [], 0, 0.0, []
+        for rep in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            tabs = [S.query_raw(q, flags=flags, stream=stream) for q in marsh]
+            b.record(stream)
+            b.synchronize()
+            if rep:
+                ms.append(a.elapsed_time(b))
+            if rep == 1:
+                for T in tabs:
+                    st = T.stats()
+                    inter += sum(r for r in st["rows"] if r > 0)
+                    est += st["est_cost"]
+                    orders.append(st["order"])
+            for T in tabs:
+                T.free()
+        return float(np.median(ms)), inter, est, orders
+
+    g_ms, g_inter, g_est, g_orders = plain(gs.SORTED)
+    c_ms, c_inter, c_est, c_orders = plain(gs.PLAN_COST)
+    nq = len(queries)
+
+    def batched(plan_cost):
+        cfg = dict(tuned, plan_cost=plan_cost)
+        t0 = time.perf_counter()
+        B = gs.Batch(S, bq, config=cfg, stream=stream)
+        prep = 1e3 * (time.perf_counter() - t0)
+        B.execute(stream)
+        runs = []
+        for _ in range(max(3, args.steps)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            B.execute(stream)
+            b.record(stream)
+            b.synchronize()
+            runs.append(a.elapsed_time(b))
+        rows = sum(B.result(i)[0] for i in range(len(bq)))
+        B.free()
+        return float(np.median(runs)), prep, rows
+
+    bg_ms, bg_prep, bg_rows = batched(0)
+    bc_ms, bc_prep, bc_rows = batched(1)
+    assert bg_rows == bc_rows, (bg_rows, bc_rows)
+    S.free()
+    return {
+        "workload": f"medium, {nq} BGPs one at a time (store resident); batched mix of {len(bq)} BGPs",
+        "plain": {"alg1_queries_per_s": round(nq / (g_ms / 1e3), 1), "cost_queries_per_s": round(nq / (c_ms / 1e3), 1),
+                  "plans_changed": sum(a != b for a, b in zip(g_orders, c_orders)),
+                  "alg1_intermediate_rows": int(g_inter), "cost_intermediate_rows": int(c_inter),
+                  "alg1_est_cost": g_est, "cost_est_cost": c_est},
+        "batched": {"alg1_queries_per_s": round(len(bq) / (bg_ms / 1e3), 1),
+                    "cost_queries_per_s": round(len(bq) / (bc_ms / 1e3), 1),
+                    "alg1_prepare_ms": round(bg_prep, 2), "cost_prepare_ms": round(bc_prep, 2)},
+    }
 
 
 def _spin_until(t):
@@ -670,6 +744,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-n", type=int, default=4096)
+    ap.add_argument("--no-planner", action="store_true", help="skip Alg. 1 vs the cost-based planner")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--served-rates", type=float, nargs="+", default=[1000, 5000, 20000])

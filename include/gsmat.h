@@ -229,6 +229,22 @@ GSMAT_API int gsmat_table_stats(const gsmat_table *table, gsmat_query_stats *sta
 
 GSMAT_API void gsmat_table_free(gsmat_table *table);
 
+/* Projection and DISTINCT (the Select|Project form of Sec. 3.2): a new
+ * table whose columns are the given variables of `table`, in the order
+ * given, with every row of `table` restricted to them (distinct = 0) or
+ * each such row once (distinct = 1); rows ascend lexicographically over the
+ * new columns.  Runs on the device: a stable radix reorder by the new
+ * columns (skipped when they are already the table's leading columns,
+ * whose rows are sorted) and, for DISTINCT, a comparison of each row with
+ * its predecessor and a stable compaction.
+ *  vars       host int32[n], distinct variable numbers held by `table`
+ *             (1 <= n <= its columns).
+ * Errors: INVALID_ARG (a variable the table does not hold, a repeated one,
+ * a count-only table), OOM, CUDA, DEVICE_CHECK.  Synchronises `stream`.
+ * The new table is independent of `table`. */
+GSMAT_API int gsmat_table_project(const gsmat_table *table, const int32_t *vars, int32_t n, int distinct,
+                                  gsmat_stream_t stream, gsmat_table **out);
+
 /* ------------------------------------------------------------------------ */
 /* Batched evaluation: many BGPs in one persistent kernel                    */
 /* (the same results as gsmat_query with GSMAT_SORTED, query by query)       */
@@ -382,6 +398,86 @@ GSMAT_API int gsmat_server_stats(gsmat_server *srv, gsmat_server_stats_t *stats)
 /* Stop admitting, finish what is in flight, fail what is still queued, join
  * the threads and free everything (results included). */
 GSMAT_API void gsmat_server_destroy(gsmat_server *srv);
+
+/* ------------------------------------------------------------------------ */
+/* String dictionary and SPARQL text (host code, no GPU needed)              */
+
+/* Dictionary of the bijections h_p and h_so (Sec. 5.2): predicates are
+ * numbered 1, 2, ... and subjects and objects share a second numbering
+ * 1, 2, ..., each term by its first occurrence as triples are added, the
+ * subject of a triple before its object.  Code 0 is never given out.
+ *
+ * Data text: statements "subject predicate object ." in the N-Triples /
+ * Turtle subset: <iri>, "literal" (backslash escapes, optional @lang or
+ * ^^datatype), _:blank, or a bare word (a run of bytes other than
+ * whitespace and < > " { } ; , .); "@prefix p: <iri> ." declarations, after
+ * which a word p:local stands for <iri local>; ';' and ',' lists; the
+ * predicate word 'a' for rdf:type; '#' comments.  A term is identified by
+ * its text after that prefix expansion.  A literal cannot be a subject or a
+ * predicate.
+ *
+ * Threading: lookups, decoding and parsing may run concurrently; an add
+ * may not run concurrently with anything on the same dictionary. */
+typedef struct gsmat_dict gsmat_dict;
+
+#define GSMAT_DICT_SO 0 /* subjects and objects (h_so) */
+#define GSMAT_DICT_P 1  /* predicates (h_p) */
+
+GSMAT_API int gsmat_dict_create(gsmat_dict **out);
+GSMAT_API void gsmat_dict_free(gsmat_dict *dict);
+
+/* Read the statements of text[0..len) and append their encoded triples.
+ * The whole text is checked first: on INVALID_ARG nothing changes.
+ * *n_added (may be NULL) receives the number of triples read (repeated
+ * triples included: gsmat_load removes them).  CAPACITY: more than
+ * 2^31 - 1 terms of one kind (the triples of this text are not appended). */
+GSMAT_API int gsmat_dict_add_text(gsmat_dict *dict, const char *text, int64_t len, int64_t *n_added);
+
+/* All triples added so far as host int32[n][3] (s, p, o) codes, ready for
+ * gsmat_load; owned by the dictionary, valid until the next add or free. */
+GSMAT_API int gsmat_dict_triples(const gsmat_dict *dict, const int32_t **triples, int64_t *n);
+
+GSMAT_API int gsmat_dict_size(const gsmat_dict *dict, int32_t *n_predicates, int32_t *n_terms);
+
+/* Code of a term given by its identity text (prefixes expanded); 0 if the
+ * dictionary does not hold it. */
+GSMAT_API int gsmat_dict_lookup(const gsmat_dict *dict, int kind, const char *term, int64_t len, int32_t *code);
+
+/* Decode n codes of one kind (ID decode): terms[i] receives a
+ * NUL-terminated text owned by the dictionary (valid until it is freed),
+ * lens[i] (may be NULL) its length.  INVALID_ARG for a code the dictionary
+ * did not give out. */
+GSMAT_API int gsmat_dict_decode(const gsmat_dict *dict, int kind, const int32_t *codes, int64_t n,
+                                const char **terms, int32_t *lens);
+
+/* A parsed SPARQL query. */
+typedef struct gsmat_sparql gsmat_sparql;
+
+/* Parse SPARQL text: PREFIX declarations, SELECT [DISTINCT] followed by
+ * variables (?name or $name) or '*', an optional WHERE and a brace-enclosed
+ * basic graph pattern of triple patterns separated by '.', with ';' and ','
+ * lists and the terms of the data text.  Variables are numbered 0, 1, ...
+ * in order of first occurrence in the pattern block; '*' projects all of
+ * them in that order.  Constants are coded by `dict` (a term it does not
+ * hold gets code 0, which no triple has); with dict = NULL constants must
+ * be decimal codes.
+ * Errors: INVALID_ARG (syntax, a projected variable that no pattern uses
+ * or that is repeated, more than 64 patterns or 32 variables, a literal
+ * predicate); UNSUPPORTED (a variable predicate (Sec. 6.3), FILTER,
+ * OPTIONAL, UNION, GRAPH, MINUS, BIND, VALUES, SERVICE, nested groups,
+ * ORDER/LIMIT/OFFSET/GROUP/HAVING after the block, ASK, CONSTRUCT,
+ * DESCRIBE, BASE). */
+GSMAT_API int gsmat_sparql_parse(const gsmat_dict *dict, const char *text, int64_t len, gsmat_sparql **out);
+
+/* The parsed query: its BGP (for gsmat_query), the projected variables and
+ * the DISTINCT flag (for gsmat_table_project).  Pointers are owned by q. */
+GSMAT_API int gsmat_sparql_info(const gsmat_sparql *q, const gsmat_pattern **pats, int32_t *n_pats, int32_t *n_vars,
+                                const int32_t **proj, int32_t *n_proj, int32_t *distinct);
+
+/* Name of variable v (without its sigil), owned by q; NULL if out of range. */
+GSMAT_API const char *gsmat_sparql_var_name(const gsmat_sparql *q, int32_t v);
+
+GSMAT_API void gsmat_sparql_free(gsmat_sparql *q);
 
 /* ------------------------------------------------------------------------ */
 /* Host planner (Alg. 1; Sec. 6.2), callable without a GPU                   */

@@ -1,6 +1,7 @@
 // The C ABI of libgsmat (include/gsmat.h): argument checks and dispatch.
 #include <string.h>
 
+#include "dict.h"
 #include "join.cuh"
 #include "plan.h"
 #include "query.cuh"
@@ -259,6 +260,60 @@ GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, cons
     if (!keys || !stats || !order_out) return set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
     return gs::plan_bgp(pats, n_pats, keys, stats, order_out, kinds_out, est_out);
 }
+
+GSMAT_API int gsmat_table_project(const gsmat_table *table, const int32_t *vars, int32_t n, int distinct,
+                                  gsmat_stream_t stream, gsmat_table **out) {
+    gs::clear_error();
+    return gs::table_project(table, vars, n, distinct, (cudaStream_t)stream, out);
+}
+
+GSMAT_API int gsmat_dict_create(gsmat_dict **out) {
+    gs::clear_error();
+    return gs::dict_create(out);
+}
+
+GSMAT_API void gsmat_dict_free(gsmat_dict *dict) { gs::dict_free(dict); }
+
+GSMAT_API int gsmat_dict_add_text(gsmat_dict *dict, const char *text, int64_t len, int64_t *n_added) {
+    gs::clear_error();
+    return gs::dict_add_text(dict, text, len, n_added);
+}
+
+GSMAT_API int gsmat_dict_triples(const gsmat_dict *dict, const int32_t **triples, int64_t *n) {
+    gs::clear_error();
+    return gs::dict_triples(dict, triples, n);
+}
+
+GSMAT_API int gsmat_dict_size(const gsmat_dict *dict, int32_t *n_predicates, int32_t *n_terms) {
+    gs::clear_error();
+    return gs::dict_size(dict, n_predicates, n_terms);
+}
+
+GSMAT_API int gsmat_dict_lookup(const gsmat_dict *dict, int kind, const char *term, int64_t len, int32_t *code) {
+    gs::clear_error();
+    return gs::dict_lookup(dict, kind, term, len, code);
+}
+
+GSMAT_API int gsmat_dict_decode(const gsmat_dict *dict, int kind, const int32_t *codes, int64_t n,
+                                const char **terms, int32_t *lens) {
+    gs::clear_error();
+    return gs::dict_decode(dict, kind, codes, n, terms, lens);
+}
+
+GSMAT_API int gsmat_sparql_parse(const gsmat_dict *dict, const char *text, int64_t len, gsmat_sparql **out) {
+    gs::clear_error();
+    return gs::sparql_parse(dict, text, len, out);
+}
+
+GSMAT_API int gsmat_sparql_info(const gsmat_sparql *q, const gsmat_pattern **pats, int32_t *n_pats,
+                                int32_t *n_vars, const int32_t **proj, int32_t *n_proj, int32_t *distinct) {
+    gs::clear_error();
+    return gs::sparql_info(q, pats, n_pats, n_vars, proj, n_proj, distinct);
+}
+
+GSMAT_API const char *gsmat_sparql_var_name(const gsmat_sparql *q, int32_t v) { return gs::sparql_var_name(q, v); }
+
+GSMAT_API void gsmat_sparql_free(gsmat_sparql *q) { gs::sparql_free(q); }
 
 GSMAT_API int gsmat_plan_cost(const gsmat_pattern *pats, int n_pats, int n_vars, const int64_t *keys,
                               const gsmat_pred_stats *stats, int32_t *order_out, int32_t *kinds_out,

@@ -21,6 +21,7 @@
 #include "join.cuh"
 #include "plan.h"
 #include "query.cuh"
+#include "select.cuh"
 #include "store.cuh"
 
 namespace gs {
@@ -127,6 +128,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
     if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY | GSMAT_NO_INTERSECT | GSMAT_PLAN_COST)) {
         return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
     }
+    T->id_bits = std::max(1, bits_for((uint64_t)std::max(S->max_entity, 0)));
     Ctx cx;
     cx.S = S;
     cx.st = st;
@@ -527,6 +529,7 @@ int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const in
     }
     T->storage = std::move(fin.buf);
     T->stats.result_rows = fin.rows;
+    T->id_bits = std::max(1, bits_for((uint64_t)std::max(S->max_entity, 0)));
     int64_t unused = 0;
     const int rc = cx.read_count(&unused);  // waits for the reorder, checks its bounded waits
     if (rc != GSMAT_OK) {
@@ -536,6 +539,105 @@ int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const in
     }
     T->storage.st = nullptr;
     *out = T;
+    return GSMAT_OK;
+}
+
+namespace {
+
+// Row i is the first of its run of equal rows (rows sorted, k columns).
+struct FirstOfRunOp {
+    Cols in;
+    OutCols out;
+    int k;
+    __device__ bool flag(int64_t i) const {
+        if (i == 0) return true;
+        for (int c = 0; c < k; ++c) {
+            if (in.c[c][i] != in.c[c][i - 1]) return true;
+        }
+        return false;
+    }
+    __device__ void emit(int64_t i, int64_t j) const {
+        for (int c = 0; c < k; ++c) out.c[c][j] = in.c[c][i];
+    }
+};
+
+}  // namespace
+
+int table_project(const gsmat_table *T, const int32_t *vars, int32_t n, int distinct, cudaStream_t st,
+                  gsmat_table **out) {
+    if (!T || !vars || !out) return set_error(GSMAT_ERR_INVALID_ARG, "table, vars or out is NULL");
+    *out = nullptr;
+    if (T->ncols == 0) return set_error(GSMAT_ERR_INVALID_ARG, "a count-only table has no columns");
+    if (n < 1 || n > T->ncols) return set_error(GSMAT_ERR_INVALID_ARG, "%d projected variables (1..%d)", n, T->ncols);
+    if (distinct != 0 && distinct != 1) return set_error(GSMAT_ERR_INVALID_ARG, "distinct must be 0 or 1");
+    int idx[kMaxCols];
+    bool leading = true;  // the new columns are the table's first n, in order
+    for (int c = 0; c < n; ++c) {
+        idx[c] = -1;
+        for (int j = 0; j < T->ncols; ++j) {
+            if (T->vars[j] == vars[c]) idx[c] = j;
+        }
+        if (idx[c] < 0) return set_error(GSMAT_ERR_INVALID_ARG, "variable %d is not a column of the table", vars[c]);
+        for (int b = 0; b < c; ++b) {
+            if (idx[b] == idx[c]) return set_error(GSMAT_ERR_INVALID_ARG, "variable %d projected twice", vars[c]);
+        }
+        leading = leading && idx[c] == c;
+    }
+    const int64_t rows = T->rows;
+    auto fill = [&](gsmat_table *R, int64_t r) {
+        R->rows = r;
+        R->ncols = n;
+        R->id_bits = T->id_bits;
+        R->stats.result_rows = r;
+        for (int c = 0; c < n; ++c) R->vars[c] = vars[c];
+    };
+    if (rows == 0) {
+        gsmat_table *R = new gsmat_table();
+        fill(R, 0);
+        *out = R;
+        return GSMAT_OK;
+    }
+    Ctx cx;
+    cx.S = nullptr;
+    cx.st = st;
+    cx.h = pinned_scratch(4 + 8 * GSMAT_MAX_PATTERNS);
+    if (!cx.h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    GS_TRY(cx.qstat.alloc(4 * sizeof(int64_t), st));
+    GS_CUDA(cudaMemsetAsync(cx.qstat.p, 0, 4 * sizeof(int64_t), st));
+    Cols in;
+    for (int c = 0; c < kMaxCols; ++c) in.c[c] = c < n ? T->col[idx[c]] : nullptr;
+    // rows of the table ascend in its column order, so its leading columns
+    // are already sorted; other selections are reordered (stable LSD)
+    Tbl srt;
+    if (!leading || !distinct) {
+        OutCols oc;
+        GS_TRY(alloc_cols(srt, n, rows, st, &oc));
+        if (leading) {
+            GS_TRY(launch_copy_cols(in, n, rows, oc, st));
+        } else {
+            GS_TRY(reorder_rows(in, n, n, std::max(1, T->id_bits), rows, oc, st, cx.d_err()));
+        }
+        in = srt.cols();
+    }
+    int64_t kept = rows;
+    Tbl res;
+    if (distinct) {
+        OutCols oc;
+        GS_TRY(alloc_cols(res, n, rows, st, &oc));
+        FirstOfRunOp op{in, oc, n};
+        GS_TRY(run_select(op, rows, cx.d_count(), st, cx.d_err()));
+        GS_TRY(cx.read_count(&kept));  // waits for the device, checks its bounded waits
+    } else {
+        res = std::move(srt);
+        int64_t unused = 0;
+        GS_TRY(cx.read_count(&unused));
+    }
+    gsmat_table *R = new gsmat_table();
+    fill(R, kept);
+    for (int c = 0; c < n; ++c) R->col[c] = res.col[c];
+    R->storage = std::move(res.buf);
+    R->storage.st = nullptr;  // freed on the legacy stream later
+    *out = R;
     return GSMAT_OK;
 }
 

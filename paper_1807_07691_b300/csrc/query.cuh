@@ -10,6 +10,7 @@ struct gsmat_table {
     const int32_t *col[32] = {nullptr};
     gs::DevBuf storage;  // owns the columns
     gsmat_query_stats stats{};
+    int32_t id_bits = 31;  // every value is below 2^id_bits
 };
 
 namespace gs {
@@ -22,6 +23,9 @@ int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream
 // to variable order, rows ascending; the result owns its columns.
 int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const int32_t *plan_vars, int V, int64_t rows,
                  cudaStream_t st, gsmat_table **out);
+// Projection / DISTINCT of a table (gsmat_table_project).
+int table_project(const gsmat_table *T, const int32_t *vars, int32_t n, int distinct, cudaStream_t st,
+                  gsmat_table **out);
 // Columns of a table in the order the plan binds variables, and the number
 // of leading variables a stable reorder must sort (see canonical_order).
 int leading_sort_vars(const int32_t *plan_vars, int V);

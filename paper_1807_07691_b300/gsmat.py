@@ -127,6 +127,18 @@ def _load():
         "gsmat_table_free": ([vp], None),
         "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
         "gsmat_plan_cost": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
+        "gsmat_table_project": ([vp, vp, i32, c_int, vp, P(vp)], c_int),
+        "gsmat_dict_create": ([P(vp)], c_int),
+        "gsmat_dict_free": ([vp], None),
+        "gsmat_dict_add_text": ([vp, ctypes.c_char_p, i64, P(i64)], c_int),
+        "gsmat_dict_triples": ([vp, P(vp), P(i64)], c_int),
+        "gsmat_dict_size": ([vp, P(i32), P(i32)], c_int),
+        "gsmat_dict_lookup": ([vp, c_int, ctypes.c_char_p, i64, P(i32)], c_int),
+        "gsmat_dict_decode": ([vp, c_int, vp, i64, vp, vp], c_int),
+        "gsmat_sparql_parse": ([vp, ctypes.c_char_p, i64, P(vp)], c_int),
+        "gsmat_sparql_info": ([vp, P(vp), P(i32), P(i32), P(vp), P(i32), P(i32)], c_int),
+        "gsmat_sparql_var_name": ([vp, i32], ctypes.c_char_p),
+        "gsmat_sparql_free": ([vp], None),
         "gsmat_batch_prepare": ([vp, vp, i32, vp, vp, P(vp)], c_int),
         "gsmat_batch_execute": ([vp, vp], c_int),
         "gsmat_batch_result": ([vp, i32, P(i64), P(i32), P(i32)], c_int),
@@ -294,6 +306,15 @@ class Table:
             _check(_lib.gsmat_table_copy(self._h, ctypes.c_void_p(out.data_ptr()), 1, _stream_ptr(stream)))
         return out
 
+    def project(self, variables, distinct: bool = False, stream=None) -> "Table":
+        """gsmat_table_project: the given variables' columns, rows ascending
+        (each once with ``distinct``), as a new device table."""
+        v = np.ascontiguousarray(np.asarray(list(variables), dtype=np.int32))
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_table_project(self._h, v.ctypes.data, int(v.size), 1 if distinct else 0,
+                                        _stream_ptr(stream), ctypes.byref(h)))
+        return Table(h)
+
     def stats(self) -> dict:
         s = QueryStats()
         _check(_lib.gsmat_table_stats(self._h, ctypes.byref(s)))
@@ -389,6 +410,126 @@ class Store:
 
     def query(self, bgp, n_vars=None, flags: int = SORTED, stream=None) -> Table:
         return self.query_raw(self.marshal(bgp, n_vars), flags, stream)
+
+    def sparql(self, query, dictionary: "Dictionary | None" = None, flags: int = SORTED, stream=None) -> Table:
+        """Evaluate SPARQL text (or a parsed Sparql): the BGP by gsmat_query,
+        then the projection / DISTINCT by gsmat_table_project when the
+        query asks for anything but all variables in order."""
+        q = query if isinstance(query, Sparql) else Sparql(query, dictionary)
+        T = self.query(q, flags=flags & ~PLAN_ORDER, stream=stream)
+        if q.projection == list(range(q.n_vars)) and not q.distinct:
+            return T
+        P = T.project(q.projection, q.distinct, stream=stream)
+        T.free()
+        return P
+
+
+# ----------------------------------------------------------------------------
+
+
+def _text_bytes(text) -> bytes:
+    return text.encode("utf-8") if isinstance(text, str) else bytes(text)
+
+
+class Dictionary:
+    """h_p and h_so by first occurrence (gsmat_dict_*; Sec. 5.2)."""
+
+    SO = 0
+    P = 1
+
+    def __init__(self, text=None):
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_dict_create(ctypes.byref(h)))
+        self._h = h
+        if text is not None:
+            self.add_text(text)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.gsmat_dict_free(h)
+        self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def add_text(self, text) -> int:
+        b = _text_bytes(text)
+        n = ctypes.c_int64()
+        _check(_lib.gsmat_dict_add_text(self._h, b, len(b), ctypes.byref(n)))
+        return int(n.value)
+
+    def triples(self) -> np.ndarray:
+        """(n, 3) int32 (s, p, o) codes of everything added (a copy)."""
+        p, n = ctypes.c_void_p(), ctypes.c_int64()
+        _check(_lib.gsmat_dict_triples(self._h, ctypes.byref(p), ctypes.byref(n)))
+        if n.value == 0:
+            return np.zeros((0, 3), np.int32)
+        arr = (ctypes.c_int32 * (3 * n.value)).from_address(p.value)
+        return np.frombuffer(arr, dtype=np.int32).reshape(-1, 3).copy()
+
+    def size(self) -> tuple:
+        np_, nt = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.gsmat_dict_size(self._h, ctypes.byref(np_), ctypes.byref(nt)))
+        return int(np_.value), int(nt.value)
+
+    def lookup(self, term: str, kind: int = 0) -> int:
+        b = _text_bytes(term)
+        c = ctypes.c_int32()
+        _check(_lib.gsmat_dict_lookup(self._h, kind, b, len(b), ctypes.byref(c)))
+        return int(c.value)
+
+    def decode(self, codes, kind: int = 0) -> list:
+        c = np.ascontiguousarray(np.asarray(codes, dtype=np.int32).ravel())
+        n = int(c.size)
+        terms = (ctypes.c_char_p * max(1, n))()
+        lens = np.zeros(max(1, n), np.int32)
+        _check(_lib.gsmat_dict_decode(self._h, kind, c.ctypes.data, n, ctypes.cast(terms, ctypes.c_void_p),
+                                      lens.ctypes.data))
+        return [ctypes.string_at(terms[i], int(lens[i])).decode("utf-8") for i in range(n)]
+
+    def decode_rows(self, rows) -> list:
+        """Rows of a result (subject/object codes) as tuples of terms."""
+        rows = np.asarray(rows, dtype=np.int32)
+        if rows.size == 0:
+            return [tuple() for _ in range(rows.shape[0])]
+        flat = self.decode(rows.ravel(), self.SO)
+        k = rows.shape[1]
+        return [tuple(flat[i * k:(i + 1) * k]) for i in range(rows.shape[0])]
+
+
+class Sparql:
+    """A parsed SPARQL query (gsmat_sparql_*): usable wherever a BGP is."""
+
+    def __init__(self, text, dictionary: Dictionary | None = None):
+        b = _text_bytes(text)
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_sparql_parse(dictionary.handle if dictionary is not None else None, b, len(b),
+                                       ctypes.byref(h)))
+        self._h = h
+        pats, n, nv, proj, nproj, dist = (ctypes.c_void_p(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_void_p(),
+                                          ctypes.c_int32(), ctypes.c_int32())
+        _check(_lib.gsmat_sparql_info(h, ctypes.byref(pats), ctypes.byref(n), ctypes.byref(nv), ctypes.byref(proj),
+                                      ctypes.byref(nproj), ctypes.byref(dist)))
+        arr = (Pattern * n.value).from_address(pats.value)
+        self.patterns = [(p.s, p.p, p.o, p.s_var, p.o_var) for p in arr]
+        self.n_vars = int(nv.value)
+        pr = (ctypes.c_int32 * max(1, nproj.value)).from_address(proj.value) if nproj.value else []
+        self.projection = [int(pr[i]) for i in range(nproj.value)]
+        self.distinct = bool(dist.value)
+        self.var_names = [_lib.gsmat_sparql_var_name(h, v).decode("utf-8") for v in range(self.n_vars)]
+        _lib.gsmat_sparql_free(h)
+        self._h = None
+
+    def as_array(self) -> np.ndarray:
+        a = np.zeros((len(self.patterns), 6), np.int64)
+        for i, (s, p, o, sv, ov) in enumerate(self.patterns):
+            a[i] = (s, p, o, sv, 0, ov)
+        return a
 
 
 # ----------------------------------------------------------------------------
