@@ -265,6 +265,9 @@ def run_gsmat(args):
         batched, bq, tuned = run_batched(args, gs, torch, d_tri, stream)
         if not args.no_planner:
             planner = run_planner(args, gs, torch, d_tri, stream, queries, bq, tuned)
+    frontend = None
+    if not args.no_frontend:
+        frontend = run_frontend(args, gs, torch, d_tri, stream, triples, queries)
         if not args.no_served:
             served = run_served(args, gs, torch, d_tri, stream, bq)
     served_large = None
@@ -333,6 +336,8 @@ def run_gsmat(args):
         out["batched"] = batched
     if planner is not None:
         out["planner"] = planner
+    if frontend is not None:
+        out["frontend"] = frontend
     if served is not None:
         out["served"] = served
     if served_large is not None:
@@ -485,6 +490,70 @@ def run_planner(args, gs, torch, d_tri, stream, queries, bq, tuned):
         "batched": {"alg1_queries_per_s": round(len(bq) / (bg_ms / 1e3), 1),
                     "cost_queries_per_s": round(len(bq) / (bc_ms / 1e3), 1),
                     "alg1_prepare_ms": round(bg_prep, 2), "cost_prepare_ms": round(bc_prep, 2)},
+    }
+
+
+def run_frontend(args, gs, torch, d_tri, stream, triples, queries):
+    """The user-facing path on the medium workload: dictionary encoding of
+    10^6 of its triples written as IRI text (host), reading the 40 BGPs
+    written as SPARQL text (host, through the Python binding), and device
+    projection with DISTINCT of their results onto one variable -- the
+    leading one (rows already sorted: one compaction) and the last one
+    (stable radix reorder, then the compaction)."""
+    sample = np.asarray(triples[:1_000_000])
+    text = "\n".join(f"<http://x.org/e{s}> <http://x.org/p{p}> <http://x.org/e{o}> ." for s, p, o in sample.tolist())
+    t0 = time.perf_counter()
+    d = gs.Dictionary()
+    d.add_text(text)
+    enc_s = time.perf_counter() - t0
+    n_pred, n_terms = d.size()
+    d.free()
+
+    def as_text(q):
+        def term(x, isv):
+            return f"?v{x}" if isv else str(x)
+        body = " . ".join(f"{term(s, sv)} {p} {term(o, ov)}" for (s, p, o, sv, ov) in q.patterns)
+        return f"SELECT * WHERE {{ {body} }}"
+
+    texts = [as_text(q) for q in queries]
+    t0 = time.perf_counter()
+    for _ in range(10):
+        for t in texts:
+            gs.Sparql(t)
+    parse_us = 1e6 * (time.perf_counter() - t0) / (10 * len(texts))
+
+    S = gs.Store(d_tri, stream=stream)
+    marsh = [gs.Store.marshal(q) for q in queries]
+    res = {}
+    for which in ("leading", "last"):
+        ms, rows_in, rows_out, algo = 0.0, 0, 0, 0.0
+        for rep in range(2):
+            for q, m in zip(queries, marsh):
+                T = S.query_raw(m, stream=stream)
+                v = 0 if which == "leading" else q.n_vars - 1
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                P = T.project([v], True, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                if rep:
+                    ms += a.elapsed_time(b)
+                    rows_in += T.rows
+                    rows_out += P.rows
+                    algo += 4.0 * T.rows + 4.0 * P.rows
+                P.free()
+                T.free()
+        res[which] = {"ms": round(ms, 3), "rows_in": int(rows_in), "rows_out": int(rows_out),
+                      "GBps": round(algo / 1e9 / (ms / 1e3), 1) if ms > 0 else None}
+    S.free()
+    return {
+        "workload": "medium: 10^6 triples as IRI text; its 40 BGPs as SPARQL text; DISTINCT of one variable of each result",
+        "encode_triples_per_s": round(len(sample) / enc_s, 1),
+        "encode_terms": {"predicates": n_pred, "subjects_objects": n_terms},
+        "sparql_parse_us": round(parse_us, 2),
+        "distinct_leading": res["leading"],
+        "distinct_last": res["last"],
     }
 
 
@@ -745,6 +814,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-n", type=int, default=4096)
     ap.add_argument("--no-planner", action="store_true", help="skip Alg. 1 vs the cost-based planner")
+    ap.add_argument("--no-frontend", action="store_true", help="skip the dictionary / SPARQL / DISTINCT leg")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--served-rates", type=float, nargs="+", default=[1000, 5000, 20000])

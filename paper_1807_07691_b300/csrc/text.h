@@ -188,6 +188,10 @@ inline void expand_word(std::string_view w, const Prefixes &pf, std::string &out
     out.append(w);
 }
 
+// The identity text of t: a view of the token itself when nothing expands
+// (no declared prefix involved), else of `scratch` holding the expansion.
+inline std::string_view identity(const Tok &t, const Prefixes &pf, std::string &scratch);
+
 inline void expand(const Tok &t, const Prefixes &pf, std::string &out) {
     out.clear();
     if (t.kind == kWord) {
@@ -200,6 +204,28 @@ inline void expand(const Tok &t, const Prefixes &pf, std::string &out) {
         if (t.dtype_kind == kIri) out.append(t.dtype);
         else expand_word(t.dtype, pf, out);
     }
+}
+
+inline bool declared_prefix(std::string_view w, const Prefixes &pf) {
+    if (pf.empty()) return false;
+    const size_t colon = w.find(':');
+    return colon != std::string_view::npos && pf.count(std::string(w.substr(0, colon))) != 0;
+}
+
+inline std::string_view identity(const Tok &t, const Prefixes &pf, std::string &scratch) {
+    if (t.kind == kWord && declared_prefix(t.text, pf)) {
+        expand(t, pf, scratch);
+        return scratch;
+    }
+    if (t.kind == kLit && t.dtype_kind != kEnd) {
+        if (t.dtype_kind == kWord && declared_prefix(t.dtype, pf)) {
+            expand(t, pf, scratch);
+            return scratch;
+        }
+        // body, "^^" and datatype lie back to back in the text
+        return std::string_view(t.text.data(), (size_t)(t.dtype.data() + t.dtype.size() - t.text.data()));
+    }
+    return t.text;
 }
 
 constexpr const char *kRdfType = "<http://www.w3.org/1999/02/22-rdf-syntax-ns#type>";
