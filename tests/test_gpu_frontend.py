@@ -81,6 +81,8 @@ def test_project_random_bgps(gs, tiny, seed):
     rng = np.random.default_rng(900 + seed)
     for _ in range(10):
         pats, V = random_bgp(rng, t, n_vars_max=5, n_pats_max=4, p_const=0.3)
+        if V == 0:
+            continue  # nothing to project
         try:
             want_rows = ix.query(pats, V, row_limit=3_000_000)
         except oracle.OracleError:
@@ -118,6 +120,8 @@ def test_sparql_text_random_queries(gs, tiny):
     n = 0
     while n < 30:
         pats, V = random_bgp(rng, t, n_vars_max=4, n_pats_max=4, p_const=0.3)
+        if V == 0:
+            continue  # SELECT needs a variable
         try:
             want_rows = ix.query(pats, V, row_limit=3_000_000)
         except oracle.OracleError:
