@@ -144,7 +144,7 @@ def _mutate(rng, text):
 
 
 @pytest.mark.parametrize("seed", range(20))
-def test_mutated_data_same_verdict(gs, seed):
+def test_mutated_data_same_outcome(gs, seed):
     """Damaged texts: the library and the oracle accept the same ones (with
     the same codes) and reject the others; a rejected text adds nothing."""
     rng = np.random.default_rng(100 + seed)
