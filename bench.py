@@ -268,6 +268,9 @@ def run_gsmat(args):
     frontend = None
     if not args.no_frontend:
         frontend = run_frontend(args, gs, torch, d_tri, stream, triples, queries)
+    shards = None
+    if not args.no_shards:
+        shards = run_shards(args, gs, torch, d_tri, stream, queries)
         if not args.no_served:
             served = run_served(args, gs, torch, d_tri, stream, bq)
     served_large = None
@@ -338,6 +341,8 @@ def run_gsmat(args):
         out["planner"] = planner
     if frontend is not None:
         out["frontend"] = frontend
+    if shards is not None:
+        out["row_shards"] = shards
     if served is not None:
         out["served"] = served
     if served_large is not None:
@@ -557,6 +562,48 @@ def run_frontend(args, gs, torch, d_tri, stream, triples, queries):
         "distinct_leading": res["leading"],
         "distinct_last": res["last"],
     }
+
+
+def run_shards(args, gs, torch, d_tri, stream, queries, n_shards=2):
+    """Row sharding of the medium queries, shards one after another on this
+    GPU (as each of n_shards GPUs would run one), then the device merge of
+    the sorted shards; against the unsharded query.  Rows are checked equal."""
+    S = gs.Store(d_tri, stream=stream)
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        b.synchronize()
+        return r, a.elapsed_time(b)
+
+    whole_ms = shard_ms = merge_ms = 0.0
+    max_shard_ms = 0.0
+    rows = 0
+    for rep in range(2):
+        for q in queries:
+            T, t_whole = timed(lambda: S.query(q, stream=stream))
+            parts, t_parts = [], []
+            for k in range(n_shards):
+                P, t = timed(lambda: S.query_shard(q, k, n_shards, stream=stream))
+                parts.append(P)
+                t_parts.append(t)
+            M, t_merge = timed(lambda: gs.merge_tables(parts, stream=stream))
+            assert M.rows == T.rows
+            if rep:
+                whole_ms += t_whole
+                shard_ms += sum(t_parts)
+                max_shard_ms += max(t_parts)
+                merge_ms += t_merge
+                rows += T.rows
+            for x in parts + [M, T]:
+                x.free()
+    S.free()
+    return {"workload": f"medium, 40 BGPs, {n_shards} row shards run one after another on one GPU",
+            "whole_ms": round(whole_ms, 3), "shards_ms": round(shard_ms, 3),
+            "slowest_shard_ms": round(max_shard_ms, 3), "merge_ms": round(merge_ms, 3), "result_rows": int(rows)}
 
 
 def _spin_until(t):
@@ -895,6 +942,7 @@ def main():
     ap.add_argument("--batched-n", type=int, default=4096)
     ap.add_argument("--no-planner", action="store_true", help="skip Alg. 1 vs the cost-based planner")
     ap.add_argument("--no-frontend", action="store_true", help="skip the dictionary / SPARQL / DISTINCT leg")
+    ap.add_argument("--no-shards", action="store_true", help="skip the row-sharding leg")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-seconds", type=float, default=2.0)
     ap.add_argument("--served-rates", type=float, nargs="+", default=[1000, 5000, 20000])

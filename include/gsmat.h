@@ -186,6 +186,30 @@ typedef struct {
 GSMAT_API int gsmat_query(const gsmat_store *store, const gsmat_pattern *pats, int n_pats, int n_vars,
                           uint32_t flags, gsmat_stream_t stream, gsmat_table **out);
 
+/* Row sharding of one query (the rows of every step after the first are
+ * independent of each other, Alg. 3): evaluate only what derives from the
+ * shard-th of n_shards contiguous, near-equal parts of the first plan
+ * step's relation, as gsmat_query does otherwise (same plan, flags and
+ * errors; INVALID_ARG unless 0 <= shard < n_shards <= 2^20).  The shards'
+ * results partition the full result: with GSMAT_PLAN_ORDER their tables
+ * follow each other in shard order (concatenated, they are the full
+ * table); sorted shards give the full sorted result through
+ * gsmat_table_merge; COUNT_ONLY counts add up.  Shards can run on
+ * different GPUs, each with a replica of the store, or one after another
+ * on one GPU. */
+GSMAT_API int gsmat_query_shard(const gsmat_store *store, const gsmat_pattern *pats, int n_pats, int n_vars,
+                                uint32_t flags, int32_t shard, int32_t n_shards, gsmat_stream_t stream,
+                                gsmat_table **out);
+
+/* The rows of k >= 1 tables that hold the same variables in the same column
+ * order (e.g. the shards of one query), together in one new table, rows
+ * ascending lexicographically in that column order: the tables are copied
+ * back to back and reordered by all columns on the device.  INVALID_ARG
+ * for other columns or a count-only table; CAPACITY above 2^32 - 1 rows.
+ * Synchronises `stream`. */
+GSMAT_API int gsmat_table_merge(const gsmat_table *const *tables, int32_t k, gsmat_stream_t stream,
+                                gsmat_table **out);
+
 /* Shape of a result.  col_vars (host int32[cols], may be NULL) receives the
  * variable number held by each column. */
 GSMAT_API int gsmat_table_info(const gsmat_table *table, int64_t *rows, int32_t *cols, int32_t *col_vars);

@@ -261,6 +261,19 @@ GSMAT_API int gsmat_plan(const gsmat_pattern *pats, int n_pats, int n_vars, cons
     return gs::plan_bgp(pats, n_pats, keys, stats, order_out, kinds_out, est_out);
 }
 
+GSMAT_API int gsmat_query_shard(const gsmat_store *store, const gsmat_pattern *pats, int n_pats, int n_vars,
+                                uint32_t flags, int32_t shard, int32_t n_shards, gsmat_stream_t stream,
+                                gsmat_table **out) {
+    gs::clear_error();
+    return gs::query_run(store, pats, n_pats, n_vars, flags, (cudaStream_t)stream, out, shard, n_shards);
+}
+
+GSMAT_API int gsmat_table_merge(const gsmat_table *const *tables, int32_t k, gsmat_stream_t stream,
+                                gsmat_table **out) {
+    gs::clear_error();
+    return gs::table_merge(tables, k, (cudaStream_t)stream, out);
+}
+
 GSMAT_API int gsmat_table_project(const gsmat_table *table, const int32_t *vars, int32_t n, int distinct,
                                   gsmat_stream_t stream, gsmat_table **out) {
     gs::clear_error();

@@ -123,7 +123,7 @@ int canonical_order(Ctx &cx, Tbl &t, Tbl &out) {
 }
 
 int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
-        gsmat_table *T) {
+        gsmat_table *T, int shard, int n_shards) {
     GS_TRY(validate_bgp(pats, n_pats, n_vars));
     if (flags & ~(GSMAT_PLAN_ORDER | GSMAT_COUNT_ONLY | GSMAT_NO_INTERSECT | GSMAT_PLAN_COST)) {
         return set_error(GSMAT_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
@@ -424,6 +424,14 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
             for (int c = 0; c < rc; ++c) nxt.vars[cur.ncols + c] = rv[c];
         }
         cur = std::move(nxt);
+        if (step == 0 && n_shards > 1) {
+            // row sharding: keep this shard's contiguous part of the first
+            // relation; every later step maps each row to rows of its own, in
+            // order, so the shards partition the result
+            const int64_t lo = cur.rows * shard / n_shards, hi = cur.rows * (shard + 1) / n_shards;
+            for (int c = 0; c < cur.ncols; ++c) cur.col[c] += lo;
+            cur.rows = hi - lo;
+        }
         qs.rows[step] = cur.rows;
     }
 
@@ -483,13 +491,16 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
 }  // namespace
 
 int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
-              gsmat_table **out) {
+              gsmat_table **out, int shard, int n_shards) {
     if (!S || !out) return set_error(GSMAT_ERR_INVALID_ARG, "store or out is NULL");
     *out = nullptr;
+    if (n_shards < 1 || n_shards > (1 << 20) || shard < 0 || shard >= n_shards) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "shard %d of %d", shard, n_shards);
+    }
     gsmat_table *T = new gsmat_table();
     // on success run() has waited for its last device work (its final read
     // of the error word); a failed call drains what it enqueued
-    const int rc = run(S, pats, n_pats, n_vars, flags, st, T);
+    const int rc = run(S, pats, n_pats, n_vars, flags, st, T, shard, n_shards);
     if (rc != GSMAT_OK) cudaStreamSynchronize(st);
     profile_flush();
     if (rc != GSMAT_OK) {
@@ -635,6 +646,78 @@ int table_project(const gsmat_table *T, const int32_t *vars, int32_t n, int dist
     gsmat_table *R = new gsmat_table();
     fill(R, kept);
     for (int c = 0; c < n; ++c) R->col[c] = res.col[c];
+    R->storage = std::move(res.buf);
+    R->storage.st = nullptr;  // freed on the legacy stream later
+    *out = R;
+    return GSMAT_OK;
+}
+
+int table_merge(const gsmat_table *const *tables, int k, cudaStream_t st, gsmat_table **out) {
+    if (!tables || !out || k < 1) return set_error(GSMAT_ERR_INVALID_ARG, "tables, k or out");
+    *out = nullptr;
+    const gsmat_table *t0 = tables[0];
+    if (!t0 || t0->ncols == 0) return set_error(GSMAT_ERR_INVALID_ARG, "table 0 is NULL or has no columns");
+    const int V = t0->ncols;
+    int64_t total = 0;
+    int bits = 1;
+    for (int i = 0; i < k; ++i) {
+        const gsmat_table *t = tables[i];
+        if (!t || t->ncols != V) return set_error(GSMAT_ERR_INVALID_ARG, "table %d: other columns", i);
+        for (int c = 0; c < V; ++c) {
+            if (t->vars[c] != t0->vars[c]) return set_error(GSMAT_ERR_INVALID_ARG, "table %d: other variables", i);
+        }
+        total += t->rows;
+        bits = std::max(bits, t->id_bits);
+    }
+    if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "%lld rows", (long long)total);
+    gsmat_table *R = new gsmat_table();
+    R->ncols = V;
+    R->id_bits = bits;
+    for (int c = 0; c < V; ++c) R->vars[c] = t0->vars[c];
+    if (total == 0) {
+        *out = R;
+        return GSMAT_OK;
+    }
+    auto fail = [&](int rc) {
+        cudaStreamSynchronize(st);
+        delete R;
+        return rc;
+    };
+    Ctx cx;
+    cx.S = nullptr;
+    cx.st = st;
+    cx.h = pinned_scratch(4 + 8 * GSMAT_MAX_PATTERNS);
+    if (!cx.h) return fail(set_error(GSMAT_ERR_CUDA, "pinned host scratch"));
+    int rc = cx.qstat.alloc(4 * sizeof(int64_t), st);
+    if (rc != GSMAT_OK) return fail(rc);
+    if (cudaMemsetAsync(cx.qstat.p, 0, 4 * sizeof(int64_t), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(set_error(GSMAT_ERR_CUDA, "memset"));
+    }
+    // the tables back to back, then one stable reorder by all columns
+    Tbl cat, res;
+    OutCols oc, ro;
+    if ((rc = alloc_cols(cat, V, total, st, &oc)) != GSMAT_OK) return fail(rc);
+    int64_t at = 0;
+    for (int i = 0; i < k; ++i) {
+        const gsmat_table *t = tables[i];
+        if (t->rows == 0) continue;
+        Cols in;
+        OutCols dst;
+        for (int c = 0; c < kMaxCols; ++c) {
+            in.c[c] = c < V ? t->col[c] : nullptr;
+            dst.c[c] = c < V ? oc.c[c] + at : nullptr;
+        }
+        if ((rc = launch_copy_cols(in, V, t->rows, dst, st)) != GSMAT_OK) return fail(rc);
+        at += t->rows;
+    }
+    if ((rc = alloc_cols(res, V, total, st, &ro)) != GSMAT_OK) return fail(rc);
+    if ((rc = reorder_rows(cat.cols(), V, V, bits, total, ro, st, cx.d_err())) != GSMAT_OK) return fail(rc);
+    int64_t unused = 0;
+    if ((rc = cx.read_count(&unused)) != GSMAT_OK) return fail(rc);
+    R->rows = total;
+    R->stats.result_rows = total;
+    for (int c = 0; c < V; ++c) R->col[c] = res.col[c];
     R->storage = std::move(res.buf);
     R->storage.st = nullptr;  // freed on the legacy stream later
     *out = R;

@@ -15,8 +15,12 @@ struct gsmat_table {
 
 namespace gs {
 
+// shard / n_shards: evaluate only what derives from the shard-th of n_shards
+// contiguous parts of the first plan step's relation.
 int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars, uint32_t flags, cudaStream_t st,
-              gsmat_table **out);
+              gsmat_table **out, int shard = 0, int n_shards = 1);
+// Rows of k tables with the same columns, together, ascending (gsmat_table_merge).
+int table_merge(const gsmat_table *const *tables, int k, cudaStream_t st, gsmat_table **out);
 // sync = false: enqueue only (the caller keeps T alive until st passes it).
 int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream_t st, bool sync = true);
 // Reorder a table given in plan column order (rows ascending in that order)

@@ -128,6 +128,8 @@ def _load():
         "gsmat_plan": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
         "gsmat_plan_cost": ([vp, c_int, c_int, vp, vp, vp, vp, vp], c_int),
         "gsmat_table_project": ([vp, vp, i32, c_int, vp, P(vp)], c_int),
+        "gsmat_query_shard": ([vp, vp, c_int, c_int, u32, i32, i32, vp, P(vp)], c_int),
+        "gsmat_table_merge": ([vp, i32, vp, P(vp)], c_int),
         "gsmat_dict_create": ([P(vp)], c_int),
         "gsmat_dict_free": ([vp], None),
         "gsmat_dict_add_text": ([vp, ctypes.c_char_p, i64, P(i64)], c_int),
@@ -411,6 +413,15 @@ class Store:
     def query(self, bgp, n_vars=None, flags: int = SORTED, stream=None) -> Table:
         return self.query_raw(self.marshal(bgp, n_vars), flags, stream)
 
+    def query_shard(self, bgp, shard: int, n_shards: int, n_vars=None, flags: int = SORTED, stream=None) -> Table:
+        """gsmat_query_shard: the part of the result that derives from the
+        shard-th of n_shards contiguous parts of the first plan step."""
+        pats, n, nv = self.marshal(bgp, n_vars)
+        h = ctypes.c_void_p()
+        _check(_lib.gsmat_query_shard(self._h, pats, n, nv, flags, int(shard), int(n_shards), _stream_ptr(stream),
+                                      ctypes.byref(h)))
+        return Table(h)
+
     def sparql(self, query, dictionary: "Dictionary | None" = None, flags: int = SORTED, stream=None) -> Table:
         """Evaluate SPARQL text (or a parsed Sparql): the BGP by gsmat_query,
         then the projection / DISTINCT by gsmat_table_project when the
@@ -422,6 +433,33 @@ class Store:
         P = T.project(q.projection, q.distinct, stream=stream)
         T.free()
         return P
+
+
+def merge_tables(tables, stream=None) -> Table:
+    """gsmat_table_merge: the rows of tables with the same columns, together,
+    ascending (e.g. the sorted shards of one query)."""
+    arr = (ctypes.c_void_p * len(tables))(*[t._h.value for t in tables])
+    h = ctypes.c_void_p()
+    _check(_lib.gsmat_table_merge(arr, len(tables), _stream_ptr(stream), ctypes.byref(h)))
+    return Table(h)
+
+
+def gather_rows(rows: np.ndarray, dst: int = 0, group=None):
+    """Host side of row sharding across ranks: rank r passes the rows of
+    shard r (int32, rows x cols, e.g. gsmat_query_shard with
+    GSMAT_PLAN_ORDER copied to the host); rank `dst` returns all of them
+    back to back in rank order -- for plan-order shards, the full plan-order
+    result -- and the other ranks return None.  Uses torch.distributed
+    object collectives (any backend)."""
+    import torch.distributed as dist
+
+    rank = dist.get_rank(group)
+    world = dist.get_world_size(group)
+    parts = [None] * world if rank == dst else None
+    dist.gather_object(np.ascontiguousarray(rows, dtype=np.int32), parts, dst=dst, group=group)
+    if rank != dst:
+        return None
+    return np.concatenate([p.reshape(-1, rows.shape[1]) for p in parts], axis=0)
 
 
 # ----------------------------------------------------------------------------

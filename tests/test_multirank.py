@@ -57,3 +57,44 @@ def test_single_process_is_identity():
 
     assert bench.reduce_over_ranks(12.5, 7) == (12.5, 7)
     assert bench.job_value(1, 5, 40, 100.0) == pytest.approx(2000.0)
+
+
+def _shard_worker(rank, world, port, q):
+    import sys
+
+    import numpy as np
+    import torch.distributed as dist
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    import synth
+    from paper_1807_07691_b300 import gsmat
+
+    t = synth.make_graph("tiny")
+    qq = synth.make_queries("tiny", t)[1]
+    full = oracle.OracleIndex(t).query(qq)
+    # rank r holds shard r: the r-th contiguous part, split as the library
+    # splits the first relation (lo = rows * r // world)
+    lo, hi = full.shape[0] * rank // world, full.shape[0] * (rank + 1) // world
+    got = gsmat.gather_rows(full[lo:hi], dst=0)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, None if got is None else bool(np.array_equal(got, full)), full.shape[0]))
+
+
+def test_two_rank_row_shards_gather_gloo():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] is True and res[1][1] is None and res[0][2] > 0
