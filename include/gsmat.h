@@ -457,6 +457,12 @@ GSMAT_API void gsmat_dict_free(gsmat_dict *dict);
  * gsmat_load removes them). */
 GSMAT_API int gsmat_dict_add_text(gsmat_dict *dict, const char *text, int64_t len, int64_t *n_added);
 
+/* Host threads that number the terms of an add (0, the default: one for
+ * texts under 2^16 triples, else up to 16).  The codes do not depend on
+ * it: terms are hashed into partitions numbered in parallel, and the codes
+ * follow from the first positions of the new terms. */
+GSMAT_API int gsmat_dict_set_threads(gsmat_dict *dict, int32_t n_threads);
+
 /* All triples added so far as host int32[n][3] (s, p, o) codes, ready for
  * gsmat_load; owned by the dictionary, valid until the next add or free. */
 GSMAT_API int gsmat_dict_triples(const gsmat_dict *dict, const int32_t **triples, int64_t *n);

@@ -287,6 +287,11 @@ GSMAT_API int gsmat_dict_create(gsmat_dict **out) {
 
 GSMAT_API void gsmat_dict_free(gsmat_dict *dict) { gs::dict_free(dict); }
 
+GSMAT_API int gsmat_dict_set_threads(gsmat_dict *dict, int32_t n_threads) {
+    gs::clear_error();
+    return gs::dict_set_threads(dict, n_threads);
+}
+
 GSMAT_API int gsmat_dict_add_text(gsmat_dict *dict, const char *text, int64_t len, int64_t *n_added) {
     gs::clear_error();
     return gs::dict_add_text(dict, text, len, n_added);

@@ -11,6 +11,7 @@ namespace gs {
 
 int dict_create(gsmat_dict **out);
 void dict_free(gsmat_dict *d);
+int dict_set_threads(gsmat_dict *d, int32_t n_threads);
 int dict_add_text(gsmat_dict *d, const char *text, int64_t len, int64_t *n_added);
 int dict_triples(const gsmat_dict *d, const int32_t **triples, int64_t *n);
 int dict_size(const gsmat_dict *d, int32_t *n_predicates, int32_t *n_terms);

@@ -133,6 +133,7 @@ def _load():
         "gsmat_dict_create": ([P(vp)], c_int),
         "gsmat_dict_free": ([vp], None),
         "gsmat_dict_add_text": ([vp, ctypes.c_char_p, i64, P(i64)], c_int),
+        "gsmat_dict_set_threads": ([vp, i32], c_int),
         "gsmat_dict_triples": ([vp, P(vp), P(i64)], c_int),
         "gsmat_dict_size": ([vp, P(i32), P(i32)], c_int),
         "gsmat_dict_lookup": ([vp, c_int, ctypes.c_char_p, i64, P(i32)], c_int),
@@ -475,12 +476,19 @@ class Dictionary:
     SO = 0
     P = 1
 
-    def __init__(self, text=None):
+    def __init__(self, text=None, threads: int = 0):
         h = ctypes.c_void_p()
         _check(_lib.gsmat_dict_create(ctypes.byref(h)))
         self._h = h
+        if threads:
+            self.set_threads(threads)
         if text is not None:
             self.add_text(text)
+
+    def set_threads(self, n: int):
+        """Host threads numbering the terms (0: automatic); codes do not
+        depend on it."""
+        _check(_lib.gsmat_dict_set_threads(self._h, int(n)))
 
     def __del__(self):
         self.free()

@@ -277,3 +277,30 @@ def test_sparql_limits(gs):
             gs.Sparql(bad)
         assert e.value.code == 1
     assert gs.Sparql("SELECT * { ?a 2147483647 ?b }").patterns[0][1] == 2147483647
+
+
+@pytest.mark.parametrize("threads", [2, 3, 8, 64])
+def test_parallel_numbering_matches_oracle(gs, threads):
+    """Terms numbered by several host threads get the codes of a sequential
+    reading (first occurrence), over several adds and with repeated terms."""
+    rng = np.random.default_rng(threads)
+    o = fe.Dictionary()
+    d = gs.Dictionary(threads=threads)
+    for _ in range(3):
+        text = _rand_data(rng) + "\n".join(
+            f"<http://x.org/n{int(a)}> <http://x.org/r{int(b)}> <http://x.org/n{int(c)}> ."
+            for a, b, c in rng.integers(0, [3000, 7, 3000], size=(4000, 3)))
+        assert d.add_text(text) == len(o.add_text(text))
+    assert d.triples().tolist() == np.array(o.triples, dtype=np.int32).reshape(-1, 3).tolist()
+    assert d.size() == (len(o.h_p), len(o.h_so))
+    so = sorted(o.h_so.items(), key=lambda kv: kv[1])
+    assert d.decode([c for _, c in so], d.SO) == [t for t, _ in so]
+    for term, code in list(o.h_so.items())[::97]:
+        assert d.lookup(term, d.SO) == code
+    # a bad text after that leaves everything as it was
+    with pytest.raises(gs.GsmatError):
+        d.add_text("<a> <p> <b> . <c> <q> ")
+    assert d.size() == (len(o.h_p), len(o.h_so))
+    assert d.triples().shape[0] == len(o.triples)
+    with pytest.raises(gs.GsmatError):
+        d.set_threads(-1)
