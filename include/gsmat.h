@@ -451,8 +451,9 @@ GSMAT_API int gsmat_dict_create(gsmat_dict **out);
 GSMAT_API void gsmat_dict_free(gsmat_dict *dict);
 
 /* Read the statements of text[0..len) and append their encoded triples.
- * On any error (INVALID_ARG for bad text, CAPACITY for more than 2^31 - 1
- * terms of one kind) the dictionary is left as it was.  *n_added (may be
+ * On INVALID_ARG (bad text) or CAPACITY (more than 2^31 - 1 terms of one
+ * kind) the dictionary is left as it was; after OOM (host memory) it must
+ * be freed.  *n_added (may be
  * NULL) receives the number of triples read (repeated triples included:
  * gsmat_load removes them). */
 GSMAT_API int gsmat_dict_add_text(gsmat_dict *dict, const char *text, int64_t len, int64_t *n_added);

@@ -1,6 +1,8 @@
 // The C ABI of libgsmat (include/gsmat.h): argument checks and dispatch.
 #include <string.h>
 
+#include <new>
+
 #include "dict.h"
 #include "join.cuh"
 #include "plan.h"
@@ -294,7 +296,11 @@ GSMAT_API int gsmat_dict_set_threads(gsmat_dict *dict, int32_t n_threads) {
 
 GSMAT_API int gsmat_dict_add_text(gsmat_dict *dict, const char *text, int64_t len, int64_t *n_added) {
     gs::clear_error();
-    return gs::dict_add_text(dict, text, len, n_added);
+    try {
+        return gs::dict_add_text(dict, text, len, n_added);
+    } catch (const std::bad_alloc &) {
+        return set_error(GSMAT_ERR_OOM, "host memory ran out while adding text (free the dictionary)");
+    }
 }
 
 GSMAT_API int gsmat_dict_triples(const gsmat_dict *dict, const int32_t **triples, int64_t *n) {

@@ -19,6 +19,7 @@
 #include <memory>
 #include <string>
 #include <string_view>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -50,9 +51,13 @@ void parallel_for(int threads, int n, F &&f) {
     std::vector<std::thread> pool;
     const int t = std::min(threads, n);
     for (int k = 0; k < t; ++k) {
-        pool.emplace_back([&, k] {
-            for (int i = k; i < n; i += t) f(i);
-        });
+        try {
+            pool.emplace_back([&, k] {
+                for (int i = k; i < n; i += t) f(i);
+            });
+        } catch (const std::system_error &) {
+            for (int i = k; i < n; i += t) f(i);  // no thread to be had: this share inline
+        }
     }
     for (auto &th : pool) th.join();
 }
