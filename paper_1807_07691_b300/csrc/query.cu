@@ -572,6 +572,53 @@ struct FirstOfRunOp {
     }
 };
 
+// -1, 0, 1: row ia of A against row ib of B, lexicographically over V columns
+__device__ __forceinline__ int cmp_rows(const Cols &A, int64_t ia, const Cols &B, int64_t ib, int V) {
+    for (int c = 0; c < V; ++c) {
+        const int32_t x = A.c[c][ia], y = B.c[c][ib];
+        if (x != y) return x < y ? -1 : 1;
+    }
+    return 0;
+}
+
+// *flag = 1 if some row of the n-row table is below its predecessor.
+__global__ void __launch_bounds__(256) unsorted_kernel(Cols A, int64_t n, int V, int *flag) {
+    for (int64_t i = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (cmp_rows(A, i - 1, A, i, V) > 0) {
+            *flag = 1;
+            return;
+        }
+    }
+}
+
+// Merge path: thread t writes outputs [16 t, 16 t + 16) of the merge of the
+// sorted tables A (nA rows) and B (nB rows), A's row first among equal ones.
+// A binary search on the cross diagonal gives how many of the first 16 t
+// outputs come from A; the thread then merges sequentially from there.
+constexpr int kMergeItems = 16;
+__global__ void __launch_bounds__(256) merge2_kernel(Cols A, int64_t nA, Cols B, int64_t nB, int V, OutCols C) {
+    const int64_t total = nA + nB;
+    const int64_t d0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMergeItems;
+    if (d0 >= total) return;
+    int64_t lo = d0 > nB ? d0 - nB : 0, hi = d0 < nA ? d0 : nA;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;  // mid < nA, 0 <= d0 - 1 - mid < nB
+        if (cmp_rows(A, mid, B, d0 - 1 - mid, V) <= 0) lo = mid + 1;
+        else hi = mid;
+    }
+    int64_t i = lo, j = d0 - lo;
+    const int64_t d1 = d0 + kMergeItems < total ? d0 + kMergeItems : total;
+    for (int64_t d = d0; d < d1; ++d) {
+        if (i < nA && (j >= nB || cmp_rows(A, i, B, j, V) <= 0)) {
+            for (int c = 0; c < V; ++c) C.c[c][d] = A.c[c][i];
+            ++i;
+        } else {
+            for (int c = 0; c < V; ++c) C.c[c][d] = B.c[c][j];
+            ++j;
+        }
+    }
+}
+
 }  // namespace
 
 int table_project(const gsmat_table *T, const int32_t *vars, int32_t n, int distinct, cudaStream_t st,
@@ -694,25 +741,72 @@ int table_merge(const gsmat_table *const *tables, int k, cudaStream_t st, gsmat_
         cudaGetLastError();
         return fail(set_error(GSMAT_ERR_CUDA, "memset"));
     }
-    // the tables back to back, then one stable reorder by all columns
-    Tbl cat, res;
-    OutCols oc, ro;
-    if ((rc = alloc_cols(cat, V, total, st, &oc)) != GSMAT_OK) return fail(rc);
-    int64_t at = 0;
+    struct Run {
+        Cols cols;
+        int64_t rows = 0;
+        Tbl own;  // the columns' storage; empty for an input table
+    };
+    std::vector<Run> runs;
     for (int i = 0; i < k; ++i) {
-        const gsmat_table *t = tables[i];
-        if (t->rows == 0) continue;
-        Cols in;
-        OutCols dst;
-        for (int c = 0; c < kMaxCols; ++c) {
-            in.c[c] = c < V ? t->col[c] : nullptr;
-            dst.c[c] = c < V ? oc.c[c] + at : nullptr;
-        }
-        if ((rc = launch_copy_cols(in, V, t->rows, dst, st)) != GSMAT_OK) return fail(rc);
-        at += t->rows;
+        if (tables[i]->rows == 0) continue;
+        Run r;
+        for (int c = 0; c < kMaxCols; ++c) r.cols.c[c] = c < V ? tables[i]->col[c] : nullptr;
+        r.rows = tables[i]->rows;
+        runs.push_back(std::move(r));
     }
-    if ((rc = alloc_cols(res, V, total, st, &ro)) != GSMAT_OK) return fail(rc);
-    if ((rc = reorder_rows(cat.cols(), V, V, bits, total, ro, st, cx.d_err())) != GSMAT_OK) return fail(rc);
+    // are the tables sorted (as query results are)?  then merge them
+    // pairwise by merge path; otherwise put them back to back and reorder
+    int *d_flag = reinterpret_cast<int *>(cx.qstat.as<int64_t>() + 2);
+    for (const Run &r : runs) {
+        if (r.rows < 2) continue;
+        unsorted_kernel<<<grid_1d(r.rows, 256), 256, 0, st>>>(r.cols, r.rows, V, d_flag);
+        GS_LAUNCH_CHECK();
+    }
+    if ((rc = read_words(cx.qstat.p, cx.h, 3, st)) != GSMAT_OK) return fail(rc);
+    const bool sorted = reinterpret_cast<const int *>(cx.h + 2)[0] == 0;
+    Tbl res;
+    OutCols ro;
+    if (!sorted) {
+        Tbl cat;
+        OutCols oc;
+        if ((rc = alloc_cols(cat, V, total, st, &oc)) != GSMAT_OK) return fail(rc);
+        int64_t at = 0;
+        for (const Run &r : runs) {
+            OutCols dst;
+            for (int c = 0; c < kMaxCols; ++c) dst.c[c] = c < V ? oc.c[c] + at : nullptr;
+            if ((rc = launch_copy_cols(r.cols, V, r.rows, dst, st)) != GSMAT_OK) return fail(rc);
+            at += r.rows;
+        }
+        if ((rc = alloc_cols(res, V, total, st, &ro)) != GSMAT_OK) return fail(rc);
+        if ((rc = reorder_rows(cat.cols(), V, V, bits, total, ro, st, cx.d_err())) != GSMAT_OK) return fail(rc);
+    } else if (runs.size() == 1) {
+        if ((rc = alloc_cols(res, V, total, st, &ro)) != GSMAT_OK) return fail(rc);
+        if ((rc = launch_copy_cols(runs[0].cols, V, total, ro, st)) != GSMAT_OK) return fail(rc);
+    } else {
+        // rounds of pairwise merges (the odd run waits a round, keeping its
+        // storage); replacing a round's runs frees the merged inputs, in
+        // stream order after the merges that read them
+        while (runs.size() > 1) {
+            std::vector<Run> next;
+            for (size_t a = 0; a + 1 < runs.size(); a += 2) {
+                const Run &A = runs[a], &B = runs[a + 1];
+                Run m;
+                m.rows = A.rows + B.rows;
+                OutCols oc;
+                if ((rc = alloc_cols(m.own, V, m.rows, st, &oc)) != GSMAT_OK) return fail(rc);
+                // one thread per kMergeItems outputs, no grid cap
+                const int64_t threads = (m.rows + kMergeItems - 1) / kMergeItems;
+                const unsigned blocks = (unsigned)((threads + 255) / 256);
+                merge2_kernel<<<blocks, 256, 0, st>>>(A.cols, A.rows, B.cols, B.rows, V, oc);
+                GS_LAUNCH_CHECK();
+                m.cols = m.own.cols();
+                next.push_back(std::move(m));
+            }
+            if (runs.size() % 2) next.push_back(std::move(runs.back()));
+            runs = std::move(next);
+        }
+        res = std::move(runs[0].own);  // made by the last merge
+    }
     int64_t unused = 0;
     if ((rc = cx.read_count(&unused)) != GSMAT_OK) return fail(rc);
     R->rows = total;
