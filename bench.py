@@ -261,18 +261,19 @@ def run_gsmat(args):
     batched = None
     served = None
     planner = None
+    bq = None
     if not args.no_batched:
         batched, bq, tuned = run_batched(args, gs, torch, d_tri, stream)
         if not args.no_planner:
             planner = run_planner(args, gs, torch, d_tri, stream, queries, bq, tuned)
-        if not args.no_served:
-            served = run_served(args, gs, torch, d_tri, stream, bq)
     frontend = None
     if not args.no_frontend:
         frontend = run_frontend(args, gs, torch, d_tri, stream, triples, queries)
     shards = None
     if not args.no_shards:
         shards = run_shards(args, gs, torch, d_tri, stream, queries)
+    if bq is not None and not args.no_served:  # the served mix is the batched one
+        served = run_served(args, gs, torch, d_tri, stream, bq)
     served_large = None
     if args.served_graph == "large" and rank == 0:
         served_large = run_served_large(args, gs, torch, stream)
