@@ -290,7 +290,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
             GS_TRY(launch_isect_count(S->view, side_a, pa, a, side_b, pb, b, cur.rows, cnt.as<int32_t>(), st));
             GS_TRY(exclusive_scan_i32(cnt.as<int32_t>(), off.as<int64_t>(), cur.rows, st, cx.d_err()));
             GS_CUDA(cudaMemcpyAsync(cx.d_count(), off.as<int64_t>() + cur.rows, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-            int64_t total;
+            int64_t total = 0;
             GS_TRY(cx.read_count(&total));
             if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "step %d: %lld rows", step, (long long)total);
             bool last_live = true;  // every later step runs inside this one
@@ -320,7 +320,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
             const int keep = (count_only && last) ? 0 : cur.ncols;
             GS_TRY(alloc_cols(nxt, cur.ncols, cur.rows, st, &oc));
             GS_TRY(launch_filter(S->view, ps0, ps1, vs, vo, cur.cols(), keep, cur.rows, oc, cx.d_count(), cx.d_err(), st));
-            int64_t cnt;
+            int64_t cnt = 0;
             GS_TRY(cx.read_count(&cnt));
             nxt.rows = cnt;
             for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
@@ -361,7 +361,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
                 GS_TRY(fst.alloc(sizeof(int32_t) * (size_t)cur.rows, st));
                 GS_TRY(launch_count_scan(S->view, side, ps, cur.col[xc], cur.rows, off.as<int64_t>(), fst.as<int32_t>(),
                                          cx.d_count(), cx.d_err(), st));
-                int64_t total;
+                int64_t total = 0;
                 GS_TRY(cx.read_count(&total));
                 if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "step %d: %lld rows", step, (long long)total);
                 if (count_only && last) {
@@ -379,7 +379,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         } else {  // CROSS
             Cols rel;
             int rc;
-            int64_t m;
+            int64_t m = 0;
             DevBuf diag;
             int32_t rv[2];
             if (p.s == p.o) {  // ?x p ?x
