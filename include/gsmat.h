@@ -27,6 +27,8 @@
  *  - Threading: a store is read-only after gsmat_load, so queries on one
  *    store may run concurrently from several host threads on different
  *    streams.  gsmat_set_allocator and gsmat_profile_* are process-global.
+ *    A dictionary may be read (lookups, decoding, parsing) from several
+ *    threads at once, but not while text is being added to it.
  */
 #ifndef GSMAT_H_
 #define GSMAT_H_
