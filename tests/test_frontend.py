@@ -304,3 +304,37 @@ def test_parallel_numbering_matches_oracle(gs, threads):
     assert d.triples().shape[0] == len(o.triples)
     with pytest.raises(gs.GsmatError):
         d.set_threads(-1)
+
+
+def test_host_entry_points_reject_bad_arguments(gs):
+    import ctypes
+
+    lib = gs.lib()
+    h = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    assert lib.gsmat_dict_create(None) == 1
+    assert lib.gsmat_dict_create(ctypes.byref(h)) == 0
+    assert lib.gsmat_dict_add_text(None, b"<a> <p> <b> .", 13, ctypes.byref(n)) == 1
+    assert lib.gsmat_dict_add_text(h, None, 5, ctypes.byref(n)) == 1
+    assert lib.gsmat_dict_add_text(h, b"x", -1, ctypes.byref(n)) == 1
+    assert lib.gsmat_dict_add_text(h, None, 0, ctypes.byref(n)) == 0 and n.value == 0  # empty text
+    assert lib.gsmat_dict_triples(h, None, ctypes.byref(n)) == 1
+    code = ctypes.c_int32()
+    assert lib.gsmat_dict_lookup(h, 2, b"<a>", 3, ctypes.byref(code)) == 1  # bad kind
+    assert lib.gsmat_dict_lookup(h, 0, b"<a>", 3, None) == 1
+    assert lib.gsmat_dict_decode(h, 0, None, 1, None, None) == 1
+    assert lib.gsmat_dict_decode(h, 0, None, 0, None, None) == 0  # nothing to decode
+    assert lib.gsmat_dict_set_threads(h, 257) == 1
+    q = ctypes.c_void_p()
+    assert lib.gsmat_sparql_parse(h, b"SELECT * { ?a 1 ?b }", 20, None) == 1
+    assert lib.gsmat_sparql_parse(h, None, 4, ctypes.byref(q)) == 1
+    assert lib.gsmat_sparql_info(None, None, None, None, None, None, None) == 1
+    assert lib.gsmat_sparql_var_name(None, 0) is None
+    assert lib.gsmat_sparql_parse(None, b"SELECT * { ?a 1 ?b }", 20, ctypes.byref(q)) == 0
+    assert lib.gsmat_sparql_var_name(q, 2) is None and lib.gsmat_sparql_var_name(q, -1) is None
+    assert lib.gsmat_sparql_var_name(q, 1) == b"b"
+    lib.gsmat_sparql_free(q)
+    lib.gsmat_sparql_free(None)
+    lib.gsmat_dict_free(h)
+    lib.gsmat_dict_free(None)
+    assert lib.gsmat_last_error() is not None
