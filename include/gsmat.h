@@ -203,10 +203,12 @@ GSMAT_API int gsmat_query_shard(const gsmat_store *store, const gsmat_pattern *p
                                 uint32_t flags, int32_t shard, int32_t n_shards, gsmat_stream_t stream,
                                 gsmat_table **out);
 
-/* The rows of k >= 1 tables that hold the same variables in the same column
+/* (No counterpart in the paper: the gather step of row sharding.)
+ * The rows of k >= 1 tables that hold the same variables in the same column
  * order (e.g. the shards of one query), together in one new table, rows
- * ascending lexicographically in that column order: the tables are copied
- * back to back and reordered by all columns on the device.  INVALID_ARG
+ * ascending lexicographically in that column order: sorted tables (every
+ * query result is) are merged pairwise by merge path on the device, others
+ * copied back to back and reordered by all columns.  INVALID_ARG
  * for other columns or a count-only table; CAPACITY above 2^32 - 1 rows.
  * Synchronises `stream`. */
 GSMAT_API int gsmat_table_merge(const gsmat_table *const *tables, int32_t k, gsmat_stream_t stream,
@@ -486,7 +488,8 @@ GSMAT_API int gsmat_dict_decode(const gsmat_dict *dict, int kind, const int32_t 
 /* A parsed SPARQL query. */
 typedef struct gsmat_sparql gsmat_sparql;
 
-/* Parse SPARQL text: PREFIX declarations, SELECT [DISTINCT] followed by
+/* Parse SPARQL text (the Select|Project|Join form over one BGP that
+ * Sec. 3.2 shows): PREFIX declarations, SELECT [DISTINCT] followed by
  * variables (?name or $name) or '*', an optional WHERE and a brace-enclosed
  * basic graph pattern of triple patterns separated by '.', with ';' and ','
  * lists and the terms of the data text.  Variables are numbered 0, 1, ...
