@@ -290,8 +290,10 @@ class Table:
             return dst
         fn = _lib.gsmat_table_copy if sync else _lib.gsmat_table_copy_async
         if hasattr(dst, "data_ptr"):
-            if dst.numel() < rows * cols:
-                raise ValueError("destination too small")
+            import torch
+
+            if dst.dtype != torch.int32 or not dst.is_contiguous() or dst.numel() < rows * cols:
+                raise ValueError("destination must be a contiguous int32 tensor of rows*cols elements")
             _check(fn(self._h, ctypes.c_void_p(dst.data_ptr()), 1 if dst.is_cuda else 0, _stream_ptr(stream)))
         else:
             if dst.size < rows * cols or dst.dtype != np.int32 or not dst.flags.c_contiguous:
@@ -650,10 +652,20 @@ class Batch:
         return out
 
     def copy_to(self, i: int, dst, stream=None):
+        """Copy result i row-major into dst (a contiguous int32 numpy array
+        or torch tensor, host or CUDA, of at least rows*cols elements)."""
         rows, cols, _ = self.result(i)
         if rows and cols:
-            on_dev = 1 if getattr(dst, "is_cuda", False) else 0
-            ptr = dst.data_ptr() if hasattr(dst, "data_ptr") else dst.ctypes.data
+            if hasattr(dst, "data_ptr"):
+                import torch
+
+                if dst.dtype != torch.int32 or not dst.is_contiguous() or dst.numel() < rows * cols:
+                    raise ValueError("destination must be a contiguous int32 tensor of rows*cols elements")
+                on_dev, ptr = (1 if dst.is_cuda else 0), dst.data_ptr()
+            else:
+                if dst.dtype != np.int32 or not dst.flags.c_contiguous or dst.size < rows * cols:
+                    raise ValueError("destination must be a contiguous int32 array of rows*cols elements")
+                on_dev, ptr = 0, dst.ctypes.data
             _check(_lib.gsmat_batch_copy(self._h, i, ctypes.c_void_p(ptr), on_dev, _stream_ptr(stream)))
         return dst
 
