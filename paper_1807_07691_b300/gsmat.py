@@ -772,8 +772,29 @@ def plan(bgp, keys, stats, n_vars=None, cost: bool = False):
     return order.tolist(), kinds.tolist(), est.tolist()
 
 
+def _require(t, dtypes, n_min: int, what: str):
+    """A contiguous CUDA tensor of one of `dtypes` with >= n_min elements: the
+    library dereferences these pointers on the device, so a host tensor,
+    a strided view or a short buffer is refused here."""
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{what}: a CUDA tensor is required")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{what}: dtype {t.dtype} is not one of {tuple(dtypes)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: the tensor must be contiguous")
+    if t.numel() < n_min:
+        raise ValueError(f"{what}: {t.numel()} elements, {n_min} needed")
+
+
 def radix_sort_u64(keys, vals=None, begin_bit: int = 0, end_bit: int = 64, stream=None):
     """Sort a CUDA uint64/int64 tensor in place (optional int32/uint32 payload)."""
+    import torch
+
+    _require(keys, (torch.int64, torch.uint64), 0, "keys")
+    if vals is not None:
+        _require(vals, (torch.int32, torch.uint32), keys.numel(), "vals")
     _check(_lib.gsmat_radix_sort_u64(ctypes.c_void_p(keys.data_ptr()),
                                      ctypes.c_void_p(vals.data_ptr()) if vals is not None else None,
                                      keys.numel(), begin_bit, end_bit, _stream_ptr(stream)))
@@ -786,10 +807,18 @@ def sort_rows(cols, m: int, bits: int, out=None, stream=None, flags: int = 0):
     """Stable lexicographic reorder of the rows of V int32 CUDA columns by
     the first m; returns (or fills) V new columns.  flags: SORT_CARRY /
     SORT_GATHER force how the other columns travel (0: by size)."""
+    import torch
+
     V = len(cols)
+    n = cols[0].numel() if V else 0
+    for i, c in enumerate(cols):
+        _require(c, (torch.int32,), n, f"column {i}")
     if out is None:
         out = [c.new_empty(c.shape) for c in cols]
-    n = cols[0].numel() if V else 0
+    if len(out) != V:
+        raise ValueError(f"{len(out)} output columns for {V} input columns")
+    for i, c in enumerate(out):
+        _require(c, (torch.int32,), n, f"output column {i}")
     src = (ctypes.c_void_p * max(V, 1))(*[c.data_ptr() for c in cols])
     dst = (ctypes.c_void_p * max(V, 1))(*[c.data_ptr() for c in out])
     _check(_lib.gsmat_sort_rows(src, V, m, bits, n, dst, flags, _stream_ptr(stream)))
@@ -798,6 +827,10 @@ def sort_rows(cols, m: int, bits: int, out=None, stream=None, flags: int = 0):
 
 def exclusive_scan_i32(src, dst, stream=None):
     """dst[0..n] (int64 CUDA tensor) = exclusive prefix sums of src (int32)."""
+    import torch
+
+    _require(src, (torch.int32,), 0, "src")
+    _require(dst, (torch.int64,), src.numel() + 1, "dst")
     _check(_lib.gsmat_exclusive_scan_i32(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
                                          src.numel(), _stream_ptr(stream)))
 
@@ -805,6 +838,10 @@ def exclusive_scan_i32(src, dst, stream=None):
 def exclusive_scan_i32_noalloc(src, dst, stream=None):
     """As exclusive_scan_i32, with no device allocation (static scratch;
     n <= exclusive_scan_i32_noalloc_max(); overlapping calls race)."""
+    import torch
+
+    _require(src, (torch.int32,), 0, "src")
+    _require(dst, (torch.int64,), src.numel() + 1, "dst")
     _check(_lib.gsmat_exclusive_scan_i32_noalloc(ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
                                                  src.numel(), _stream_ptr(stream)))
 

@@ -151,3 +151,26 @@ def test_lazy_package_names_resolve(gs):
     for name in dir(pkg):
         if name not in ("build", "gsmat"):
             assert getattr(pkg, name) is getattr(gs, name), name
+
+
+def test_primitives_refuse_host_and_mismatched_tensors(gs):
+    """The device primitives' bindings refuse what the library would
+    dereference wrongly on the device: host tensors, wrong dtypes, short or
+    strided buffers (checked before any library call, so CPU only)."""
+    import torch
+
+    k64 = torch.zeros(8, dtype=torch.int64)
+    i32 = torch.zeros(8, dtype=torch.int32)
+    for call in (lambda: gs.radix_sort_u64(k64),
+                 lambda: gs.exclusive_scan_i32(i32, torch.zeros(9, dtype=torch.int64)),
+                 lambda: gs.exclusive_scan_i32_noalloc(i32, torch.zeros(9, dtype=torch.int64)),
+                 lambda: gs.sort_rows([i32, i32], 1, 8),
+                 lambda: gs.sort_rows([torch.zeros(8, dtype=torch.float32)], 1, 8)):
+        with pytest.raises(ValueError):
+            call()
+    from paper_1807_07691_b300 import gsmat
+
+    with pytest.raises(ValueError):
+        gsmat._require(k64, (torch.int64,), 0, "keys")  # host tensor
+    with pytest.raises(ValueError):
+        gsmat._require(k64[::2], (torch.int64,), 0, "keys")
