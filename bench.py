@@ -299,9 +299,12 @@ def run_gsmat(args):
         achieved = p["algo_bytes"] / 1e9 / (p["total_ms"] / 1e3) if p["total_ms"] > 0 else 0.0
         per_launch_algo = p["algo_bytes"] / max(1, p["launches"])
         traffic = round(per_launch_algo * traffic_ratio[name]) if name in traffic_ratio else None
+        per_launch_ms = p["total_ms"] / max(1, p["launches"])
         roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "per_launch_ms": round(p["total_ms"] / max(1, p["launches"]), 4),
+                # DRAM bytes (from the ncu ratio) over the same event time
+                "dram_GBps": round(traffic / 1e9 / (per_launch_ms / 1e3), 1) if traffic and per_launch_ms > 0 else None,
+                "per_launch_ms": round(per_launch_ms, 4),
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
     launches = int(lc1 - lc0)  # kernels the library launched in the timed steps
     value = job_value(ws, args.steps, nq, total_ms)
