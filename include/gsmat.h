@@ -50,9 +50,11 @@ typedef struct CUstream_st *gsmat_stream_t; /* == cudaStream_t */
 
 /* Status codes. */
 #define GSMAT_OK 0
-#define GSMAT_ERR_INVALID_ARG 1  /* bad pointer, size, id or BGP shape */
-#define GSMAT_ERR_UNSUPPORTED 2  /* a variable predicate (Sec. 6.3 assumes known predicates) */
-#define GSMAT_ERR_OOM 3          /* the allocator hook returned NULL */
+#define GSMAT_ERR_INVALID_ARG 1  /* bad pointer, size, id, BGP shape or text */
+#define GSMAT_ERR_UNSUPPORTED 2  /* a variable predicate (Sec. 6.3 assumes known predicates), or
+                                    SPARQL beyond one basic graph pattern */
+#define GSMAT_ERR_OOM 3          /* the allocator hook returned NULL (host memory, for the
+                                    dictionary) */
 #define GSMAT_ERR_CAPACITY 4     /* a table would exceed the library's row/offset limits */
 #define GSMAT_ERR_CUDA 5         /* a CUDA runtime call failed */
 #define GSMAT_ERR_DEVICE_CHECK 6 /* a kernel's own check fired (bounded wait expired) */
@@ -174,8 +176,9 @@ typedef struct {
  *  n_vars         0 <= n_vars <= 32; every variable 0..n_vars-1 must occur.
  * The plan is Alg. 1 (connected minimal upper bound) with the
  * intermediate-size estimate of Sec. 6.2 (with GSMAT_PLAN_COST, the
- * connected order of least estimated cost, gsmat_plan_cost); each step is one SM-based join
- * (Alg. 3) of the running relation with the next pattern's matrix:
+ * connected order of least estimated cost, gsmat_plan_cost); each step is
+ * one SM-based join (Alg. 3) of the running relation with the next
+ * pattern's matrix:
  * a gather-expand along the pattern's CSR or CSC rows when one end is bound,
  * a membership filter with prefix-sum compaction when both ends are bound,
  * a Cartesian product when neither is.  Result semantics: every assignment
