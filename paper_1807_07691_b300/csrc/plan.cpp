@@ -26,6 +26,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <limits>
 #include <vector>
 
 #include "plan.h"
@@ -115,7 +116,31 @@ struct CostSearch {
     uint64_t vm[kCostPlanMax];  // variables of L[t]
     int cur[kCostPlanMax];
     int best_order[kCostPlanMax];
+    double fmin[kCostPlanMax];  // least factor L[t] can contribute as any step
     double best;
+
+    // Lower bound on what the remaining patterns add to the cost from a
+    // running estimate e: every factor is at least its pattern's fmin, and
+    // a product of positive factors is at least the product of as many of
+    // the smallest fmin, so the k-th remaining running estimate is at least
+    // e times the k smallest fmin.  Scaled down by 1e-9 so that rounding
+    // never cuts an order that is cheaper by less than that.
+    double remaining_bound(unsigned taken, double e) const {
+        double f[kCostPlanMax];
+        int r = 0;
+        for (int t = 0; t < n; ++t) {
+            if ((taken >> t) & 1) continue;
+            int j = r++;
+            for (; j > 0 && f[j - 1] > fmin[t]; --j) f[j] = f[j - 1];
+            f[j] = fmin[t];
+        }
+        double sum = 0.0, run = e;
+        for (int k = 0; k < r; ++k) {
+            run *= f[k];
+            sum += run;
+        }
+        return sum * (1.0 - 1e-9);
+    }
 
     void run(int depth, unsigned taken, uint64_t bound, double e, double partial) {
         if (depth == n) {
@@ -125,6 +150,7 @@ struct CostSearch {
             }
             return;
         }
+        if (depth > 0 && depth < n - 1 && !(partial + remaining_bound(taken, e) < best)) return;
         bool connected = false;
         if (depth > 0) {
             for (int t = 0; t < n && !connected; ++t) connected = !((taken >> t) & 1) && (vm[t] & bound);
@@ -161,6 +187,29 @@ int plan_bgp_cost(const gsmat_pattern *pats, int n, const int64_t *keys, const g
     for (int i = 0; i < n; ++i) cs.L[i] = i;
     std::stable_sort(cs.L, cs.L + n, [&](int a, int b) { return keys[a] < keys[b]; });
     for (int t = 0; t < n; ++t) cs.vm[t] = vars_of(pats[cs.L[t]]);
+    // fmin: the least factor over the step kinds a pattern can take; a
+    // variable end can be known beforehand only if another pattern (or the
+    // other end of this one) holds the variable too
+    int occ[64] = {0};
+    for (int i = 0; i < n; ++i) {
+        const uint64_t v = vars_of(pats[i]);
+        for (int b = 0; b < 64; ++b) occ[b] += (int)((v >> b) & 1);
+    }
+    for (int t = 0; t < n; ++t) {
+        const int i = cs.L[t];
+        const gsmat_pattern &p = pats[i];
+        const bool s_pre = !p.s_var || occ[p.s] > 1;  // s can be known before this step
+        const bool o_pre = !p.o_var || occ[p.o] > 1;
+        double f = std::numeric_limits<double>::infinity();
+        if (p.s_var && p.o_var) f = std::min(f, step_factor(p, GSMAT_STEP_CROSS, keys[i], stats[i]));
+        if (s_pre && p.o_var) f = std::min(f, step_factor(p, GSMAT_STEP_EXPAND_S, keys[i], stats[i]));
+        if (o_pre && p.s_var) f = std::min(f, step_factor(p, GSMAT_STEP_EXPAND_O, keys[i], stats[i]));
+        if ((s_pre && o_pre) || (p.s_var && p.o_var && p.s == p.o)) {
+            f = std::min(f, step_factor(p, GSMAT_STEP_FILTER, keys[i], stats[i]));
+        }
+        if (!(f >= 0.0) || f == std::numeric_limits<double>::infinity()) f = 0.0;  // no usable bound
+        cs.fmin[t] = f;
+    }
     // Alg. 1's order is the first connected order of the search: start from
     // it, so that it wins every tie and bounds the search from the outset
     double greedy_cost = 0.0;
