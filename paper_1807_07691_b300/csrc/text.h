@@ -35,10 +35,20 @@ struct Tok {
     std::string_view dtype;
 };
 
-inline bool is_ws(char c) { return c == ' ' || c == '\t' || c == '\r' || c == '\n'; }
-inline bool is_special(char c) {
-    return c == '<' || c == '>' || c == '"' || c == '{' || c == '}' || c == ';' || c == ',' || c == '.';
-}
+// Byte classes: whitespace, and the bytes that end a word.
+struct ByteClass {
+    uint8_t c[256];
+    constexpr ByteClass() : c() {
+        const char ws[] = " \t\r\n";
+        const char sp[] = "<>\"{};,.";
+        for (const char *q = ws; *q; ++q) c[(unsigned char)*q] = 3;  // whitespace ends a word too
+        for (const char *q = sp; *q; ++q) c[(unsigned char)*q] = 2;
+    }
+};
+inline constexpr ByteClass kByteClass{};
+inline bool is_ws(char c) { return kByteClass.c[(unsigned char)c] == 3; }
+inline bool is_special(char c) { return kByteClass.c[(unsigned char)c] == 2; }
+inline bool ends_word(char c) { return kByteClass.c[(unsigned char)c] != 0; }
 inline bool is_alnum_ascii(char c) {
     return (c >= '0' && c <= '9') || (c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z');
 }
@@ -138,7 +148,7 @@ inline int Lexer::scan(Tok &t) {
                 j = e + 1;
             } else {
                 size_t e = k;
-                while (e < n && !is_ws(s_[e]) && !is_special(s_[e])) ++e;
+                while (e < n && !ends_word(s_[e])) ++e;
                 if (e == k) return set_error(GSMAT_ERR_INVALID_ARG, "empty datatype at byte %zu", k);
                 t.dtype_kind = kWord;
                 t.dtype = s_.substr(k, e - k);
@@ -152,7 +162,7 @@ inline int Lexer::scan(Tok &t) {
     }
     if (c == '>') return set_error(GSMAT_ERR_INVALID_ARG, "unexpected '>' at byte %zu", i_);
     size_t j = i_;
-    while (j < n && !is_ws(s_[j]) && !is_special(s_[j])) ++j;
+    while (j < n && !ends_word(s_[j])) ++j;
     const std::string_view w = s_.substr(i_, j - i_);
     i_ = j;
     if (w[0] == '?' || w[0] == '$') {
