@@ -16,9 +16,11 @@ Contents:
   intermediate-size estimate of Sec. 6.2 (Prop. 1, Thm. 1, Thm. 2).
 
 Parity status: the join and the storage are pinned (paper worked examples,
-brute force, invariants); the planner's order is pinned by the paper's BGP
-sequence example; the intermediate-size *estimate* is "parity unpinned"
-beyond the Thm. 2 upper-bound invariant.
+brute force, invariants; the matrices, their row arrays on both sides and
+the row statistics by the D_G example); the planner's order is pinned by the
+paper's BGP sequence example; the intermediate-size estimate (a stated
+reading, the paper gives only bounds) is pinned by hand-costed cases of
+every step kind on D_G's statistics and by the Thm. 1 upper bound.
 """
 
 from .join import OracleIndex, oracle_query, OracleError

@@ -21,8 +21,9 @@ a pattern in both branches, so the prose of Sec. 6.2.1 is followed):
 
 Intermediate-size estimate (Sec. 6.2.1, Prop. 1 and Thm. 1-2 bound the
 accumulated number of intermediate results; the paper gives no estimator,
-so this one is a stated reading and its parity is UNPINNED apart from the
-Thm. 1 upper bound): starting from 1 (the empty assignment), each step
+so the formula is a stated reading; the restatement is pinned by
+hand-costed cases of every step kind on the paper's D_G statistics and by
+the Thm. 1 upper bound): starting from 1 (the empty assignment), each step
 multiplies the running estimate by
   CROSS   (no end bound)              key of the pattern
   EXPAND  from a constant end         key (the constant's row size)

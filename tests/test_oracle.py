@@ -56,6 +56,91 @@ def test_dg_auxiliary_arrays():
     assert g["aux_B_W_entry"] in storage.aux_arrays(M1, 1).tolist()
 
 
+def test_dg_csr_by_both_sides():
+    """csr_by: the doubly-compressed rows of every M_h (Sec. 5.3) on the
+    subject side (CSR) and the object side (CSC), i.e. the Row and Rpos
+    arrays of Sec. 6.3 for either join column.  Expected arrays: the printed
+    matrices read row by row by hand (fixture)."""
+    g = golden("dg_example.json")
+    cube = np.array(g["cube_spo"])
+    for side, key in (("s", "csr_by_s"), ("o", "csr_by_o")):
+        got = storage.csr_by(cube, side)
+        assert sorted(got) == [1, 2, 3]
+        for h, (rid, ptr, ent) in got.items():
+            assert [rid.tolist(), ptr.tolist(), ent.tolist()] == g[key][str(h)], (side, h)
+    # (Row, Num, Rpos) of :likes on X as printed: Num = pointer difference,
+    # Rpos = pointer + 1
+    rid, ptr, _ = storage.csr_by(cube, "s")[1]
+    aux = [[int(r), int(ptr[i + 1] - ptr[i]), int(ptr[i]) + 1] for i, r in enumerate(rid)]
+    assert aux == g["aux_A_X"]
+    # and the entry of :likes on W (object side) that the paper prints
+    rid, ptr, _ = storage.csr_by(cube, "o")[1]
+    aux_o = [[int(r), int(ptr[i + 1] - ptr[i]), int(ptr[i]) + 1] for i, r in enumerate(rid)]
+    assert g["aux_B_W_entry"] in aux_o
+
+
+def test_dg_statistics_row_counts():
+    """statistics: m = nnz (Sec. 5.3) and the distinct subjects and objects
+    of each printed matrix (nr_s, nr_o), counted by hand (fixture)."""
+    g = golden("dg_example.json")
+    stats = storage.statistics(np.array(g["cube_spo"]))
+    assert {str(h): [s["nnz"], s["nr_s"], s["nr_o"]] for h, s in stats.items()} == g["stats_nnz_nrs_nro"]
+
+
+def _dg_stats():
+    # (nnz, nr_s, nr_o) of :likes (1), :follows (2), :related (3), as in the fixture
+    g = golden("dg_example.json")
+    return {int(h): dict(nnz=v[0], nr_s=v[1], nr_o=v[2]) for h, v in g["stats_nnz_nrs_nro"].items()}
+
+
+def test_estimate_filter_step_hand_costed():
+    """The FILTER factor min(1, nnz / (nr_s nr_o)) of the estimate (Sec.
+    6.2.1 reading), costed by hand on D_G's statistics:
+      ?x :likes ?w . ?x :follows ?w   in that order
+      CROSS 3 (m of :likes), then FILTER by :follows: 3 * 4/(3*3) = 4/3;
+      cost 3 + 4/3 = 13/3.
+      ?x :follows ?w . ?x :related ?w: 4, then 4 * 2/(2*1) = 4; cost 8."""
+    st = _dg_stats()
+    pats = [(0, 1, 1, 1, 1), (0, 2, 1, 1, 1)]
+    per_step, total, kinds = planner.estimate(pats, [0, 1], [3, 4], [st[1], st[2]])
+    assert kinds == [planner.STEP_CROSS, planner.STEP_FILTER]
+    assert per_step == pytest.approx([3.0, 4.0 / 3.0], rel=1e-15)
+    assert total == pytest.approx(13.0 / 3.0, rel=1e-15)
+    pats = [(0, 2, 1, 1, 1), (0, 3, 1, 1, 1)]
+    per_step, total, kinds = planner.estimate(pats, [0, 1], [4, 2], [st[2], st[3]])
+    assert kinds == [planner.STEP_CROSS, planner.STEP_FILTER]
+    assert per_step == [4.0, 4.0] and total == 8.0
+
+
+def test_estimate_constant_anchored_expand_hand_costed():
+    """EXPAND from a constant end multiplies by that constant's row size
+    (its key); EXPAND from a bound variable by nnz / nr on that side; a
+    pattern with a constant end whose other end is bound is a FILTER.  By
+    hand on D_G (A = 1, I2 = 3):
+      A :follows ?y . ?y :follows ?z . ?z :likes I2
+        A's :follows row has 1 entry      -> 1
+        * nnz/nr_s of :follows = 4/3      -> 4/3
+        * FILTER 3/(2*2) of :likes        -> 1;      cost 1 + 4/3 + 1 = 10/3
+      ?x :likes I2 . ?x :follows ?y
+        I2's :likes column has 2 entries  -> 2  (object side)
+        * 4/3                             -> 8/3;    cost 2 + 8/3 = 14/3"""
+    st = _dg_stats()
+    pats = [(1, 2, 0, 0, 1), (0, 2, 1, 1, 1), (1, 1, 3, 1, 0)]
+    per_step, total, kinds = planner.estimate(pats, [0, 1, 2], [1, 4, 2], [st[2], st[2], st[1]])
+    assert kinds == [planner.STEP_EXPAND_S, planner.STEP_EXPAND_S, planner.STEP_FILTER]
+    assert per_step == pytest.approx([1.0, 4.0 / 3.0, 1.0], rel=1e-15)
+    assert total == pytest.approx(10.0 / 3.0, rel=1e-15)
+    pats = [(0, 1, 3, 1, 0), (0, 2, 1, 1, 1)]
+    per_step, total, kinds = planner.estimate(pats, [0, 1], [2, 4], [st[1], st[2]])
+    assert kinds == [planner.STEP_EXPAND_O, planner.STEP_EXPAND_S]
+    assert per_step == pytest.approx([2.0, 8.0 / 3.0], rel=1e-15)
+    assert total == pytest.approx(14.0 / 3.0, rel=1e-15)
+    # the hand-counted row sizes are the oracle's rows for those constants
+    ix = oracle.OracleIndex(np.array(golden("dg_example.json")["cube_spo"]))
+    assert ix.query([(1, 2, 0, 0, 1)], 1).shape[0] == 1
+    assert ix.query([(0, 1, 3, 1, 0)], 1).shape[0] == 2
+
+
 def test_dg_first_intermediate_row():
     g = golden("dg_example.json")
     ix = oracle.OracleIndex(np.array(g["cube_spo"]))
