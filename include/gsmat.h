@@ -603,13 +603,18 @@ GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int6
  *    larger n returns GSMAT_ERR_CAPACITY without touching the device.
  *  - The first call on a device looks the array's device address up once
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the rest of the
+ *    process: it does not survive cudaDeviceReset (which reloads the
+ *    library's device code), so do not call this after a device reset.
  *  - Every call shares the array and clears the part it uses (stream-ordered
  *    memsets) before its kernel; calls whose work overlaps on the GPU (other
  *    streams, other host threads) race on it and must be serialised by the
  *    caller.
- *  - d_in, d_out: device arrays as for gsmat_exclusive_scan_i32.  Does not
- *    synchronise. */
+ *  - d_in, d_out: device arrays as for gsmat_exclusive_scan_i32.  n = 0
+ *    writes d_out[0] = 0.
+ *  - Does not synchronise, so a bounded wait that expires inside is not
+ *    reported (output unspecified); the error word it sets in the array is
+ *    cleared by the next call. */
 GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_out, int64_t n,
                                                gsmat_stream_t stream);
 GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void);

@@ -31,16 +31,17 @@ def env():
     return gs, torch
 
 
-def _scan_both(gs, torch, x):
+def _scan_both(gs, torch, x, stream=None):
     lib = gs.lib()
-    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    stream = stream or torch.cuda.current_stream()
+    st = ctypes.c_void_p(stream.cuda_stream)
     n = x.numel()
     ref = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
     out = torch.full((n + 1,), -7, dtype=torch.int64, device="cuda")
     assert lib.gsmat_exclusive_scan_i32(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(ref.data_ptr()), n, st) == 0
     assert lib.gsmat_exclusive_scan_i32_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
                                                 st) == 0
-    torch.cuda.synchronize()
+    stream.synchronize()
     return ref.cpu().numpy(), out.cpu().numpy()
 
 
@@ -52,6 +53,26 @@ def test_noalloc_scan_matches_regular_scan_on_consecutive_calls(env):
         ref, out = _scan_both(gs, torch, x)
         assert np.array_equal(ref, out), n
         assert out[-1] == int(x.sum().item())
+
+
+def test_noalloc_scan_of_nothing_writes_a_zero_total(env):
+    gs, torch = env
+    x = torch.zeros(0, dtype=torch.int32, device="cuda")
+    ref, out = _scan_both(gs, torch, x)
+    assert ref.tolist() == out.tolist() == [0]
+
+
+def test_noalloc_scan_on_a_side_stream(env):
+    """Work ordered on a stream other than the current one: the clearing
+    memsets and the kernel follow that stream's order."""
+    gs, torch = env
+    rng = np.random.default_rng(6)
+    side = torch.cuda.Stream()
+    for n in (1_000_003, 40_000):
+        x = torch.from_numpy(rng.integers(0, 1 << 16, size=n).astype(np.int32)).cuda()
+        side.wait_stream(torch.cuda.current_stream())
+        ref, out = _scan_both(gs, torch, x, stream=side)
+        assert np.array_equal(ref, out), n
 
 
 def test_noalloc_scan_at_its_maximum_size(env):
