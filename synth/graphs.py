@@ -26,6 +26,7 @@ Configurations (graph seed = 1807 + k):
 from __future__ import annotations
 
 import dataclasses
+import os
 
 import numpy as np
 
@@ -185,6 +186,25 @@ def _chung_lu(cfg: GraphConfig, rng: np.random.Generator) -> np.ndarray:
 
 _CACHE: dict = {}
 
+# Graphs of at least this many triples are also kept on disk (they take
+# minutes to generate, and the tests and the benchmark need the same one in
+# separate processes).  GSMAT_SYNTH_CACHE names the folder ("0" turns the
+# disk cache off); the file name carries a digest of this module's source,
+# so a changed generator never reads an old file.
+_DISK_MIN_TRIPLES = 100_000_000
+
+
+def _disk_path(cfg: GraphConfig, seed: int):
+    import hashlib
+    import tempfile
+
+    where = os.environ.get("GSMAT_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "gsmat_synth"))
+    if where == "0" or cfg.n_triples < _DISK_MIN_TRIPLES:
+        return None
+    with open(__file__, "rb") as f:
+        digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    return os.path.join(where, f"{cfg.name}_{seed}_{cfg.n_triples}_{digest}.npy")
+
 
 def make_graph(cfg: GraphConfig | str, seed: int | None = None, cache: bool = True) -> np.ndarray:
     """Return an (n_triples, 3) int32 array of distinct (s, p, o) triples."""
@@ -194,13 +214,32 @@ def make_graph(cfg: GraphConfig | str, seed: int | None = None, cache: bool = Tr
     key = (cfg, seed)
     if cache and key in _CACHE:
         return _CACHE[key]
-    rng = np.random.Generator(np.random.PCG64(seed))
-    if cfg.model == "zipf_subjects":
-        g = _tiny(cfg, rng)
-    elif cfg.model == "chung_lu":
-        g = _chung_lu(cfg, rng)
-    else:
-        raise ValueError(cfg.model)
+    path = _disk_path(cfg, seed) if cache else None
+    g = None
+    if path and os.path.exists(path):
+        try:
+            g = np.load(path)
+            if g.shape != (cfg.n_triples, 3) or g.dtype != np.int32:
+                g = None
+        except (OSError, ValueError):
+            g = None
+    if g is None:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        if cfg.model == "zipf_subjects":
+            g = _tiny(cfg, rng)
+        elif cfg.model == "chung_lu":
+            g = _chung_lu(cfg, rng)
+        else:
+            raise ValueError(cfg.model)
+        if path:
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                tmp = f"{path}.{os.getpid()}.tmp"
+                with open(tmp, "wb") as f:
+                    np.save(f, g)
+                os.replace(tmp, path)
+            except OSError:
+                pass  # no room or no permission: keep going without the disk copy
     g.setflags(write=False)
     if cache:
         _CACHE[key] = g
