@@ -385,6 +385,11 @@ GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_o
 
 GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void) { return gs::exclusive_scan_i32_noalloc_max(); }
 
+GSMAT_API int gsmat_selftest_wait_expiry(int32_t poll_limit, gsmat_stream_t stream) {
+    gs::clear_error();
+    return gs::selftest_wait_expiry(poll_limit, (cudaStream_t)stream);
+}
+
 GSMAT_API int gsmat_profile_enable(int on) { return gs::profile_enable(on); }
 
 GSMAT_API int64_t gsmat_launch_count(void) { return gs::launch_count(); }

@@ -103,9 +103,45 @@ struct KernelTimer {
     cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
     double bytes, items;
-    KernelTimer(const char *n, cudaStream_t s, double algo_bytes, double n_items);
+    bool counts;
+    // counts_call = false: a further segment of a call already counted (its
+    // time and bytes add to the family, its call count does not)
+    KernelTimer(const char *n, cudaStream_t s, double algo_bytes, double n_items, bool counts_call = true);
     void stop();
     ~KernelTimer() { if (a) stop(); }
+};
+
+// The device time of one call made of several stream segments (the host
+// waits between them): segments are timed separately and add up to one
+// call of the family, so host round trips are not counted as device time.
+struct PhaseTimer {
+    const char *name;
+    cudaStream_t st;
+    double bytes = 0, items = 0;
+    bool started = false;
+    KernelTimer *cur = nullptr;
+    PhaseTimer(const char *n, cudaStream_t s, double n_items) : name(n), st(s), items(n_items) {}
+    PhaseTimer(const PhaseTimer &) = delete;
+    PhaseTimer &operator=(const PhaseTimer &) = delete;
+    void resume() {
+        if (cur) return;
+        cur = new KernelTimer(name, st, 0.0, started ? 0.0 : items, !started);
+        started = true;
+    }
+    void pause() {
+        if (!cur) return;
+        cur->stop();
+        delete cur;
+        cur = nullptr;
+    }
+    // algorithmic bytes, attributed to the segment in progress (or the next)
+    void add_bytes(double b) { bytes += b; }
+    void finish() {
+        resume();
+        cur->bytes = bytes;
+        pause();
+    }
+    ~PhaseTimer() { pause(); }
 };
 // Resolve finished timers of the calling thread into the global counters
 // (call after the stream they were recorded on has been synchronised).
@@ -293,6 +329,7 @@ struct LookbackScratch {
     unsigned long long *status; // [n_tiles]
     unsigned int *tile_counter; // [1]
     int *error;                 // [1]; set to 1 if a bounded wait expired
+    int poll_limit;             // polls before a wait gives up (kLookbackPollLimit)
 };
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p) {
@@ -336,7 +373,7 @@ __device__ __forceinline__ int64_t tile_lookback(const LookbackScratch &ls, int 
                     w = (j >= 0) ? ld_volatile_u64(&ls.status[j]) : (unsigned long long)(kTilePrefix << 62);
                     const bool ready = (w >> 62) != kTileInvalid;
                     if (__all_sync(0xffffffffu, ready)) break;
-                    if (++polls > kLookbackPollLimit) {
+                    if (++polls > ls.poll_limit) {
                         failed = true;
                         break;
                     }
@@ -378,6 +415,7 @@ struct LookbackBuf {
         view.status = buf.as<unsigned long long>();
         view.tile_counter = reinterpret_cast<unsigned int *>(buf.as<char>() + words * 8);
         view.error = err_word ? err_word : reinterpret_cast<int *>(buf.as<char>() + words * 8 + 4);
+        view.poll_limit = kLookbackPollLimit;
         return GSMAT_OK;
     }
 };
@@ -397,6 +435,10 @@ int radix_sort_u64_wide(uint64_t *keys, uint64_t *vals, int64_t n, int begin_bit
 // Exclusive scan of int32 counts into int64[n+1]; *err_word (device int) is
 // set if a bounded wait expired (may be null).
 int exclusive_scan_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t st, int *err_word);
+// The scan kernel over four tiles with tile 0 never handed out, so that the
+// other tiles' look-back waits run out after poll_limit polls; returns
+// GSMAT_ERR_DEVICE_CHECK when they did (the designed outcome).
+int selftest_wait_expiry(int poll_limit, cudaStream_t st);
 
 // exclusive_scan_i32 with its scratch in a static device array (no
 // allocation); n at most exclusive_scan_i32_noalloc_max().

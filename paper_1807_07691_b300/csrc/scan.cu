@@ -163,8 +163,45 @@ int exclusive_scan_i32_noalloc(const int32_t *in, int64_t *out, int64_t n, cudaS
     view.status = scratch;
     view.tile_counter = reinterpret_cast<unsigned int *>(scratch + kNoAllocMaxTiles);
     view.error = reinterpret_cast<int *>(scratch + kNoAllocMaxTiles + 1);
+    view.poll_limit = kLookbackPollLimit;
     scan_kernel<int32_t, int64_t, true><<<(unsigned)ntiles, kScanBlock, 0, st>>>(in, out, n, view);
     GS_LAUNCH_CHECK();
+    return GSMAT_OK;
+}
+
+namespace {
+__global__ void set_word_kernel(unsigned int *p, unsigned int v) { *p = v; }
+}  // namespace
+
+int selftest_wait_expiry(int poll_limit, cudaStream_t st) {
+    if (poll_limit < 1 || poll_limit > kLookbackPollLimit) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "poll limit %d outside [1, %d]", poll_limit, kLookbackPollLimit);
+    }
+    constexpr int64_t kTiles = 4;
+    const int64_t n = kTiles * kScanTile;
+    DevBuf in, out, err;
+    GS_TRY(in.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(out.alloc(sizeof(int64_t) * (size_t)(n + 1), st));
+    GS_TRY(err.alloc(sizeof(int64_t), st));  // an aligned word for read_words
+    GS_CUDA(cudaMemsetAsync(in.p, 0, sizeof(int32_t) * (size_t)n, st));
+    GS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int64_t), st));
+    LookbackBuf lb;
+    GS_TRY(lb.make(kTiles, st, err.as<int>()));
+    lb.view.poll_limit = poll_limit;
+    // The tile counter starts at 1: the kTiles - 1 CTAs take tiles 1..3 (all
+    // inside the input), and tile 0's descriptor, which every look-back
+    // window reaches, is never written.
+    set_word_kernel<<<1, 1, 0, st>>>(lb.view.tile_counter, 1u);
+    GS_LAUNCH_CHECK();
+    scan_kernel<int32_t, int64_t, true><<<(unsigned)(kTiles - 1), kScanBlock, 0, st>>>(in.as<int32_t>(),
+                                                                                      out.as<int64_t>(), n, lb.view);
+    GS_LAUNCH_CHECK();
+    int64_t *h = pinned_scratch(4);
+    if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    GS_TRY(read_words(err.p, h, 1, st));
+    if ((int)h[0]) {
+        return set_error(GSMAT_ERR_DEVICE_CHECK, "bounded wait expired (self-test: tile 0 never published)");
+    }
     return GSMAT_OK;
 }
 

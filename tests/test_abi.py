@@ -174,3 +174,12 @@ def test_primitives_refuse_host_and_mismatched_tensors(gs):
         gsmat._require(k64, (torch.int64,), 0, "keys")  # host tensor
     with pytest.raises(ValueError):
         gsmat._require(k64[::2], (torch.int64,), 0, "keys")
+
+
+def test_wait_expiry_selftest_rejects_bad_poll_limits(gs):
+    """Argument checks of the bounded-wait self-test happen on the host,
+    before any device work."""
+    lib = gs.lib()
+    for bad in (0, -1, (1 << 22) + 1):
+        assert lib.gsmat_selftest_wait_expiry(bad, None) == 1  # GSMAT_ERR_INVALID_ARG
+        assert b"poll limit" in lib.gsmat_last_error()
