@@ -222,6 +222,7 @@ struct PendingTimer {
     const char *name;
     cudaEvent_t a, b;
     double bytes, items;
+    bool counts;  // counts as a call (false: a later segment of the same call)
 };
 static thread_local std::vector<PendingTimer> t_pending;
 static thread_local std::vector<cudaEvent_t> t_event_pool;
@@ -242,8 +243,8 @@ static cudaEvent_t get_event() {
 
 bool profile_on() { return g_prof_on.load(std::memory_order_relaxed); }
 
-KernelTimer::KernelTimer(const char *n, cudaStream_t s, double algo_bytes, double n_items)
-    : name(n), st(s), bytes(algo_bytes), items(n_items) {
+KernelTimer::KernelTimer(const char *n, cudaStream_t s, double algo_bytes, double n_items, bool counts_call)
+    : name(n), st(s), bytes(algo_bytes), items(n_items), counts(counts_call) {
     if (!g_prof_on.load(std::memory_order_relaxed)) return;
     a = get_event();
     b = get_event();
@@ -257,7 +258,7 @@ KernelTimer::KernelTimer(const char *n, cudaStream_t s, double algo_bytes, doubl
 void KernelTimer::stop() {
     if (!a) return;
     cudaEventRecord(b, st);
-    t_pending.push_back({name, a, b, bytes, items});
+    t_pending.push_back({name, a, b, bytes, items, counts});
     a = b = nullptr;
 }
 
@@ -268,7 +269,7 @@ void profile_flush() {
         float ms = 0;
         if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
             auto &g = g_prof[p.name];
-            g.launches++;
+            if (p.counts) g.launches++;
             g.ms += ms;
             g.bytes += p.bytes;
             g.items += p.items;

@@ -307,7 +307,7 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
 
 // Build one side from entries sorted by (slot, key, val).
 int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t *slot, int64_t n, int *err,
-               cudaStream_t st) {
+               cudaStream_t st, PhaseTimer &pt) {
     const int P = S->n_pred;
     DevBuf rid, roff, rslot, cnt, bases;
     GS_TRY(rid.alloc(sizeof(int32_t) * (size_t)n, st));
@@ -319,8 +319,11 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     int64_t *h = pinned_scratch(4);
     if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
     GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    pt.pause();
     GS_CUDA(cudaStreamSynchronize(st));
+    pt.resume();
     const int64_t R = h[0];
+    pt.add_bytes(8.0 * (double)R);  // Row and Rpos of the side's non-zero rows
     // exact-size auxiliary arrays, rowoff with its sentinel
     GS_TRY(S->rowid[side].alloc(sizeof(int32_t) * (size_t)R, st));
     GS_TRY(S->rowoff[side].alloc(sizeof(int32_t) * (size_t)(R + 1), st));
@@ -340,7 +343,9 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     }
     std::vector<int32_t> hb(2 * (size_t)(P + 1));
     GS_CUDA(cudaMemcpyAsync(hb.data(), bases.p, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, st));
+    pt.pause();
     GS_CUDA(cudaStreamSynchronize(st));
+    pt.resume();
     hb[P] = (int32_t)n;
     hb[(P + 1) + P] = (int32_t)R;
     S->side[side].resize(P);
@@ -372,6 +377,7 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     }
     S->n_dense[side] = 0;
     if (total > 0) {
+        pt.add_bytes(4.0 * (double)total);  // dense row pointers written
         GS_TRY(S->dense[side].alloc(sizeof(int32_t) * (size_t)total, st));
         const int64_t per = (len + kDenseChunk - 1) / kDenseChunk;
         std::vector<DensePart> parts;
@@ -417,7 +423,13 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
         GS_CUDA(cudaMemcpyAsync(d_tri_own.p, triples, sizeof(int32_t) * 3 * (size_t)n, cudaMemcpyHostToDevice, st));
         tri = d_tri_own.as<int32_t>();
     }
-    KernelTimer t_all("store_build", st, (double)n * 12.0, (double)n);
+    // Device time of the build, without the host's waits between its
+    // phases.  Algorithmic bytes: the triples read once (12 per triple),
+    // both sides' columns (4 + 4 per unique triple), every non-zero row's
+    // Row and Rpos words (8 per row and side) and the dense row pointers.
+    PhaseTimer pt("store_build", st, (double)n);
+    pt.add_bytes(12.0 * (double)n);
+    pt.resume();
     int64_t *h = pinned_scratch(8);
     if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
     // 1. ranges
@@ -428,7 +440,9 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     GS_LAUNCH_CHECK();
     std::vector<int> hr_all(kRangesWords);
     GS_CUDA(cudaMemcpyAsync(hr_all.data(), ranges.p, sizeof(int) * kRangesWords, cudaMemcpyDeviceToHost, st));
+    pt.pause();
     GS_CUDA(cudaStreamSynchronize(st));
+    pt.resume();
     const int *hr = hr_all.data();
     if (n > 0 && hr[2] < 0) return set_error(GSMAT_ERR_INVALID_ARG, "negative id in triples (min %d)", hr[2]);
     S->max_entity = n > 0 ? hr[0] : -1;
@@ -463,13 +477,17 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
         DistinctU32Op op{pcol.as<uint32_t>(), pdist.as<int32_t>()};
         GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err.as<int>()));
         GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        pt.pause();
         GS_CUDA(cudaStreamSynchronize(st));
+        pt.resume();
         const int64_t P = h[0];
         if (P <= 0 || P > INT32_MAX / 4) return set_error(GSMAT_ERR_CAPACITY, "%lld distinct predicates", (long long)P);
         S->n_pred = (int32_t)P;
         S->pred_ids.resize((size_t)P);
         GS_CUDA(cudaMemcpyAsync(S->pred_ids.data(), pdist.p, sizeof(int32_t) * (size_t)P, cudaMemcpyDeviceToHost, st));
+        pt.pause();
         GS_CUDA(cudaStreamSynchronize(st));
+        pt.resume();
     }
     {
         uint32_t cap = 16;
@@ -515,10 +533,13 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
                     s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>()};
         GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err.as<int>()));
         GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        pt.pause();
         GS_CUDA(cudaStreamSynchronize(st));
+        pt.resume();
     }
     const int64_t nu = h[0];
     S->n_unique = nu;
+    pt.add_bytes(8.0 * (double)nu);  // the two sides' entry columns
     // side 0 arrays: key = s, val = o (exact size)
     DevBuf key0, val0, slot0;
     GS_TRY(key0.alloc(sizeof(int32_t) * (size_t)nu, st));
@@ -538,8 +559,8 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
                       key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st, err.as<int>()));
     s_sorted.release(); o_sorted.release(); slot_sorted.release();
     // 5. rows, predicate bounds, dense row pointers
-    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err.as<int>(), st));
-    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err.as<int>(), st));
+    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err.as<int>(), st, pt));
+    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err.as<int>(), st, pt));
     // device copy of the per-predicate tables
     {
         const size_t P = (size_t)S->n_pred;
@@ -548,7 +569,7 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
         GS_CUDA(cudaMemcpyAsync(S->pred_side_dev.as<PredSide>() + P, S->side[1].data(), sizeof(PredSide) * P,
                                 cudaMemcpyHostToDevice, st));
     }
-    t_all.stop();
+    pt.finish();
     GS_CUDA(cudaMemcpyAsync(h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     if (*reinterpret_cast<int *>(h)) return set_error(GSMAT_ERR_DEVICE_CHECK, "store build: a bounded wait expired");
