@@ -255,6 +255,13 @@ typedef struct {
 #define GSMAT_STEP_INTERSECT 4 /* (query stats only) an expand fused with a later filter on the
                                   new variable: the new column is the intersection of two rows */
 #define GSMAT_STEP_FUSED 5     /* (query stats only) a filter executed inside an earlier INTERSECT */
+#define GSMAT_STEP_PRODUCT 6   /* (query stats only) one of the plan's last steps whose lists depend
+                                  only on the table before them (EXPAND from a variable bound before
+                                  them or from a constant, CROSS): they run as one Cartesian product
+                                  per input row, nested by variable id, so the result needs little or
+                                  no final reorder; rows[] is -1 for the ones not built (exact running
+                                  products when the steps start from the empty assignment).  Not used
+                                  with GSMAT_NO_INTERSECT or GSMAT_PLAN_ORDER. */
 
 GSMAT_API int gsmat_table_stats(const gsmat_table *table, gsmat_query_stats *stats);
 
@@ -315,6 +322,9 @@ typedef struct {
     int64_t arena_used;   /* bytes of arena the last run used */
     int32_t block;
     int32_t grid;
+    int32_t n_intersect;  /* steps of the prepared programs that run as an intersect-expand (an
+                             EXPAND fused with a later FILTER on its new variable) */
+    int32_t _pad;
 } gsmat_batch_stats_t;
 
 /* Plan a batch of n >= 1 BGPs against a store and prepare its device run.
@@ -618,6 +628,21 @@ GSMAT_API int gsmat_exclusive_scan_i32(const int32_t *d_in, int64_t *d_out, int6
 GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_out, int64_t n,
                                                gsmat_stream_t stream);
 GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void);
+
+/* Self-test of the kernels' bounded waits (failure detection without a GPU
+ * fault).  Runs the library's single-pass scan kernel -- the look-back code
+ * of a query's count, scan and compaction steps -- over four tiles of zeros
+ * with its tile counter starting at 1: tile 0 never runs, so the look-back
+ * of every other tile waits on a descriptor that nothing writes.  After
+ * poll_limit polls (1 <= poll_limit <= 2^22; each poll sleeps about 64 ns)
+ * each wait gives up, records the error word and lets its CTA finish; the
+ * call then synchronises `stream` and reads the word.
+ * Returns GSMAT_ERR_DEVICE_CHECK when the waits expired (the designed
+ * outcome; the device and the stream stay usable), GSMAT_OK if they did
+ * not (a defect), GSMAT_ERR_INVALID_ARG for a poll limit out of range.
+ * The paper has no counterpart: this checks the library's own failure
+ * handling. */
+GSMAT_API int gsmat_selftest_wait_expiry(int32_t poll_limit, gsmat_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Kernel timing (CUDA events on the launching stream)                       */

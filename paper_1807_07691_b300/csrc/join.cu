@@ -151,6 +151,157 @@ __global__ void __launch_bounds__(kExBlock) expand_kernel(ExpandArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// product of independent expansions
+
+constexpr int kPcBlock = 256;
+constexpr int kPcItems = 4;
+constexpr int kPcTile = kPcBlock * kPcItems;
+constexpr uint64_t kProdSaturate = uint64_t(1) << 32;  // already past the row limit of a table
+
+__device__ __forceinline__ uint64_t sat_mul(uint64_t c, uint64_t l) {
+    return (l != 0 && c > kProdSaturate / l) ? kProdSaturate : c * l;
+}
+
+// Count + scan, laid out like count_scan_kernel (warp-striped items, warp
+// scans, the CTA's warp totals, decoupled look-back across tiles).
+__global__ void __launch_bounds__(kPcBlock) product_count_scan_kernel(StoreView sv, ProdSpec spec, Cols in, int64_t n,
+                                                                      int64_t *__restrict__ off,
+                                                                      int32_t *__restrict__ first,
+                                                                      int32_t *__restrict__ len,
+                                                                      int64_t *__restrict__ d_total, LookbackScratch ls) {
+    __shared__ int tile_sm;
+    __shared__ int64_t scan_sm[kPcBlock / 32 + 1];
+    __shared__ int64_t prefix_sm;
+    const int tile = acquire_tile_id(ls, &tile_sm);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i0 = (int64_t)tile * kPcTile + (int64_t)warp * (32 * kPcItems) + lane;
+    uint64_t cnt[kPcItems];
+    bool ok[kPcItems];
+#pragma unroll
+    for (int j = 0; j < kPcItems; ++j) {
+        ok[j] = i0 + 32 * j < n;
+        cnt[j] = ok[j] ? 1 : 0;
+    }
+    for (int fi = 0; fi < spec.nf; ++fi) {
+        const ProdFactor &f = spec.f[fi];
+        if (f.kind != kProdRow) {
+#pragma unroll
+            for (int j = 0; j < kPcItems; ++j) cnt[j] = sat_mul(cnt[j], f.len);
+            continue;
+        }
+        int32_t xv[kPcItems];
+#pragma unroll
+        for (int j = 0; j < kPcItems; ++j) xv[j] = ok[j] ? __ldg(in.c[f.xcol] + i0 + 32 * j) : 0;
+        int2 rr[kPcItems];
+        row_ranges<kPcItems>(sv.side[f.side], f.ps, xv, ok, rr);
+#pragma unroll
+        for (int j = 0; j < kPcItems; ++j) {
+            const uint64_t l = (uint64_t)(rr[j].y - rr[j].x);
+            cnt[j] = sat_mul(cnt[j], l);
+            if (ok[j]) {
+                first[(int64_t)f.slot * n + i0 + 32 * j] = rr[j].x;
+                len[(int64_t)f.slot * n + i0 + 32 * j] = rr[j].y - rr[j].x;
+            }
+        }
+    }
+    int64_t ex[kPcItems];
+    int64_t wrun = 0;
+#pragma unroll
+    for (int j = 0; j < kPcItems; ++j) {
+        const int64_t c = (int64_t)cnt[j];
+        const int64_t inc = warp_inclusive_sum(c);
+        ex[j] = wrun + inc - c;
+        wrun += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    int64_t tot;
+    const int64_t wex = block_exclusive_sum<kPcBlock>(lane == 0 ? wrun : 0, scan_sm, &tot);
+    const int64_t wbase = __shfl_sync(0xffffffffu, wex, 0);
+    const int64_t pre = tile_lookback(ls, tile, tot, &prefix_sm);
+#pragma unroll
+    for (int j = 0; j < kPcItems; ++j) {
+        if (ok[j]) off[i0 + 32 * j] = pre + wbase + ex[j];
+    }
+    if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) {
+        off[n] = pre + tot;
+        *d_total = pre + tot;
+    }
+}
+
+struct ProductArgs {
+    StoreView sv;
+    ProdSpec spec;
+    Cols in;
+    int k;
+    int64_t n_in;
+    const int64_t *off;
+    const int32_t *first;
+    const int32_t *len;
+    int64_t total;
+    const int64_t *cuts;
+    OutCols out;
+};
+
+// Slots are partitioned as in expand_kernel (merge path of row ends and
+// slots, kExItems per CTA, the CTA's offsets staged in shared memory).
+__global__ void __launch_bounds__(kExBlock) product_kernel(ProductArgs a) {
+    __shared__ int64_t soff[kExItems + 2];
+    const int64_t d0 = (int64_t)blockIdx.x * kExItems;
+    const int64_t d1 = d0 + kExItems < a.n_in + a.total ? d0 + kExItems : a.n_in + a.total;
+    const int64_t r0 = __ldg(a.cuts + blockIdx.x);
+    const int64_t r1 = __ldg(a.cuts + blockIdx.x + 1);
+    const int64_t j0 = d0 - r0, j1 = d1 - r1;
+    if (j1 <= j0) return;
+    const int64_t r_last = r1 < a.n_in ? r1 : a.n_in - 1;
+    const int nr = (int)(r_last - r0 + 1);
+    for (int i = threadIdx.x; i <= nr; i += kExBlock) soff[i] = __ldg(a.off + r0 + i);
+    __syncthreads();
+    const int nf = a.spec.nf;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += kExBlock) {
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (soff[mid] <= j) lo = mid; else hi = mid - 1;
+        }
+        const int64_t r = r0 + lo;
+        for (int c = 0; c < a.k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + r);
+        uint32_t q = (uint32_t)(j - soff[lo]);  // < N_r <= total < 2^32
+        for (int fi = nf - 1; fi >= 0; --fi) {
+            const ProdFactor &f = a.spec.f[fi];
+            if (f.kind == kProdRow) {
+                const int64_t at = (int64_t)f.slot * a.n_in + r;
+                const uint32_t l = (uint32_t)__ldg(a.len + at);
+                const uint32_t qq = q / l;
+                const uint32_t idx = q - qq * l;
+                q = qq;
+                a.out.c[f.out0][j] = __ldg(a.sv.side[f.side].val + __ldg(a.first + at) + idx);
+            } else {
+                const uint32_t qq = fastdiv_quot(q, f.div);
+                const uint32_t idx = q - qq * f.len;
+                q = qq;
+                a.out.c[f.out0][j] = __ldg(f.a + idx);
+                if (f.kind == kProdPairs) a.out.c[f.out0 + 1][j] = __ldg(f.b + idx);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) product_fixed_kernel(ProdSpec spec, uint32_t total, OutCols out) {
+    const int nf = spec.nf;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < (int64_t)total;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q = (uint32_t)j;
+        for (int fi = nf - 1; fi >= 0; --fi) {
+            const ProdFactor &f = spec.f[fi];
+            const uint32_t qq = fastdiv_quot(q, f.div);
+            const uint32_t idx = q - qq * f.len;
+            q = qq;
+            out.c[f.out0][j] = __ldg(f.a + idx);
+            if (f.kind == kProdPairs) out.c[f.out0 + 1][j] = __ldg(f.b + idx);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // filter (membership test of (s, o) in the predicate) + compaction
 
 // Rows this short are searched directly, without looking up the other side.
@@ -199,44 +350,12 @@ struct IsectSrc {
 // count (in every lane).  k parent columns are copied for each match.
 __device__ __forceinline__ int warp_intersect_row(const IsectSrc &s, int64_t i, int64_t out_base, const Cols &in,
                                                   int k, OutCols *out) {
-    const int lane = threadIdx.x & 31;
-    const int2 ra = row_range(s.sa, s.pa, s.a.at(i));
-    const int2 rb = row_range(s.sb, s.pb, s.b.at(i));
-    const int la = ra.y - ra.x, lb = rb.y - rb.x;
-    if (la <= 0 || lb <= 0) return 0;
-    const int32_t *S = la <= lb ? s.sa.val + ra.x : s.sb.val + rb.x;
-    const int32_t *L = la <= lb ? s.sb.val + rb.x : s.sa.val + ra.x;
-    const int ls = la <= lb ? la : lb, ll = la <= lb ? lb : la;
-    int count = 0;
-    int lo_all = 0;  // no element of L before this position can match any later element of S
-    for (int base = 0; base < ls; base += 32) {
-        const int idx = base + lane;
-        int32_t v = 0;
-        bool found = false;
-        int pos = ll;
-        if (idx < ls) {
-            v = __ldg(S + idx);
-            int lo = lo_all, hi = ll;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(L + mid) < v) lo = mid + 1; else hi = mid;
-            }
-            pos = lo;
-            found = lo < ll && __ldg(L + lo) == v;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, found);
-        if (out && found) {
-            const int64_t j = out_base + count + __popc(m & ((1u << lane) - 1u));
-            for (int c = 0; c < k; ++c) out->c[c][j] = __ldg(in.c[c] + i);
-            out->c[k][j] = v;
-        }
-        count += __popc(m);
-        // the chunk's last element bounds the next chunk's searches from below
-        const int last = min(31, ls - 1 - base);
-        lo_all = __shfl_sync(0xffffffffu, pos, last);
-        if (lo_all >= ll) break;
-    }
-    return count;
+    if (!out) return warp_intersect(s.sa, s.pa, s.a.at(i), s.sb, s.pb, s.b.at(i), [](int, int32_t) {});
+    return warp_intersect(s.sa, s.pa, s.a.at(i), s.sb, s.pb, s.b.at(i), [&](int r, int32_t v) {
+        const int64_t j = out_base + r;
+        for (int c = 0; c < k; ++c) out->c[c][j] = __ldg(in.c[c] + i);
+        out->c[k][j] = v;
+    });
 }
 
 __global__ void __launch_bounds__(256) isect_count_kernel(IsectSrc s, int64_t n, int32_t *__restrict__ counts) {
@@ -356,6 +475,81 @@ int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t 
                                                                                   cuts.as<int64_t>());
     GS_LAUNCH_CHECK();
     expand_kernel<<<(unsigned)n_parts, kExBlock, 0, st>>>(a);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_product_count_scan(const StoreView &sv, const ProdSpec &spec, const Cols &in, int64_t n, int64_t *off,
+                              int32_t *first, int32_t *len, int64_t *d_total, int *err, cudaStream_t st) {
+    if (n <= 0) {
+        GS_CUDA(cudaMemsetAsync(off, 0, sizeof(int64_t), st));
+        GS_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int64_t), st));
+        return GSMAT_OK;
+    }
+    const int64_t ntiles = (n + kPcTile - 1) / kPcTile;
+    if (ntiles > INT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "count over %lld rows", (long long)n);
+    LookbackBuf lb;
+    GS_TRY(lb.make(ntiles, st, err));
+    // algorithmic bytes: per row factor the bound value, a row lookup and
+    // the first entry and length out; the offset out
+    KernelTimer t("product_count", st, (double)n * (8.0 + spec.nrow * (4.0 + 8.0 + 8.0)), (double)n);
+    product_count_scan_kernel<<<(unsigned)ntiles, kPcBlock, 0, st>>>(sv, spec, in, n, off, first, len, d_total,
+                                                                     lb.view);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+static int product_out_cols(const ProdSpec &spec) {
+    int c = 0;
+    for (int i = 0; i < spec.nf; ++i) c += spec.f[i].kind == kProdPairs ? 2 : 1;
+    return c;
+}
+
+int launch_product(const StoreView &sv, const ProdSpec &spec, const Cols &in, int k, int64_t n_in, const int64_t *off,
+                   const int32_t *first, const int32_t *len, int64_t total, OutCols out, cudaStream_t st) {
+    if (total <= 0 || n_in <= 0) return GSMAT_OK;
+    if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+    const int64_t n_parts = (n_in + total + kExItems - 1) / kExItems;
+    DevBuf cuts;
+    GS_TRY(cuts.alloc(sizeof(int64_t) * (size_t)(n_parts + 1), st));
+    ProductArgs a;
+    a.sv = sv;
+    a.spec = spec;
+    a.in = in;
+    a.k = k;
+    a.n_in = n_in;
+    a.off = off;
+    a.first = first;
+    a.len = len;
+    a.total = total;
+    a.cuts = cuts.as<int64_t>();
+    a.out = out;
+    // algorithmic bytes: per input row its k columns, its offset and each
+    // row factor's range; per output row the innermost factor's value read
+    // and k + (factor columns) values written
+    const int fc = product_out_cols(spec);
+    KernelTimer t("product", st, (double)n_in * (4.0 * k + 8.0 + 8.0 * spec.nrow) + (double)total * (4.0 + 4.0 * (k + fc)),
+                  (double)total);
+    expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts,
+                                                                                  cuts.as<int64_t>());
+    GS_LAUNCH_CHECK();
+    product_kernel<<<(unsigned)n_parts, kExBlock, 0, st>>>(a);
+    GS_LAUNCH_CHECK();
+    t.stop();
+    return GSMAT_OK;
+}
+
+int launch_product_fixed(const ProdSpec &spec, int64_t total, OutCols out, cudaStream_t st) {
+    if (total <= 0) return GSMAT_OK;
+    if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+    const int fc = product_out_cols(spec);
+    KernelTimer t("product", st, (double)total * (4.0 + 4.0 * fc), (double)total);
+    int64_t g = (total + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    if (g > cap) g = cap;
+    product_fixed_kernel<<<(unsigned)g, 256, 0, st>>>(spec, (uint32_t)total, out);
     GS_LAUNCH_CHECK();
     t.stop();
     return GSMAT_OK;

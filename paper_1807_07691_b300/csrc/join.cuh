@@ -22,6 +22,53 @@ struct ValueSrc {
     __device__ __forceinline__ int32_t at(int64_t i) const { return col ? col[i] : constant; }
 };
 
+// Intersection of two sorted entry lists by one warp (all 32 lanes call it
+// with the same arguments): the row of a_val on predicate side (sa, pa) and
+// the row of b_val on (sb, pb).  The warp walks the shorter list in chunks of
+// 32; each lane binary-searches its element in the part of the longer list
+// not yet passed, and ballot / popc rank the matches.  emit(r, v) is called
+// by the lane holding the r-th match (ascending) v; returns the count in
+// every lane.  A new variable bound by two patterns of Alg. 3 takes exactly
+// these values, in the order an expand followed by a filter gives.
+template <class Emit>
+__device__ __forceinline__ int warp_intersect(const SideView &sa, const PredSide &pa, int32_t a_val,
+                                              const SideView &sb, const PredSide &pb, int32_t b_val, Emit emit) {
+    const int lane = threadIdx.x & 31;
+    const int2 ra = row_range(sa, pa, a_val);
+    const int2 rb = row_range(sb, pb, b_val);
+    const int la = ra.y - ra.x, lb = rb.y - rb.x;
+    if (la <= 0 || lb <= 0) return 0;
+    const int32_t *S = la <= lb ? sa.val + ra.x : sb.val + rb.x;
+    const int32_t *L = la <= lb ? sb.val + rb.x : sa.val + ra.x;
+    const int ls = la <= lb ? la : lb, ll = la <= lb ? lb : la;
+    int count = 0;
+    int lo_all = 0;  // no element of L before this position can match any later element of S
+    for (int base = 0; base < ls; base += 32) {
+        const int idx = base + lane;
+        int32_t v = 0;
+        bool found = false;
+        int pos = ll;
+        if (idx < ls) {
+            v = __ldg(S + idx);
+            int lo = lo_all, hi = ll;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(L + mid) < v) lo = mid + 1; else hi = mid;
+            }
+            pos = lo;
+            found = lo < ll && __ldg(L + lo) == v;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, found);
+        if (found) emit(count + __popc(m & ((1u << lane) - 1u)), v);
+        count += __popc(m);
+        // the chunk's last element bounds the next chunk's searches from below
+        const int last = min(31, ls - 1 - base);
+        lo_all = __shfl_sync(0xffffffffu, pos, last);
+        if (lo_all >= ll) break;
+    }
+    return count;
+}
+
 // Count + exclusive scan (Alg. 4): for every input row i, N_i = size of the
 // row of x_i on the given side of the predicate, first_i = its first entry;
 // off[i] = sum of N_j for j < i, off[n] = total; *d_total = total.
@@ -54,6 +101,82 @@ int launch_isect_write(const StoreView &sv, int side_a, const PredSide &pa, Valu
 // the relation has r_cols (1 or 2) columns of length m.
 int launch_cross(const Cols &in, int k, int64_t n_in, const Cols &rel, int r_cols, int64_t m, OutCols out,
                  cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Product of independent expansions.  When the last steps of a plan each
+// bind one new variable from a list that depends only on the table before
+// them -- the row of a bound column's value (EXPAND from a variable), a
+// constant's row (EXPAND from a constant) or a whole matrix (CROSS, two new
+// variables) -- every input row r joins with the Cartesian product of its
+// lists L_1(r) x ... x L_F(r) (Alg. 3 applied step by step gives exactly
+// these rows).  The product is written in one pass, nested in a chosen
+// factor order (outermost first), each list ascending, so that output rows
+// ascend in (input columns, factor columns in nesting order).
+
+// Division by a divisor that is fixed for many dividends: the multiply and
+// shift of Granlund and Montgomery ("Division by invariant integers using
+// multiplication", PLDI 1994), round-up form: for 1 <= d < 2^32 let
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1 (< 2^32); then for
+// every 32-bit n, n / d = (mulhi(n, m) + n) >> l, the sum taken in 64 bits.
+struct FastDiv {
+    uint32_t d;
+    uint32_t m;
+    uint32_t l;
+};
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while (l < 32 && (uint64_t(1) << l) < (uint64_t)d) ++l;
+    f.l = l;
+    f.m = d == 0 ? 0u : (uint32_t)((((uint64_t(1) << l) - (uint64_t)d) << 32) / (uint64_t)d + 1);
+    return f;
+}
+__host__ __device__ inline uint32_t fastdiv_quot(uint32_t n, const FastDiv &f) {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(n, f.m);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)n * (uint64_t)f.m) >> 32);
+#endif
+    return (uint32_t)(((uint64_t)t + (uint64_t)n) >> f.l);
+}
+
+constexpr int kMaxProdFactors = 16;
+enum { kProdRow = 0, kProdList = 1, kProdPairs = 2 };
+
+struct ProdFactor {
+    int kind;          // kProdRow, kProdList or kProdPairs
+    int side;          // kProdRow: store side whose row is taken
+    int xcol;          // kProdRow: input column holding the row's id
+    int slot;          // kProdRow: index among the row factors (first / len arrays)
+    PredSide ps;       // kProdRow: the predicate side
+    const int32_t *a;  // kProdList: the values; kProdPairs: first column
+    const int32_t *b;  // kProdPairs: second column
+    uint32_t len;      // kProdList / kProdPairs: length
+    FastDiv div;       // kProdList / kProdPairs: divisor len
+    int out0;          // output column of the factor's (first) value
+};
+struct ProdSpec {
+    int nf;    // factors, outermost first
+    int nrow;  // factors of kind kProdRow (slots 0..nrow-1)
+    ProdFactor f[kMaxProdFactors];
+};
+
+// Count + scan: N_r = product over the factors of |L_i(r)| (saturating at
+// 2^32; a total past 2^32 - 1 rows is refused by the caller);
+// off[r] = exclusive prefix, off[n] = *d_total = total; for row factor with
+// slot s: first[s * n + r] / len[s * n + r] = its row's entry range.
+int launch_product_count_scan(const StoreView &sv, const ProdSpec &spec, const Cols &in, int64_t n, int64_t *off,
+                              int32_t *first, int32_t *len, int64_t *d_total, int *err, cudaStream_t st);
+// Write: output row j of [0, total) belongs to input row r (off[r] <= j <
+// off[r+1]); its k input columns are copied and q = j - off[r] is split in
+// mixed radix over the factors (innermost factor fastest) to pick each
+// factor's entry.
+int launch_product(const StoreView &sv, const ProdSpec &spec, const Cols &in, int k, int64_t n_in, const int64_t *off,
+                   const int32_t *first, const int32_t *len, int64_t total, OutCols out, cudaStream_t st);
+// The product of fixed lists only (no input columns, one input row):
+// total = product of the factors' lengths (< 2^32).
+int launch_product_fixed(const ProdSpec &spec, int64_t total, OutCols out, cudaStream_t st);
 
 // Entries of one predicate (side 0) with key == val, as one column.
 int launch_diag(const StoreView &sv, const PredSide &ps0, int32_t *out, int64_t *d_count, int *err, cudaStream_t st);

@@ -250,11 +250,46 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         }
     }
 
+    // Product of independent expansions: the longest suffix of the plan
+    // whose steps each take their list from the table before the suffix or
+    // from the store alone (EXPAND from a variable bound before it, EXPAND
+    // from a constant, CROSS) runs as one product step (launch_product),
+    // nested by variable id so that the result needs little or no final
+    // reorder.  Off for GSMAT_NO_INTERSECT (one pattern per step) and for
+    // GSMAT_PLAN_ORDER (the paper's binding order).
+    int tail = n_pats;
+    if (!(flags & (GSMAT_NO_INTERSECT | GSMAT_PLAN_ORDER)) && !absent) {
+        std::vector<uint64_t> before(n_pats + 1, 0);  // variables bound by the steps before s
+        for (int s = 0; s < n_pats; ++s) {
+            const gsmat_pattern &p = pats[qs.order[s]];
+            before[s + 1] = before[s] | (p.s_var ? uint64_t(1) << p.s : 0) | (p.o_var ? uint64_t(1) << p.o : 0);
+        }
+        auto independent = [&](int s, uint64_t pre) {
+            if (fused[s] || partner[s] >= 0) return false;
+            const gsmat_pattern &p = pats[qs.order[s]];
+            switch (qs.kind[s]) {
+                case GSMAT_STEP_EXPAND_S: return !p.s_var || ((pre >> p.s) & 1) != 0;
+                case GSMAT_STEP_EXPAND_O: return !p.o_var || ((pre >> p.o) & 1) != 0;
+                case GSMAT_STEP_CROSS: return p.s_var && p.o_var && p.s != p.o;
+                default: return false;
+            }
+        };
+        for (int t = n_pats - 1; t >= 0; --t) {
+            bool ok = true;
+            for (int s = t; s < n_pats && ok; ++s) ok = independent(s, before[t]);
+            if (!ok) break;
+            tail = t;
+        }
+        if (n_shards > 1 && tail == 0) tail = 1;  // shards split the first step's relation
+        if (n_pats - tail > kMaxProdFactors) tail = n_pats - kMaxProdFactors;
+        if (n_pats - tail < 2) tail = n_pats;
+    }
+
     Tbl cur;
     cur.rows = absent ? 0 : 1;  // one empty assignment
     cur.ncols = 0;
     const bool count_only = (flags & GSMAT_COUNT_ONLY) != 0;
-    for (int step = 0; step < n_pats && cur.rows > 0; ++step) {
+    for (int step = 0; step < tail && cur.rows > 0; ++step) {
         const gsmat_pattern &p = pats[qs.order[step]];
         const int kind = qs.kind[step];
         const PredSide &ps0 = S->side[0][slot[qs.order[step]]];
@@ -433,6 +468,124 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
             cur.rows = hi - lo;
         }
         qs.rows[step] = cur.rows;
+    }
+
+    if (tail < n_pats && cur.rows > 0) {
+        struct Fac {
+            int32_t v0, v1;  // the factor's variables (v1 = -1 for one)
+            ProdFactor f;
+        };
+        std::vector<Fac> facs;
+        for (int s = tail; s < n_pats; ++s) {
+            const gsmat_pattern &p = pats[qs.order[s]];
+            const int sl = slot[qs.order[s]];
+            Fac x;
+            memset(&x, 0, sizeof(x));
+            x.v1 = -1;
+            if (qs.kind[s] == GSMAT_STEP_CROSS) {
+                // M_p from the side that puts the lower variable first, as a CROSS step does
+                const int sd = p.o < p.s ? 1 : 0;
+                const PredSide &pss = S->side[sd][sl];
+                x.f.kind = kProdPairs;
+                x.f.a = S->view.side[sd].key + pss.ent_base;
+                x.f.b = S->view.side[sd].val + pss.ent_base;
+                x.f.len = (uint32_t)pss.nnz;
+                x.v0 = sd == 0 ? p.s : p.o;
+                x.v1 = sd == 0 ? p.o : p.s;
+            } else {
+                const int side = qs.kind[s] == GSMAT_STEP_EXPAND_S ? 0 : 1;
+                x.v0 = side == 0 ? p.o : p.s;
+                if (side == 0 ? p.s_var : p.o_var) {
+                    x.f.kind = kProdRow;
+                    x.f.side = side;
+                    x.f.xcol = cur.col_of(side == 0 ? p.s : p.o);
+                    x.f.ps = S->side[side][sl];
+                } else {
+                    const int r = side == 0 ? req_s[qs.order[s]] : req_o[qs.order[s]];
+                    x.f.kind = kProdList;
+                    x.f.a = S->view.side[side].val + rng[2 * r];
+                    x.f.len = (uint32_t)row_len(r);
+                }
+            }
+            facs.push_back(x);
+        }
+        // outermost factor = smallest variable: inside every input row the
+        // product's rows then ascend in variable order
+        std::stable_sort(facs.begin(), facs.end(), [](const Fac &a, const Fac &b) { return a.v0 < b.v0; });
+        ProdSpec spec;
+        memset(&spec, 0, sizeof(spec));
+        spec.nf = (int)facs.size();
+        Tbl nxt;
+        int col = cur.ncols;
+        for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+        uint64_t fixed = 1;  // product of the fixed factors' lengths, saturating
+        const uint64_t kSat = uint64_t(1) << 40;
+        for (int i = 0; i < spec.nf; ++i) {
+            ProdFactor &f = spec.f[i];
+            f = facs[i].f;
+            f.out0 = col;
+            nxt.vars[col++] = facs[i].v0;
+            if (f.kind == kProdPairs) nxt.vars[col++] = facs[i].v1;
+            if (f.kind == kProdRow) {
+                f.slot = spec.nrow++;
+            } else {
+                f.div = make_fastdiv(f.len);
+                fixed = (f.len != 0 && fixed > kSat / f.len) ? kSat : fixed * f.len;
+            }
+        }
+        int64_t total = 0;
+        const bool unit = cur.rows == 1 && cur.ncols == 0;
+        if (unit) {
+            // fixed lists only (a row factor needs a column of the table)
+            total = (int64_t)fixed;
+            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+            if (!count_only && total > 0) {
+                OutCols oc;
+                GS_TRY(alloc_cols(nxt, col, total, st, &oc));
+                GS_TRY(launch_product_fixed(spec, total, oc, st));
+            }
+            // the plan-order intermediates are known exactly: running products
+            uint64_t run_rows = 1;
+            for (int s = tail; s < n_pats; ++s) {
+                const gsmat_pattern &p = pats[qs.order[s]];
+                const int sl = slot[qs.order[s]];
+                uint64_t l;
+                if (qs.kind[s] == GSMAT_STEP_CROSS) {
+                    l = (uint64_t)S->side[p.o < p.s ? 1 : 0][sl].nnz;
+                } else {
+                    const bool sd0 = qs.kind[s] == GSMAT_STEP_EXPAND_S;
+                    l = (uint64_t)row_len(sd0 ? req_s[qs.order[s]] : req_o[qs.order[s]]);
+                }
+                run_rows = (l != 0 && run_rows > kSat / l) ? kSat : run_rows * l;
+                qs.rows[s] = (int64_t)run_rows;
+                qs.kind[s] = GSMAT_STEP_PRODUCT;
+            }
+        } else {
+            DevBuf off, fr, ln;
+            GS_TRY(off.alloc(sizeof(int64_t) * (size_t)(cur.rows + 1), st));
+            if (spec.nrow > 0) {
+                GS_TRY(fr.alloc(sizeof(int32_t) * (size_t)spec.nrow * (size_t)cur.rows, st));
+                GS_TRY(ln.alloc(sizeof(int32_t) * (size_t)spec.nrow * (size_t)cur.rows, st));
+            }
+            GS_TRY(launch_product_count_scan(S->view, spec, cur.cols(), cur.rows, off.as<int64_t>(), fr.as<int32_t>(),
+                                             ln.as<int32_t>(), cx.d_count(), cx.d_err(), st));
+            GS_TRY(cx.read_count(&total));
+            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+            if (!count_only && total > 0) {
+                OutCols oc;
+                GS_TRY(alloc_cols(nxt, col, total, st, &oc));
+                GS_TRY(launch_product(S->view, spec, cur.cols(), cur.ncols, cur.rows, off.as<int64_t>(),
+                                      fr.as<int32_t>(), ln.as<int32_t>(), total, oc, st));
+            }
+            // intermediates of the fused steps are not built
+            for (int s = tail; s < n_pats; ++s) {
+                qs.rows[s] = s == n_pats - 1 ? total : -1;
+                qs.kind[s] = GSMAT_STEP_PRODUCT;
+            }
+        }
+        nxt.rows = total;
+        nxt.ncols = col;
+        cur = std::move(nxt);
     }
 
     // result

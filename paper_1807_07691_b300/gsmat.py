@@ -82,7 +82,8 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int32), ("n_in_kernel", ctypes.c_int32), ("n_reordered", ctypes.c_int32),
                 ("n_fallback", ctypes.c_int32), ("kernel_ms", ctypes.c_double), ("reorder_ms", ctypes.c_double),
                 ("arena_used", ctypes.c_int64),
-                ("block", ctypes.c_int32), ("grid", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("n_intersect", ctypes.c_int32),
+                ("_pad", ctypes.c_int32)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -163,6 +164,7 @@ def _load():
         "gsmat_exclusive_scan_i32": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc_max": ([], i64),
+        "gsmat_selftest_wait_expiry": ([i32, vp], c_int),
         "gsmat_profile_enable": ([c_int], c_int),
         "gsmat_profile_read": ([vp, i32, P(i32), c_int], c_int),
         "gsmat_launch_count": ([], i64),
