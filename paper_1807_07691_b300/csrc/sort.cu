@@ -31,19 +31,37 @@
 namespace gs {
 namespace {
 
+// Pass-kernel shape.  The defaults can be overridden at build time
+// (-DGSMAT_PASS_MIN_BLOCKS=... and so on) to measure other shapes.
+#ifndef GSMAT_PASS_MIN_BLOCKS
+#define GSMAT_PASS_MIN_BLOCKS 4
+#endif
+#ifndef GSMAT_PASS_ITEMS_U64
+#define GSMAT_PASS_ITEMS_U64 12
+#endif
+#ifndef GSMAT_PASS_ITEMS_U64_KEYS
+#define GSMAT_PASS_ITEMS_U64_KEYS 16
+#endif
+#ifndef GSMAT_PASS_ITEMS_WIDE
+#define GSMAT_PASS_ITEMS_WIDE 10
+#endif
+#ifndef GSMAT_LOOKBACK_WINDOW
+#define GSMAT_LOOKBACK_WINDOW 8
+#endif
 constexpr int kBlock = 256;               // histogram kernel
 constexpr int kPassBlock = 256;           // pass kernel (a multiple of kBins)
-constexpr int kPassMinBlocks = 4;         // pass CTAs resident per SM (register budget)
+constexpr int kPassMinBlocks = GSMAT_PASS_MIN_BLOCKS;  // pass CTAs resident per SM (register budget)
 constexpr int kPassWarps = kPassBlock / 32;
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
+constexpr int kLookbackWindow = GSMAT_LOOKBACK_WINDOW;  // predecessor descriptors read per look-back round
 
 template <class K>
 struct SortTraits;
 template <>
 struct SortTraits<uint64_t> {
-    static constexpr int kItems = 12;         // keys per thread with a payload
-    static constexpr int kItemsKeysOnly = 16; // and without
+    static constexpr int kItems = GSMAT_PASS_ITEMS_U64;             // keys per thread with a payload
+    static constexpr int kItemsKeysOnly = GSMAT_PASS_ITEMS_U64_KEYS; // and without
 };
 template <>
 struct SortTraits<uint32_t> {
@@ -51,10 +69,10 @@ struct SortTraits<uint32_t> {
     static constexpr int kItemsKeysOnly = 16;
 };
 // A 64-bit payload (packed column values carried through the passes)
-// needs more registers and shared memory per key: 10 keys per thread.
+// needs more registers and shared memory per key: fewer keys per thread.
 template <class K, bool HasVals, class V = uint32_t>
 __host__ __device__ constexpr int items_per_thread() {
-    return HasVals ? (sizeof(V) == 8 ? 10 : SortTraits<K>::kItems) : SortTraits<K>::kItemsKeysOnly;
+    return HasVals ? (sizeof(V) == 8 ? GSMAT_PASS_ITEMS_WIDE : SortTraits<K>::kItems) : SortTraits<K>::kItemsKeysOnly;
 }
 
 template <class K>
@@ -515,7 +533,7 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
         __syncwarp();
     }
     __syncthreads();
-    // per digit (thread d < kBins): cross-warp prefix, tile count, tile start
+    // per digit (thread d < kBins): cross-warp prefix and the tile's count
     const int d = threadIdx.x;
     const bool dig = d < kBins;
     uint32_t cnt = 0;
@@ -527,40 +545,26 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
             cnt += c;
         }
     }
+    const uint32_t real = cnt - (d == kBins - 1 ? (uint32_t)(TILE - valid) : 0u);
+    // Publish this tile's count of digit d before anything else, so that
+    // later tiles' look-backs find it as early as possible.  Tile 0
+    // publishes its inclusive prefix instead, with the digit's global start
+    // (exclusive scan of the pass histogram) folded in, so every later
+    // tile's look-back sum is already a global position.
     int64_t tot;
+    uint64_t excl = 0;
+    if (tile == 0) {  // uniform over the CTA (the scan synchronises)
+        const int64_t dbase =
+            block_exclusive_sum<kPassBlock>(dig ? (int64_t)__ldg(hist_pass + d) : (int64_t)0, scan_tmp, &tot);
+        excl = (uint64_t)dbase;
+        if (dig) atomicExch(desc + d, desc_pack(epoch, kDescPrefix, excl + real));
+    } else if (dig) {
+        atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescAggregate, real));
+    }
+    // tile-local start of every digit, then the tile staged in shared memory
+    // in digit order (the keys leave the registers before the look-back)
     const int64_t ts = block_exclusive_sum<kPassBlock>((int64_t)cnt, scan_tmp, &tot);
     if (dig) tstart[d] = (uint32_t)ts;
-    const uint32_t real = cnt - (d == kBins - 1 ? (uint32_t)(TILE - valid) : 0u);
-    // global start of digit d in this pass (exclusive scan of the histogram)
-    const int64_t dbase =
-        block_exclusive_sum<kPassBlock>(dig ? (int64_t)__ldg(hist_pass + d) : (int64_t)0, scan_tmp, &tot);
-    // publish this tile's count of digit d, then look back for the earlier ones
-    uint64_t excl = 0;
-    if (!dig) {
-    } else if (tile == 0) {
-        atomicExch(desc + d, desc_pack(epoch, kDescPrefix, real));
-    } else {
-        atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescAggregate, real));
-        int j = tile - 1;
-        int polls = 0;
-        while (j >= 0) {
-            const unsigned long long w = *(const volatile unsigned long long *)(desc + (int64_t)j * kBins + d);
-            const uint64_t state = (w >> 54) & 3;
-            if ((uint32_t)(w >> 56) != epoch || state == 0) {
-                if (++polls > kLookbackPollLimit) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(32);
-                continue;
-            }
-            excl += w & ((1ull << 54) - 1);
-            if (state == kDescPrefix) break;
-            --j;
-        }
-        atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescPrefix, excl + real));
-    }
-    if (dig) gbase[d] = (uint32_t)(dbase + (int64_t)excl);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
@@ -569,6 +573,51 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
         skeys[pos] = k[j];
         if (HasVals) svals[pos] = v[j];
     }
+    // Look back for digit d over the earlier tiles, kLookbackWindow
+    // descriptors in flight at a time (for each predecessor the CTA's 256
+    // digit words are one contiguous 2 KB line set), summed nearest first up
+    // to and including the first inclusive prefix.  A descriptor not yet
+    // published stops the round; the next round starts from it.  The waits
+    // are bounded: past kLookbackPollLimit the error word is set and the
+    // missing counts are taken as zero.
+    if (tile > 0 && dig) {
+        int j = tile - 1;
+        int polls = 0;
+        while (true) {
+            unsigned long long w[kLookbackWindow];
+#pragma unroll
+            for (int i = 0; i < kLookbackWindow; ++i) {
+                w[i] = j - i >= 0 ? ld_volatile_u64(desc + (int64_t)(j - i) * kBins + d)
+                                  : desc_pack(epoch, kDescPrefix, 0);
+            }
+            int used = 0;
+            bool done = false, stalled = false;
+#pragma unroll
+            for (int i = 0; i < kLookbackWindow; ++i) {
+                if (!done && !stalled) {
+                    const uint64_t state = (w[i] >> 54) & 3;
+                    if ((uint32_t)(w[i] >> 56) != epoch || state == 0) {
+                        stalled = true;
+                    } else {
+                        excl += w[i] & ((1ull << 54) - 1);
+                        used = i + 1;
+                        done = state == kDescPrefix;
+                    }
+                }
+            }
+            if (done) break;
+            j -= used;
+            if (stalled) {
+                if (++polls > kLookbackPollLimit) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescPrefix, excl + real));
+    }
+    if (dig) gbase[d] = (uint32_t)excl;
     __syncthreads();
     for (int i = threadIdx.x; i < valid; i += kPassBlock) {
         const K kk = skeys[i];
