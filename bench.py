@@ -1,17 +1,23 @@
-"""Benchmark of the plain SM-based BGP join on one B300 (or N replicas).
+"""Benchmark of the SM-based BGP join on one B300 (or N replicas).
 
-A step is one pass of the whole hot path over the medium synthetic workload
-(10^6 entities, 64 predicates, 10^7 distinct int32 triples; 40 BGPs of 3-6
-patterns):  gsmat_load of the device-resident triples (sort, dedupe,
-CSR/CSC, predicate index) followed by the 40 queries (plan, joins,
-canonical sort), each result left on the device.  The metric is queries/s
-of whole steps; result rows/s, per-query p50/p99 latency and the dominant
-kernel's HBM roofline are reported beside it.
+A step is one pass of the whole hot path over one workload: gsmat_load of
+the device-resident triples (sort, dedupe, CSR/CSC, predicate index)
+followed by every BGP of the workload (plan, joins, canonical sort), each
+result left on the device.  The headline workload is the largest
+configuration, large (4x10^7 entities, 256 predicates, 3x10^8 distinct int32
+triples; 20 anchored BGPs of 4-8 patterns); the medium one (10^7 triples,
+40 BGPs) is reported beside it.  The metric is queries/s of whole steps;
+result rows/s, per-query p50/p99 latency, an end-to-end figure with host
+buffers and the dominant kernel family's HBM roofline come with it, then
+the batched mix, the planners, the front end, row shards and the served
+arrivals.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gsmat|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|medium]
+                    [--impl gsmat|reference]
 
 --impl reference times the CPU oracle (the plain nested-loop join over the
-raw triple list) on a bounded sample of the same workload.
+raw triple list; the paper publishes no code) on the host cores, on the
+same sample of the workload as the cpu_baseline field.
 Multi-GPU (torchrun): every rank runs the same workload on its own GPU
 (independent replicas, no collective on the data path); value = all ranks'
 queries / max rank time.
@@ -33,7 +39,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "queries/s"
-CONFIG_NAME = "medium"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -44,12 +49,12 @@ def _dist():
     return ws, rank, local
 
 
-def _workload():
+def _workload(name):
     import synth
 
     t0 = time.time()
-    triples = synth.make_graph(CONFIG_NAME)
-    queries = synth.make_queries(CONFIG_NAME, triples)
+    triples = synth.make_graph(name)
+    queries = synth.make_large_queries(triples) if name == "large" else synth.make_queries(name, triples)
     return triples, queries, time.time() - t0
 
 
@@ -145,27 +150,20 @@ def _flush_l2(torch, buf):
     buf.add_(1)
 
 
-def run_gsmat(args):
-    import torch
-
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import paper_1807_07691_b300 as gs
-
-    triples, queries, gen_s = _workload()
+def plain_leg(args, gs, torch, name, triples, queries, stream, ws, local, steps, warmup):
+    """The plain path on one workload: `warmup` untimed steps, then `steps`
+    timed steps (gsmat_load of the device-resident triples + every BGP,
+    sorted results left on the device), each bracketed by CUDA events on the
+    launching stream with L2 flushed (256 MB write) before it; per-query
+    device latency; per-kernel-family event times; the library's launch
+    count; then the same steps end to end through the public API with host
+    buffers (pinned triples in, every result copied to pinned host memory)."""
     nq = len(queries)
     d_tri = torch.from_numpy(np.array(triples, copy=True)).cuda()
-    h_tri = torch.from_numpy(np.array(triples, copy=True)).pin_memory()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
     marsh = [gs.Store.marshal(q) for q in queries]  # BGPs converted to the C layout once
 
-    def step(profile_rows=None, lat=None):
+    def step(lat=None):
         S = gs.Store(d_tri, stream=stream)
         tabs = []
         rows = 0
@@ -193,11 +191,9 @@ def run_gsmat(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     barrier()
-
-    # timed region: K steps, each bracketed by events; L2 flushed between
     gs.profile_read(reset=True)
     gs.profile_enable(True)
     step_ms = []
@@ -205,9 +201,8 @@ def run_gsmat(args):
     rows_total = 0
     with ClockSampler(local) as clk:
         barrier()
-        t_wall = time.time()
         lc0 = gs.launch_count()
-        for _ in range(args.steps):
+        for _ in range(steps):
             _flush_l2(torch, flush)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
@@ -218,22 +213,22 @@ def run_gsmat(args):
             step_ms.append(a.elapsed_time(b))
         lc1 = gs.launch_count()
         barrier()
-        t_wall = time.time() - t_wall
     gs.profile_enable(False)
     prof = gs.profile_read(reset=True)
+    del flush
     my_ms = float(sum(step_ms))
     total_ms, _ = reduce_over_ranks(my_ms, rows_total, device="cuda")
     q_lat = np.array([e0.elapsed_time(e1) for (e0, e1) in lat])
 
-    # end-to-end through the public API with host buffers: H2D of the triples
-    # inside gsmat_load, D2H of every result table into pinned host memory;
-    # each result travels on a second stream (gsmat_table_copy_async) while
-    # the next query computes, and the step ends when the last copy has landed
+    # end to end: H2D of the triples inside gsmat_load, D2H of every result
+    # table into pinned host memory on a second stream while the next query
+    # computes; the step ends when the last copy has landed
+    h_tri = torch.from_numpy(np.array(triples, copy=True)).pin_memory()
     e2e_ms = []
     d2h = 0
     host_out = {}  # pinned result buffers, allocated in the first (untimed) pass
     copy_stream = torch.cuda.Stream()
-    for it in range(1 + max(1, min(args.steps, 3))):
+    for it in range(1 + max(1, min(steps, 3))):
         barrier()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -257,26 +252,135 @@ def run_gsmat(args):
         b.synchronize()
         if it > 0:
             e2e_ms.append(a.elapsed_time(b))
+    del host_out, h_tri
+    launches = int(lc1 - lc0)
+    return {
+        "name": name,
+        "value": job_value(ws, steps, nq, total_ms),
+        "total_ms": total_ms,
+        "steps": steps,
+        "step_ms": step_ms,
+        "rows_total": rows_total,
+        "q_lat": q_lat,
+        "prof": prof,
+        "launches": launches,
+        "clocks": clk.summary(),
+        "e2e": {"value": round(nq / (float(np.median(e2e_ms)) / 1e3), 2), "unit": "queries/s",
+                "h2d_bytes_per_step": int(np.asarray(triples).nbytes), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": round(float(np.median(e2e_ms)), 3)},
+        "d_tri": d_tri,
+        "nq": nq,
+        "n_triples": int(np.asarray(triples).shape[0]),
+    }
 
-    batched = None
-    served = None
-    planner = None
-    bq = None
+
+# DRAM bytes / algorithmic bytes per launch, measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum over a family's kernels
+# against the library's algorithmic bytes for the same calls); the profiles
+# named give the captures.
+TRAFFIC_RATIO = {
+    # profiles/reorder_sort_q14_traffic.md: the 62 M-row reorder of the medium
+    # chain query q14, 11719.0 MB of DRAM traffic against 10917.8 MB algorithmic
+    "reorder_sort": (11719.0 / 10917.8, "profiles/reorder_sort_q14_traffic.md (one call: medium q14)"),
+}
+
+
+def roofline(prof, ws, peak, peak_kind, exclude=("store_build",)):
+    """The dominant kernel family by event time (pipelines that bracket
+    several families, such as the whole store build, are reported in
+    `kernels` but are not a kernel): algorithmic bytes per launch over the
+    average launch time, against the measured HBM copy bandwidth."""
+    cands = [(k, v) for k, v in prof.items() if k not in exclude and v["total_ms"] > 0]
+    if not cands:
+        return None
+    name, p = max(cands, key=lambda kv: kv[1]["total_ms"])
+    achieved = p["algo_bytes"] / 1e9 / (p["total_ms"] / 1e3)
+    per_launch_algo = p["algo_bytes"] / max(1, p["launches"])
+    per_launch_ms = p["total_ms"] / max(1, p["launches"])
+    ratio = TRAFFIC_RATIO.get(name)
+    traffic = round(per_launch_algo * ratio[0]) if ratio else None
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "traffic_source": ratio[1] if ratio else "no ncu capture of this family on the current build",
+            "dram_GBps": round(traffic / 1e9 / (per_launch_ms / 1e3), 1) if traffic and per_launch_ms > 0 else None,
+            "per_launch_ms": round(per_launch_ms, 4), "launches": int(p["launches"]),
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
+
+
+def kernel_table(prof):
+    return {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
+                "GBps": round(v["algo_bytes"] / 1e9 / (v["total_ms"] / 1e3), 1) if v["total_ms"] else None}
+            for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])}
+
+
+def leg_summary(leg, peak, peak_kind, ws):
+    """The JSON fields of one workload's plain path."""
+    q = leg["q_lat"]
+    return {
+        "value": round(leg["value"], 2),
+        "unit": "queries/s",
+        "ms_per_step": round(leg["total_ms"] / leg["steps"], 3),
+        "result_rows_per_s": round(ws * leg["rows_total"] / (leg["total_ms"] / 1e3), 1),
+        "result_rows_per_step": int(leg["rows_total"] / max(1, leg["steps"])),
+        "latency_ms": {"p50": round(float(np.percentile(q, 50)), 4), "p99": round(float(np.percentile(q, 99)), 4),
+                       "note": "per-query device time inside the timed steps (store resident)"},
+        "e2e": leg["e2e"],
+        "gpu_launches": leg["launches"],
+        "roofline": roofline(leg["prof"], ws, peak, peak_kind),
+        "kernels": kernel_table(leg["prof"]),
+        "clocks": leg["clocks"],
+    }
+
+
+def run_gsmat(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1807_07691_b300 as gs
+
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = _peaks()
+    head_name = args.workload
+    triples, queries, gen_s = _workload(head_name)
+    head = plain_leg(args, gs, torch, head_name, triples, queries, stream, ws, local, args.steps, args.warmup)
+
+    # the medium workload: a second plain-path line, and the graph of the
+    # batched, planner, front-end and shard legs
+    if head_name == "medium":
+        m_tri, m_queries, m_gen_s, medium = triples, queries, gen_s, None
+        d_med = head["d_tri"]
+    else:
+        m_tri, m_queries, m_gen_s = _workload("medium")
+        medium = None
+        if not args.no_medium and head_name == "large":
+            medium = plain_leg(args, gs, torch, "medium", m_tri, m_queries, stream, ws, local, args.steps, args.warmup)
+            d_med = medium["d_tri"]
+        else:
+            d_med = torch.from_numpy(np.array(m_tri, copy=True)).cuda()
+
+    batched = served = planner = bq = None
     if not args.no_batched:
-        batched, bq, tuned = run_batched(args, gs, torch, d_tri, stream)
+        batched, bq, tuned = run_batched(args, gs, torch, d_med, stream)
         if not args.no_planner:
-            planner = run_planner(args, gs, torch, d_tri, stream, queries, bq, tuned)
+            planner = run_planner(args, gs, torch, d_med, stream, m_queries, bq, tuned)
     frontend = None
     if not args.no_frontend:
-        frontend = run_frontend(args, gs, torch, d_tri, stream, triples, queries)
+        frontend = run_frontend(args, gs, torch, d_med, stream, m_tri, m_queries)
     shards = None
     if not args.no_shards:
-        shards = run_shards(args, gs, torch, d_tri, stream, queries)
-    if bq is not None and not args.no_served:  # the served mix is the batched one
-        served = run_served(args, gs, torch, d_tri, stream, bq)
-    served_large = None
-    if args.served_graph == "large" and rank == 0:
-        served_large = run_served_large(args, gs, torch, stream)
+        shards = run_shards(args, gs, torch, d_med, stream, m_queries)
+    if not args.no_served and rank == 0:
+        if args.served_graph == "large":
+            served = run_served_large(args, gs, torch, stream,
+                                      d_tri=head["d_tri"] if head_name == "large" else None,
+                                      triples=triples if head_name == "large" else None)
+        elif bq is not None:  # the medium graph's batched mix
+            served = run_served(args, gs, torch, d_med, stream, bq)
 
     if rank != 0:
         if ws > 1:
@@ -285,60 +389,35 @@ def run_gsmat(args):
             dist.destroy_process_group()
         return None
 
-    peak, peak_kind = _peaks()
-    # DRAM bytes / algorithmic bytes of one launch, from an ncu capture
-    # (dram__bytes_read.sum + dram__bytes_write.sum over the call's kernels) of
-    # the family's largest call: the 62 M-row reorder of the chain query q14,
-    # 11719.0 MB of traffic against 10917.8 MB algorithmic
-    traffic_ratio = {"reorder_sort": 11719.0 / 10917.8}
-    # dominant kernel by total event time
-    top = max(prof.items(), key=lambda kv: kv[1]["total_ms"]) if prof else None
-    roof = None
-    if top:
-        name, p = top
-        achieved = p["algo_bytes"] / 1e9 / (p["total_ms"] / 1e3) if p["total_ms"] > 0 else 0.0
-        per_launch_algo = p["algo_bytes"] / max(1, p["launches"])
-        traffic = round(per_launch_algo * traffic_ratio[name]) if name in traffic_ratio else None
-        per_launch_ms = p["total_ms"] / max(1, p["launches"])
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                # DRAM bytes (from the ncu ratio) over the same event time
-                "dram_GBps": round(traffic / 1e9 / (per_launch_ms / 1e3), 1) if traffic and per_launch_ms > 0 else None,
-                "per_launch_ms": round(per_launch_ms, 4),
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind}
-    launches = int(lc1 - lc0)  # kernels the library launched in the timed steps
-    value = job_value(ws, args.steps, nq, total_ms)
-    rows_per_s = ws * rows_total / (total_ms / 1e3)
-    e2e_value = nq / (float(np.median(e2e_ms)) / 1e3)
+    hs = leg_summary(head, peak, peak_kind, ws)
     out = {
         "metric": METRIC,
-        "value": round(value, 2),
+        "value": hs["value"],
         "unit": "queries/s",
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(total_ms / args.steps, 3),
+        "ms_per_step": hs["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": workload_config(nq, int(triples.shape[0]), ws),
-        "result_rows_per_s": round(rows_per_s, 1),
-        "result_rows_per_step": int(rows_total / max(1, args.steps)),
-        "latency_ms": {"p50": round(float(np.percentile(q_lat, 50)), 4),
-                       "p99": round(float(np.percentile(q_lat, 99)), 4),
-                       "note": "per-query device time inside the timed steps (store resident)"},
-        "e2e": {"value": round(e2e_value, 2), "unit": "queries/s", "h2d_bytes_per_step": int(triples.nbytes),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(float(np.median(e2e_ms)), 3)},
-        "gpu_launches": launches,
-        "roofline": roof,
-        "kernels": {k: {"launches": v["launches"], "total_ms": round(v["total_ms"], 3),
-                        "GBps": round(v["algo_bytes"] / 1e9 / (v["total_ms"] / 1e3), 1) if v["total_ms"] else None}
-                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"])},
-        "clocks": clk.summary(),
+        "config": workload_config(head_name, head["nq"], head["n_triples"], ws),
+        "result_rows_per_s": hs["result_rows_per_s"],
+        "result_rows_per_step": hs["result_rows_per_step"],
+        "latency_ms": hs["latency_ms"],
+        "e2e": hs["e2e"],
+        "gpu_launches": hs["gpu_launches"],
+        "roofline": hs["roofline"],
+        "kernels": hs["kernels"],
+        "clocks": hs["clocks"],
         "generation_s": round(gen_s, 1),
     }
+    if medium is not None:
+        ms_ = leg_summary(medium, peak, peak_kind, ws)
+        ms_["config"] = workload_config("medium", medium["nq"], medium["n_triples"], ws)
+        out["medium"] = ms_
     if batched is not None:
         out["batched"] = batched
     if planner is not None:
@@ -349,12 +428,17 @@ def run_gsmat(args):
         out["row_shards"] = shards
     if served is not None:
         out["served"] = served
-    if served_large is not None:
-        out["served_large"] = served_large
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(triples, queries, budget_s=args.cpu_budget)
-        n_att = out["cpu_baseline"]["attempted"]
-        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(triples, queries[:n_att])
+        sample = reference_sample(head_name, queries)
+        out["cpu_baseline"] = cpu_baseline(triples, sample, budget_s=args.cpu_budget, workload=head_name,
+                                           n_total=len(queries))
+        if head_name == "medium" or medium is not None:
+            m_sample = reference_sample("medium", m_queries)
+            one_m = cpu_baseline(m_tri, m_sample, budget_s=args.cpu_budget, workload="medium", n_total=len(m_queries))
+            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(m_tri, m_sample[:one_m["attempted"]])
+            out["cpu_baseline_all_cores"]["workload"] = "medium"
+            if head_name != "medium":
+                out["medium"]["cpu_baseline"] = one_m
     if ws > 1:
         import torch.distributed as dist
 
@@ -672,9 +756,49 @@ def run_served(args, gs, torch, d_tri, stream, bq, workload=None):
     return out
 
 
-def cpu_baseline(triples, queries, budget_s=20.0):
+# The oracle's sample of a workload: the queries, in workload order, whose
+# generator size bound (an upper bound on every connected sub-pattern's rows;
+# exact for the large stars and chains) is at most this many rows.  The
+# others would keep a host core busy for minutes each.
+ORACLE_ROW_CAP = 30_000_000
+
+
+def reference_sample(name, queries):
+    """(sample, skipped names): the queries the oracle runs for `name`."""
+    keep, skipped = [], []
+    for q in queries:
+        b = getattr(q, "bound", None)
+        if b is not None and b > ORACLE_ROW_CAP:
+            skipped.append(q.name)
+        else:
+            keep.append(q)
+    return keep if not skipped else _Sample(keep, skipped)
+
+
+class _Sample(list):
+    """A list of queries that remembers which ones were left out."""
+
+    def __init__(self, keep, skipped):
+        super().__init__(keep)
+        self.skipped = list(skipped)
+
+
+def _run_oracle(ix, q):
+    """Runs one query on the oracle; False if it passed the guard limit."""
+    import oracle
+
+    try:
+        ix.query(q, row_limit=4 * ORACLE_ROW_CAP)
+        return True
+    except oracle.OracleError:
+        return False
+
+
+def cpu_baseline(triples, sample, budget_s=20.0, workload="medium", n_total=None):
     """The oracle as it stands, single-threaded, on a bounded sample: its
-    index build plus queries in workload order until the budget is spent."""
+    index build, then the sample's queries in workload order until the
+    budget is spent; value = queries finished / their time (an aborted
+    query's time counts too)."""
     import oracle
 
     t0 = time.perf_counter()
@@ -682,24 +806,26 @@ def cpu_baseline(triples, queries, budget_s=20.0):
     t_index = time.perf_counter() - t0
     done = 0
     t_q = 0.0
-    skipped = []
-    for q in queries:
-        if t_index + t_q > budget_s:
+    aborted = []
+    for q in sample:
+        if t_q > budget_s:
             break
         a = time.perf_counter()
-        try:
-            ix.query(q, row_limit=30_000_000)
-            t_q += time.perf_counter() - a
+        ok = _run_oracle(ix, q)
+        t_q += time.perf_counter() - a
+        if ok:
             done += 1
-        except oracle.OracleError:
-            t_q += time.perf_counter() - a
-            skipped.append(q.name)
+        else:
+            aborted.append(q.name)
     value = done / t_q if t_q > 0 else None
+    left_out = getattr(sample, "skipped", [])
+    n_total = len(sample) + len(left_out) if n_total is None else n_total
     return {"value": round(value, 3) if value else None, "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "cpu_model": _cpu_model(), "nproc": os.cpu_count(), "attempted": done + len(skipped),
-            "sample": f"index build ({t_index:.1f} s, not in value) + the first {done} of {len(queries)} medium "
-                      f"queries in workload order ({t_q:.1f} s); queries above 3e7 intermediate rows skipped: "
-                      f"{len(skipped)}"}
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count(), "attempted": done + len(aborted),
+            "sample": f"{workload}: oracle index build ({t_index:.1f} s, not in value), then {done + len(aborted)} of "
+                      f"the {n_total} queries in workload order ({t_q:.2f} s); left out (generator bound above "
+                      f"{ORACLE_ROW_CAP:.0e} rows): {len(left_out)} {left_out}; aborted past "
+                      f"{4 * ORACLE_ROW_CAP:.0e} rows: {aborted}"}
 
 
 def _cpu_model() -> str:
@@ -779,45 +905,62 @@ def cpu_baseline_all_cores(triples, queries, max_procs=32):
     return out
 
 
-def workload_config(nq, n_triples, ws):
-    """The `config` both arms report (the reference arm times a bounded
-    sample of this workload and says which in cpu_baseline.sample)."""
+WORKLOAD_TEXT = {
+    "tiny": "plain SM-join, tiny: 10^4 entities, 8 predicates, 10^5 int32 triples, 10 BGPs of 2-3 patterns",
+    "large": "plain SM-join, large: 4x10^7 entities, 256 predicates, 3x10^8 int32 triples, 20 anchored BGPs of "
+             "4-8 patterns (stars, chains, snowflakes; results up to 5x10^8 rows)",
+    "medium": "plain SM-join, medium: 10^6 entities, 64 predicates, 10^7 int32 triples, 40 BGPs of 3-6 patterns "
+              "(stars, chains, snowflakes, one 4-cycle)",
+}
+
+
+def workload_config(name, nq, n_triples, ws):
+    """The `config` of a plain-path line (the reference arm adds which
+    queries of it the oracle ran)."""
     return {
-        "workload": "plain SM-join, medium: 10^6 entities, 64 predicates, 10^7 int32 triples, 40 BGPs of 3-6 "
-                    "patterns; step = gsmat_load + 40 queries (sorted results kept on device)",
+        "workload": f"{WORKLOAD_TEXT[name]}; step = gsmat_load + {nq} queries (sorted results kept on device)",
         "queries_per_step": nq,
         "triples": n_triples,
-        "l2": "flushed between timed steps (256 MB write)",
+        "l2": "flushed between timed steps (256 MB write); the inputs are far larger than L2",
         "parallelism": f"replicas x{ws}",
     }
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper publishes no code) on the
+    host cores, each step the same sample of the workload that cpu_baseline
+    uses, with the index built once before the steps."""
     ws, rank, local = _dist()
     if rank != 0:
         return None
-    triples, queries, _ = _workload()
+    triples, queries, _ = _workload(args.workload)
     import oracle
 
+    sample = reference_sample(args.workload, queries)
+    left_out = getattr(sample, "skipped", [])
+    t0 = time.perf_counter()
     ix = oracle.OracleIndex(triples)
-    # each step: a bounded sample (the first queries of the workload)
-    sample = queries[:8]
+    t_index = time.perf_counter() - t0
     times = []
+    aborted = set()
     for i in range(args.warmup + args.steps):
         a = time.perf_counter()
         n = 0
         for q in sample:
-            try:
-                ix.query(q, row_limit=30_000_000)
+            if _run_oracle(ix, q):
                 n += 1
-            except oracle.OracleError:
-                pass
+            else:
+                aborted.add(q.name)
         dt = time.perf_counter() - a
         if i >= args.warmup:
             times.append((n, dt))
     n_tot = sum(n for n, _ in times)
     t_tot = sum(dt for _, dt in times)
     value = n_tot / t_tot if t_tot > 0 else 0.0
+    cfg = workload_config(args.workload, len(queries), int(triples.shape[0]), ws)
+    cfg["reference_sample"] = (f"{len(sample)} of {len(queries)} queries per step, workload order; left out "
+                               f"(generator bound above {ORACLE_ROW_CAP:.0e} rows): {left_out}; oracle index prebuilt "
+                               f"({t_index:.1f} s), no store load in the step")
     return {
         "impl": "reference",
         "metric": METRIC,
@@ -832,32 +975,33 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": workload_config(len(queries), int(triples.shape[0]), ws),
+        "config": cfg,
         "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: the first {len(sample)} of the {len(queries)} medium queries in "
-                                   "workload order on the oracle (one core, index prebuilt, no store load); queries "
-                                   "above 3e7 intermediate rows skipped"},
+                         "sample": f"each step: {cfg['reference_sample']}; aborted past {4 * ORACLE_ROW_CAP:.0e} "
+                                   f"rows: {sorted(aborted)}"},
         "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def run_served_large(args, gs, torch, stream):
+def run_served_large(args, gs, torch, stream, d_tri=None, triples=None):
     """The served measurement over the large graph (3x10^8 triples resident
     on the device) with its own anchored 2-8-pattern mix."""
     import synth
 
     t0 = time.time()
-    tri = synth.make_graph("large")
+    tri = synth.make_graph("large") if triples is None else triples
     qs = synth.make_large_served_queries(tri, n_queries=args.served_large_n)
     gen_s = time.time() - t0
-    d_tri = torch.from_numpy(tri).cuda()
-    del tri
+    own = d_tri is None
+    if own:
+        d_tri = torch.from_numpy(np.array(tri, copy=True)).cuda()
     out = run_served(args, gs, torch, d_tri, stream, qs,
                      workload=f"Poisson arrivals over {len(qs)} anchored BGPs of 2-8 patterns, star:chain:snowflake "
-                              "4:3:2 (large graph, 3x10^8 triples, resident store)")
+                              "4:3:2 (large graph, 3x10^8 triples, resident store, 120 GiB admission budget)")
     out["generation_s"] = round(gen_s, 1)
-    del d_tri
-    torch.cuda.empty_cache()
+    if own:
+        del d_tri
+        torch.cuda.empty_cache()
     return out
 
 
@@ -909,8 +1053,40 @@ def run_micro(args):
                 ms.append(a.elapsed_time(b))
         t = float(np.median(ms))
         out.update({"ms": round(t, 4), "algo_GBps": round(n * 12.0 / 1e9 / (t / 1e3), 1)})
+    elif args.micro == "rows":
+        # the canonical reorder on its own: n rows of V random columns of
+        # `row_bits`-bit values, stably sorted by the first key_cols
+        V, m, bits = args.cols, args.key_cols, args.row_bits
+        cols = [torch.randint(0, 1 << bits, (n,), device="cuda", dtype=torch.int32, generator=g) for _ in range(V)]
+        outc = [c.new_empty(n) for c in cols]
+        ms = []
+        gs.profile_read(reset=True)
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                gs.profile_read(reset=True)
+                gs.profile_enable(True)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            gs.sort_rows(cols, m, bits, out=outc, flags=args.sort_flags)
+            b.record()
+            b.synchronize()
+            if it >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        gs.profile_enable(False)
+        prof = gs.profile_read(reset=True).get("reorder_sort")
+        undecided = torch.ones(n - 1, dtype=torch.bool, device="cuda")
+        for c in range(m):
+            x, y = outc[c][:-1], outc[c][1:]
+            assert not bool((undecided & (y < x)).any())
+            undecided &= y == x
+        t = float(np.median(ms))
+        out.update({"cols": V, "key_cols": m, "row_bits": bits, "ms": round(t, 4),
+                    "algo_GBps": round(prof["algo_bytes"] / 1e9 / (prof["total_ms"] / 1e3), 1) if prof else None,
+                    "algo_bytes_per_row": round(prof["algo_bytes"] / prof["items"], 2) if prof else None,
+                    "Mrows_per_s": round(n / 1e3 / t, 1)})
     elif args.micro == "query":
-        triples, queries, _ = _workload()
+        triples, queries, _ = _workload(args.workload)
         S = gs.Store(torch.from_numpy(np.array(triples, copy=True)).cuda())
         q = queries[args.query_index]
         ms = []
@@ -933,14 +1109,21 @@ def run_micro(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--query-index", type=int, default=14)
-    ap.add_argument("--micro", choices=["sort", "scan", "query"], default=None,
+    ap.add_argument("--micro", choices=["sort", "scan", "rows", "query"], default=None,
                     help="time one primitive on a synthetic input instead of the workload")
     ap.add_argument("--n", type=int, default=1 << 25)
     ap.add_argument("--bits", type=int, default=40)
+    ap.add_argument("--cols", type=int, default=4, help="--micro rows: columns")
+    ap.add_argument("--key-cols", type=int, default=2, help="--micro rows: leading sort columns")
+    ap.add_argument("--row-bits", type=int, default=20, help="--micro rows: bits per value")
+    ap.add_argument("--sort-flags", type=int, default=0, help="--micro rows: 1 carry, 2 gather (0: by size)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsmat", choices=["gsmat", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
+                    help="the headline plain-path workload (large: the largest configuration)")
+    ap.add_argument("--no-medium", action="store_true", help="skip the medium plain-path line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-n", type=int, default=4096)
@@ -948,12 +1131,12 @@ def main():
     ap.add_argument("--no-frontend", action="store_true", help="skip the dictionary / SPARQL / DISTINCT leg")
     ap.add_argument("--no-shards", action="store_true", help="skip the row-sharding leg")
     ap.add_argument("--no-served", action="store_true")
-    ap.add_argument("--served-seconds", type=float, default=2.0)
+    ap.add_argument("--served-seconds", type=float, default=30.0)
     ap.add_argument("--served-rates", type=float, nargs="+", default=[1000, 5000, 20000])
     ap.add_argument("--served-max-batch", type=int, default=1024)
     ap.add_argument("--served-slots", type=int, default=4)
-    ap.add_argument("--served-graph", choices=["medium", "large"], default="medium",
-                    help="large: also serve an anchored mix over the large graph (generation takes minutes)")
+    ap.add_argument("--served-graph", choices=["medium", "large"], default="large",
+                    help="large: an anchored mix over the resident large graph; medium: the batched mix")
     ap.add_argument("--served-large-n", type=int, default=1024)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
