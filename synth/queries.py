@@ -780,16 +780,65 @@ def _large_one(adj, rng, shape, n_pat, limit, max_anchor_deg, min_bound=0.0):
     raise RuntimeError(f"no large {shape}/{n_pat} query")
 
 
+def _disk_cached(kind, triples, params, build):
+    """build() once per (triples, params, generator source) and keep the
+    result on disk (the large workloads take minutes to draw and several
+    processes need the same one).  GSMAT_SYNTH_CACHE names the folder ("0":
+    off); the key holds a fingerprint of the triples (shape and a strided
+    sample) and a digest of this package's source."""
+    import hashlib
+    import pickle
+    import tempfile
+
+    where = os.environ.get("GSMAT_SYNTH_CACHE", os.path.join(tempfile.gettempdir(), "gsmat_synth"))
+    if where == "0":
+        return build()
+    t = np.asarray(triples)
+    h = hashlib.sha256()
+    h.update(repr((t.shape, str(t.dtype), params)).encode())
+    step = max(1, t.shape[0] // 65536)
+    h.update(np.ascontiguousarray(t[::step]).tobytes())
+    here = os.path.dirname(os.path.abspath(__file__))
+    for name in ("graphs.py", "queries.py"):
+        with open(os.path.join(here, name), "rb") as f:
+            h.update(f.read())
+    path = os.path.join(where, f"{kind}_{h.hexdigest()[:24]}.pkl")
+    if os.path.exists(path):
+        try:
+            with open(path, "rb") as f:
+                return pickle.load(f)
+        except (OSError, pickle.UnpicklingError, EOFError):
+            pass
+    out = build()
+    try:
+        os.makedirs(where, exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "wb") as f:
+            pickle.dump(out, f)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return out
+
+
 def make_large_queries(triples: np.ndarray | None = None, seed: int | None = None, n_queries: int = 20,
                        limit: float = 1e9):
+    """The large configuration's 20 anchored BGPs (see _make_large_queries),
+    kept on disk between processes."""
+    cfg = CONFIGS["large"]
+    if triples is None:
+        triples = make_graph(cfg)
+    seed = cfg.query_seed if seed is None else seed
+    return _disk_cached("large_queries", triples, (seed, n_queries, limit),
+                        lambda: _make_large_queries(triples, seed, n_queries, limit))
+
+
+def _make_large_queries(triples: np.ndarray, seed: int, n_queries: int, limit: float):
     """20 anchored BGPs of 4-8 patterns over the large graph: stars,
     chains and snowflakes, from selective ones to intermediates of 10^8-10^9
     rows.  ``bgp.bound`` is the exact row count (stars, chains' largest
     frontier) or an upper bound (snowflakes)."""
     cfg = CONFIGS["large"]
-    if triples is None:
-        triples = make_graph(cfg)
-    seed = cfg.query_seed if seed is None else seed
     rng = np.random.Generator(np.random.PCG64(seed))
     adj = _LargeAdjacency(triples, cfg.n_entities)
     min_pred = int(adj.pred_nnz.min())
@@ -810,6 +859,18 @@ def make_large_queries(triples: np.ndarray | None = None, seed: int | None = Non
 
 def make_large_served_queries(triples: np.ndarray | None = None, n_queries: int = 2048, seed: int | None = None,
                               limit: float = 1e6, n_entities: int | None = None):
+    """The served mix over the large graph (see _make_large_served_queries),
+    kept on disk between processes."""
+    cfg = CONFIGS["large"]
+    if triples is None:
+        triples = make_graph(cfg)
+    seed = cfg.query_seed + 1 if seed is None else seed
+    return _disk_cached("large_served", triples, (n_queries, seed, limit, n_entities),
+                        lambda: _make_large_served_queries(triples, n_queries, seed, limit, n_entities))
+
+
+def _make_large_served_queries(triples: np.ndarray, n_queries: int, seed: int, limit: float,
+                               n_entities: int | None):
     """Served mix over the large graph: 2-8 patterns, shapes
     star:chain:snowflake = 4:3:2, each anchored at one constant whose row is
     short, every plan prefix bounded by ``limit`` rows (uneven selectivity:
@@ -817,9 +878,6 @@ def make_large_served_queries(triples: np.ndarray | None = None, n_queries: int 
     left out: closing a cycle needs a walk-count search that the sparse
     frontier sampler does not do."""
     cfg = CONFIGS["large"]
-    if triples is None:
-        triples = make_graph(cfg)
-    seed = cfg.query_seed + 1 if seed is None else seed
     rng = np.random.Generator(np.random.PCG64(seed))
     adj = _LargeAdjacency(triples, cfg.n_entities if n_entities is None else n_entities)
     shapes = ("star",) * 4 + ("chain",) * 3 + ("snowflake",) * 2
