@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -100,18 +101,20 @@ struct gsmat_server {
     bool stop = false;
     bool sched_done = false;  // the scheduler has exited (nothing more will be launched)
     gsmat_server_stats_t stats{};
-    // the lone lane: one request at a time on the plain path, on its own
-    // stream and thread, while the scheduler keeps admitting micro-batches
-    cudaStream_t lone_stream = nullptr;
-    std::condition_variable cv_lone;
-    std::shared_ptr<Request> lone_req;  // handed over, not yet finished
-    double lone_bytes = 0;
-    // mean gap between submissions (exponentially weighted, microseconds):
-    // the lone lane serves only sparse arrivals, where the next request
-    // usually comes after the lone one has finished
-    double gap_us = 1e9;
-    Clock::time_point last_submit{};
-    std::thread sched, comp, lone;
+    // direct lanes: each runs one request at a time on the plain path (as
+    // gsmat_query), on its own stream and thread, while the scheduler keeps
+    // admitting micro-batches
+    struct Lane {
+        cudaStream_t st = nullptr;
+        std::shared_ptr<Request> req;  // handed over, not yet finished (under mu)
+        double bytes = 0;
+        std::atomic<int> pending{0};   // 1 while req is set (read without the lock)
+        std::thread th;
+    };
+    std::vector<std::unique_ptr<Lane>> lanes;
+    std::condition_variable cv_lane;
+    std::atomic<uint64_t> submit_seq{0};  // submissions so far (read without the lock)
+    std::thread sched, comp;
 };
 
 namespace gs {
@@ -158,33 +161,51 @@ void fail_requests(gsmat_server *srv, std::vector<std::shared_ptr<Request>> &rs,
     }
 }
 
-// The lone lane: runs each handed-over request on the plain path (as
-// gsmat_query) on its own stream, then completes it.  The scheduler hands a
-// request over only when it was admitted alone while nothing else was on the
-// device, where the plain path's multi-CTA steps finish one query sooner
-// than a one-query micro-batch.
-constexpr double kLoneGapUs = 500.0;
+// Wait-loop pause of the threads that spin before blocking.
+inline void cpu_relax() {
+#if defined(__x86_64__)
+    __builtin_ia32_pause();
+#else
+    std::this_thread::yield();
+#endif
+}
 
-void lone_loop(gsmat_server *srv) {
+// The scheduler and the direct lanes spin this long on their next event
+// before blocking on a condition variable: at a few hundred requests per
+// second and more they never sleep, so a request is not delayed by a thread
+// wake-up (tens of microseconds each); below that they block.
+constexpr int kSpinUs = 2000;
+
+// A direct lane: runs each handed-over request on the plain path (as
+// gsmat_query) on its own stream, then completes it.  The scheduler hands a
+// request to an idle lane when it found the queue empty, so under light load
+// every request starts at once on the plain path's multi-CTA steps (a
+// one-query micro-batch runs on one CTA and pays the batch machinery);
+// requests that queue up behind busy lanes form micro-batches.
+void lane_loop(gsmat_server *srv, gsmat_server::Lane *L) {
     cudaSetDevice(srv->device);
     while (true) {
+        {
+            const Clock::time_point until = Clock::now() + std::chrono::microseconds(kSpinUs);
+            while (!L->pending.load(std::memory_order_acquire) && Clock::now() < until) cpu_relax();
+        }
         std::shared_ptr<Request> r;
         double bytes = 0;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
-            srv->cv_lone.wait(lk, [&] { return srv->sched_done || srv->lone_req != nullptr; });
-            if (!srv->lone_req) return;  // the scheduler is gone and nothing is pending
-            r = srv->lone_req;
-            bytes = srv->lone_bytes;
+            srv->cv_lane.wait(lk, [&] { return srv->sched_done || L->req != nullptr; });
+            if (!L->req) return;  // the scheduler is gone and nothing is pending
+            r = L->req;
+            bytes = L->bytes;
         }
         auto holder = std::make_shared<TableHolder>();
         const uint32_t flags = srv->cfg.batch.plan_cost ? GSMAT_PLAN_COST : GSMAT_SORTED;
-        const int rc =
-            query_run(srv->S, r->pats.data(), (int)r->pats.size(), r->n_vars, flags, srv->lone_stream, &holder->T);
+        const int rc = query_run(srv->S, r->pats.data(), (int)r->pats.size(), r->n_vars, flags, L->st, &holder->T);
         profile_flush();
         const Clock::time_point now = Clock::now();
         std::lock_guard<std::mutex> lk(srv->mu);
-        srv->lone_req = nullptr;
+        L->req = nullptr;
+        L->pending.store(0, std::memory_order_release);
         srv->inflight_bytes -= bytes;
         srv->finished_batches++;
         r->t_done = now;
@@ -211,9 +232,27 @@ void scheduler_loop(gsmat_server *srv) {
         int slot = -1;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
+            auto idle_lane = [&]() -> gsmat_server::Lane * {
+                for (auto &L : srv->lanes) {
+                    if (!L->req) return L.get();
+                }
+                return nullptr;
+            };
             // a slot is free only once the completion thread has finished
             // its micro-batch and handed the slot's resources back
-            srv->cv_sched.wait(lk, [&] { return srv->stop || (!srv->queue.empty() && !srv->free_slots.empty()); });
+            auto ready = [&] {
+                return srv->stop ||
+                       (!srv->queue.empty() && (!srv->free_slots.empty() || (srv->queue.size() == 1 && idle_lane())));
+            };
+            if (!ready()) {
+                // spin on the submissions before blocking (see kSpinUs)
+                const uint64_t seen = srv->submit_seq.load(std::memory_order_acquire);
+                lk.unlock();
+                const Clock::time_point until = Clock::now() + std::chrono::microseconds(kSpinUs);
+                while (srv->submit_seq.load(std::memory_order_acquire) == seen && Clock::now() < until) cpu_relax();
+                lk.lock();
+                srv->cv_sched.wait(lk, ready);
+            }
             if (srv->stop) {
                 std::vector<std::shared_ptr<Request>> rest(srv->queue.begin(), srv->queue.end());
                 srv->queue.clear();
@@ -221,15 +260,40 @@ void scheduler_loop(gsmat_server *srv) {
                 srv->sched_done = true;
                 srv->cv_done.notify_all();
                 srv->cv_comp.notify_all();
-                srv->cv_lone.notify_all();
+                srv->cv_lane.notify_all();
                 return;
+            }
+            // a request that found the queue empty goes to an idle direct lane
+            if (srv->queue.size() == 1) {
+                gsmat_server::Lane *L = idle_lane();
+                const double b = srv->queue.front()->est_bytes;
+                const bool fits = srv->inflight_bytes + b <= (double)srv->cfg.budget_bytes;
+                if (L && (fits || (srv->inflight.empty() && srv->launching == 0 && srv->inflight_bytes == 0))) {
+                    std::shared_ptr<Request> r = srv->queue.front();
+                    srv->queue.pop_front();
+                    srv->inflight_bytes += b;
+                    r->state = REQ_RUNNING;
+                    L->req = r;
+                    L->bytes = b;
+                    L->pending.store(1, std::memory_order_release);
+                    srv->cv_lane.notify_all();
+                    continue;
+                }
+                if (srv->free_slots.empty()) {
+                    // the lane cannot take it yet (budget) and no slot is free
+                    const uint64_t seen = srv->finished_batches;
+                    srv->cv_sched.wait(lk, [&] { return srv->stop || srv->finished_batches != seen; });
+                    continue;
+                }
             }
             // admission: arrival order, under the budget; a request larger
             // than the whole budget runs alone when nothing else is in flight
+            bool lanes_busy = false;
+            for (auto &L : srv->lanes) lanes_busy = lanes_busy || L->req != nullptr;
             while (!srv->queue.empty() && (int)take.size() < srv->cfg.max_batch) {
                 const double b = srv->queue.front()->est_bytes;
                 const bool fits = srv->inflight_bytes + bytes + b <= (double)srv->cfg.budget_bytes;
-                const bool alone = take.empty() && srv->inflight.empty() && srv->launching == 0 && !srv->lone_req;
+                const bool alone = take.empty() && srv->inflight.empty() && srv->launching == 0 && !lanes_busy;
                 if (!fits && !alone) break;
                 take.push_back(srv->queue.front());
                 srv->queue.pop_front();
@@ -240,16 +304,6 @@ void scheduler_loop(gsmat_server *srv) {
                 // budget exhausted: wait for a micro-batch to finish
                 const uint64_t seen = srv->finished_batches;
                 srv->cv_sched.wait(lk, [&] { return srv->stop || srv->finished_batches != seen; });
-                continue;
-            }
-            if (!srv->cfg.batch_lone && take.size() == 1 && !srv->lone_req && srv->inflight.empty() &&
-                srv->launching == 0 && srv->gap_us > kLoneGapUs) {
-                // admitted alone on an idle device: the lone lane runs it
-                srv->inflight_bytes += bytes;
-                take[0]->state = REQ_RUNNING;
-                srv->lone_req = take[0];
-                srv->lone_bytes = bytes;
-                srv->cv_lone.notify_one();
                 continue;
             }
             srv->inflight_bytes += bytes;
@@ -374,7 +428,8 @@ int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_se
     if (c.batch.block == 0) c.batch.block = 512;
     if (c.batch.ctas_per_sm == 0) c.batch.ctas_per_sm = 1;
     if (c.batch.arena_bytes == 0) c.batch.arena_bytes = (int64_t)8 << 30;
-    if (c.slots > 64 || c.max_batch > (1 << 20)) {
+    if (c.lanes <= 0) c.lanes = 2;
+    if (c.slots > 64 || c.max_batch > (1 << 20) || c.lanes > 64) {
         delete srv;
         return set_error(GSMAT_ERR_INVALID_ARG, "server slots or max_batch out of range");
     }
@@ -384,11 +439,18 @@ int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_se
     }
     srv->cfg = c;
     cudaGetDevice(&srv->device);
-    if (cudaStreamCreateWithFlags(&srv->prep_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&srv->lone_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        if (srv->prep_stream) cudaStreamDestroy(srv->prep_stream);
+    if (cudaStreamCreateWithFlags(&srv->prep_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete srv;
         return set_error(GSMAT_ERR_CUDA, "server stream");
+    }
+    const int n_lanes = c.batch_lone ? 0 : c.lanes;
+    for (int k = 0; k < n_lanes; ++k) {
+        srv->lanes.push_back(std::make_unique<gsmat_server::Lane>());
+        if (cudaStreamCreateWithFlags(&srv->lanes.back()->st, cudaStreamNonBlocking) != cudaSuccess) {
+            srv->lanes.back()->st = nullptr;
+            server_destroy(srv);
+            return set_error(GSMAT_ERR_CUDA, "server lane stream");
+        }
     }
     srv->res.resize(c.slots);
     for (int k = 0; k < c.slots; ++k) {
@@ -407,7 +469,7 @@ int server_create(const gsmat_store *S, const gsmat_server_config *cfg, gsmat_se
     }
     srv->sched = std::thread(scheduler_loop, srv);
     srv->comp = std::thread(completion_loop, srv);
-    srv->lone = std::thread(lone_loop, srv);
+    for (auto &L : srv->lanes) L->th = std::thread(lane_loop, srv, L.get());
     *out = srv;
     return GSMAT_OK;
 }
@@ -423,15 +485,11 @@ int server_submit(gsmat_server *srv, const gsmat_pattern *pats, int n_pats, int 
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop) return set_error(GSMAT_ERR_INVALID_ARG, "server is shutting down");
     r->ticket = srv->next_ticket++;
-    if (r->ticket > 1) {
-        const double gap = std::chrono::duration<double, std::micro>(r->t_submit - srv->last_submit).count();
-        srv->gap_us = srv->gap_us >= 1e9 ? gap : 0.875 * srv->gap_us + 0.125 * gap;
-    }
-    srv->last_submit = r->t_submit;
     srv->reqs[r->ticket] = r;
     srv->queue.push_back(r);
     srv->stats.submitted++;
     *ticket = r->ticket;
+    srv->submit_seq.fetch_add(1, std::memory_order_release);
     srv->cv_sched.notify_one();
     return GSMAT_OK;
 }
@@ -523,14 +581,16 @@ void server_destroy(gsmat_server *srv) {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->sched_done = true;  // also when the scheduler never started
     }
-    // the completion thread and the lone lane drain what they hold, then exit
+    // the completion thread and the direct lanes drain what they hold, then exit
     srv->cv_comp.notify_all();
-    srv->cv_lone.notify_all();
+    srv->cv_lane.notify_all();
     if (srv->comp.joinable()) srv->comp.join();
-    if (srv->lone.joinable()) srv->lone.join();
-    if (srv->lone_stream) {
-        cudaStreamSynchronize(srv->lone_stream);
-        cudaStreamDestroy(srv->lone_stream);
+    for (auto &L : srv->lanes) {
+        if (L->th.joinable()) L->th.join();
+        if (L->st) {
+            cudaStreamSynchronize(L->st);
+            cudaStreamDestroy(L->st);
+        }
     }
     srv->reqs.clear();
     for (BatchResources &r : srv->res) {

@@ -106,9 +106,9 @@ def test_close_with_pending_work(gs, tiny):
     srv.close()  # finishes what is in flight, fails the rest, does not hang
 
 
-def test_lone_requests_take_the_plain_path(gs, tiny):
-    # sparse arrivals (2 ms apart), one at a time on an idle device: each
-    # runs as gsmat_query on the lone lane's stream, with the same result
+def test_sparse_requests_take_a_direct_lane(gs, tiny):
+    # sparse arrivals (2 ms apart), each finding the queue empty: each runs
+    # as gsmat_query on a direct lane's stream, with the same result
     import time
 
     S, items, alone = tiny
@@ -125,3 +125,28 @@ def test_lone_requests_take_the_plain_path(gs, tiny):
     st = srv.stats()
     assert st["direct"] == 20 and st["batches"] == 0 and st["completed"] == 20
     srv.close()
+
+
+def test_burst_splits_between_lanes_and_micro_batches(gs, tiny):
+    """A burst: the first requests find idle lanes, the ones queued behind
+    them form micro-batches; every result is the one alone."""
+    import time
+
+    S, items, alone = tiny
+    srv = gs.Server(S, max_batch=16, slots=2, lanes=3)
+    tickets = []
+    for p, v in items[:3]:  # spaced out: each finds the queue empty
+        time.sleep(0.003)
+        tickets.append(srv.submit(p, v))
+    tickets += [srv.submit(p, v) for p, v in items[3:]]  # back to back: they queue up
+    for t in tickets:
+        assert srv.wait(t)
+    for t, want in zip(tickets, alone):
+        assert np.array_equal(srv.to_numpy(t), want)
+        srv.release(t)
+    st = srv.stats()
+    assert st["completed"] == len(items) and st["failed"] == 0
+    assert st["direct"] >= 1 and st["batches"] >= 1
+    srv.close()
+    with pytest.raises(gs.GsmatError):
+        gs.Server(S, lanes=65)
