@@ -310,6 +310,10 @@ typedef struct {
                              GSMAT_SORT_CARRY or GSMAT_SORT_GATHER as for gsmat_sort_rows) */
     int32_t plan_cost;    /* 0: plan every query by Alg. 1; 1: by least estimated cost, as
                              GSMAT_PLAN_COST (the results are the same) */
+    int32_t expand_slots; /* tile shape of the kernel's expand loop: output slots per thread per
+                             round, 1 (a search per slot) or 4 (a search per 4 consecutive slots,
+                             the next parents found by stepping forward); 0: 1 */
+    int32_t _pad;
 } gsmat_batch_config;
 
 typedef struct {
@@ -363,12 +367,40 @@ GSMAT_API int gsmat_batch_stats(const gsmat_batch *batch, gsmat_batch_stats_t *s
 
 GSMAT_API void gsmat_batch_free(gsmat_batch *batch);
 
-/* Autotuner of the persistent kernel's CTA shape: times every (block,
- * ctas_per_sm) in {128, 256, 512} x {1, 2, 4, 8} (at most 2048 threads per
- * SM) on the given sample batch and writes the fastest into *best (the other
- * fields come from base, which may be NULL).  Synchronises `stream`. */
+/* Autotuner of the persistent kernel's shape: times every (block,
+ * ctas_per_sm, expand_slots) in {128, 256, 512} x {1, 2, 4, 8} x {1, 4} (at
+ * most 2048 threads per SM) on the given sample batch and writes the fastest
+ * into *best (the other fields come from base, which may be NULL).
+ * Synchronises `stream`. */
 GSMAT_API int gsmat_batch_autotune(const gsmat_store *store, const gsmat_bgp *bgps, int32_t n,
                                    const gsmat_batch_config *base, gsmat_stream_t stream, gsmat_batch_config *best);
+
+/* Tile shapes of the plain path's join kernels on one store (the paper has
+ * no counterpart: these are this library's kernel parameters). */
+typedef struct {
+    int32_t expand_items; /* output slots + parent rows per CTA of the expand (Alg. 3) and
+                             product kernels, the size of their merge-path pieces: 512, 1024,
+                             2048 (default), 4096 or 8192 */
+    int32_t short_row;    /* the membership filter (Alg. 3, other join variables) searches the
+                             subject's row directly when it has at most this many entries, else
+                             the shorter of the subject's and the object's rows: 1..4096
+                             (default 64) */
+} gsmat_tiles;
+
+/* Set / read a store's tile shapes.  Setting them while queries run on the
+ * store is not allowed.  Results never depend on them.  Returns
+ * GSMAT_ERR_INVALID_ARG for values outside the ranges above. */
+GSMAT_API int gsmat_store_set_tiles(gsmat_store *store, const gsmat_tiles *tiles);
+GSMAT_API int gsmat_store_get_tiles(const gsmat_store *store, gsmat_tiles *tiles);
+
+/* Autotuner of the tile shapes: runs the n BGPs (a sample of the expected
+ * workload) under the default shape and every shape of expand_items in
+ * {512, ..., 8192} x short_row in {16, 64, 256}, each once to warm up and
+ * twice timed with CUDA events on `stream`, keeps the fastest on the store
+ * and writes it to *best (ties keep the default).  Synchronises `stream`;
+ * no query may run on the store meanwhile. */
+GSMAT_API int gsmat_store_tune(gsmat_store *store, const gsmat_bgp *bgps, int32_t n, gsmat_stream_t stream,
+                               gsmat_tiles *best);
 
 /* ------------------------------------------------------------------------ */
 /* Served evaluation: continuous batching over a resident store              */
@@ -382,10 +414,13 @@ typedef struct {
                               requests (0: 120 GiB) */
     gsmat_batch_config batch; /* kernel shape and caps of every micro-batch (zeros: block 512,
                                  1 CTA/SM, arena up to 8 GiB sized from the estimates) */
-    int32_t batch_lone;    /* 0: a request admitted alone while nothing else is in flight runs
-                              on the plain path (as gsmat_query, on its slot's stream), which
-                              has the lower latency on an idle device; 1: micro-batch it too */
-    int32_t _pad;
+    int32_t batch_lone;    /* 0: a request that finds the queue empty goes to an idle direct
+                              lane, which runs it on the plain path (as gsmat_query, on the
+                              lane's own stream and thread): under light load every request
+                              starts at once on multi-CTA steps, and only requests that queue
+                              up behind busy lanes form micro-batches; 1: no lanes, every
+                              request is micro-batched */
+    int32_t lanes;         /* direct lanes (0: 2) */
 } gsmat_server_config;
 
 typedef struct {
@@ -400,16 +435,19 @@ typedef struct {
     int64_t direct;         /* requests admitted alone and run on the plain path */
 } gsmat_server_stats_t;
 
-/* Start a server (two host threads) over a store, which must outlive it.
- * A scheduler admits queued requests in arrival order into a micro-batch
- * whenever a slot is free and their estimated bytes (the accumulated
- * intermediate-size estimate of Sec. 6.2 times the row width) fit in the
- * unclaimed budget; a request larger than the whole budget runs alone.
- * Each micro-batch is planned and run as by gsmat_batch_prepare/execute on
- * its own stream, so micro-batches overlap on the device; a completion
- * thread finishes each as its device work ends.  A request admitted alone
- * while nothing else is in flight runs on the plain path instead (see
- * batch_lone). */
+/* Start a server over a store, which must outlive it (host threads: a
+ * scheduler, a completion thread and `lanes` direct lanes).  A request that
+ * finds the queue empty goes to an idle direct lane, which runs it on the
+ * plain path (see batch_lone).  Otherwise the scheduler admits queued
+ * requests in arrival order into a micro-batch whenever a slot is free and
+ * their estimated bytes (the accumulated intermediate-size estimate of
+ * Sec. 6.2 times the row width) fit in the unclaimed budget; a request
+ * larger than the whole budget runs alone.  Each micro-batch is planned and
+ * run as by gsmat_batch_prepare/execute on its own stream, so micro-batches
+ * (and the lanes' queries) overlap on the device; a completion thread
+ * finishes each as its device work ends.  The scheduler and the lanes spin
+ * up to 2 ms on their next event before blocking, so at a few hundred
+ * requests per second and more no request waits for a thread wake-up. */
 GSMAT_API int gsmat_server_create(const gsmat_store *store, const gsmat_server_config *cfg, gsmat_server **out);
 
 /* Queue one BGP (copied; validated as gsmat_query) and return its ticket at

@@ -79,7 +79,10 @@ __device__ __forceinline__ int64_t cta_scan(CtaShared<BLOCK> &sm, int64_t v, int
     return block_exclusive_sum<BLOCK>(v, sm.scan, total);
 }
 
-template <int BLOCK>
+// EPT: output slots per thread per round of the expand loop (a tile shape
+// the autotuner picks): one search per EPT consecutive slots, the next
+// parents found by stepping forward.
+template <int BLOCK, int EPT>
 __device__ void run_query(const BatchArgs &a, CtaShared<BLOCK> &sm, int q) {
     const BQuery &Q = a.queries[q];
     const int tid = threadIdx.x;
@@ -97,6 +100,73 @@ __device__ void run_query(const BatchArgs &a, CtaShared<BLOCK> &sm, int q) {
         const int64_t n = sm.rows;
         const int k = sm.ncols;
         const bool unit = (n == 1 && k == 0);
+        if (S.kind == GSMAT_STEP_FUSED) continue;  // applied by the INTERSECT before it
+        if (S.kind == GSMAT_STEP_INTERSECT) {
+            // count the intersections (a warp per row), offsets by a running
+            // CTA scan, then each warp writes its rows' matches
+            const PredSide pa = S.a_side == 0 ? p0 : p1;
+            const PredSide pb = a.sides[S.f_side * a.n_pred + S.f_slot];
+            const SideView &sva = a.sv.side[S.a_side];
+            const SideView &svb = a.sv.side[S.f_side];
+            const int32_t *x = sm.col[S.a_side == 0 ? S.s_col : S.o_col];
+            const int32_t *bc = S.b_col >= 0 ? sm.col[S.b_col] : nullptr;
+            int32_t *tmp = cta_alloc(a, sm, sizeof(int32_t) * (size_t)(2 * n + 2));
+            if (!tmp) {
+                if (tid == 0) sm.status = BR_OVERFLOW;
+                __syncthreads();
+                break;
+            }
+            int32_t *cnt = tmp;      // n
+            int32_t *off = tmp + n;  // n + 1
+            const int warp = tid >> 5;
+            constexpr int kWarps = BLOCK / 32;
+            for (int64_t i = warp; i < n; i += kWarps) {
+                const int c = warp_intersect(sva, pa, x[i], svb, pb, bc ? bc[i] : S.b_const, [](int, int32_t) {});
+                if ((tid & 31) == 0) cnt[i] = c;
+            }
+            __syncthreads();
+            int64_t carry = 0;
+            for (int64_t base = 0; base < n; base += BLOCK) {
+                const int64_t i = base + tid;
+                const int c = i < n ? cnt[i] : 0;
+                int64_t tot;
+                const int64_t ex = cta_scan(sm, c, &tot);
+                if (i < n && carry + ex <= a.max_rows) off[i] = (int32_t)(carry + ex);
+                carry += tot;
+                if (carry > a.max_rows) break;  // uniform
+            }
+            if (carry > a.max_rows) {
+                if (tid == 0) sm.status = BR_OVERFLOW;
+                __syncthreads();
+                break;
+            }
+            if (tid == 0) off[n] = (int32_t)carry;
+            const int64_t total = carry;
+            int32_t *out = total > 0 ? cta_alloc(a, sm, sizeof(int32_t) * (size_t)total * (k + 1)) : nullptr;
+            if (total > 0 && !out) {
+                if (tid == 0) sm.status = BR_OVERFLOW;
+                __syncthreads();
+                break;
+            }
+            __syncthreads();
+            for (int64_t i = warp; i < n; i += kWarps) {
+                const int64_t o0 = off[i];
+                if (off[i + 1] == o0) continue;  // warp-uniform
+                warp_intersect(sva, pa, x[i], svb, pb, bc ? bc[i] : S.b_const, [&](int r, int32_t v) {
+                    const int64_t j = o0 + r;
+                    for (int c = 0; c < k; ++c) out[(size_t)c * total + j] = sm.col[c][i];
+                    out[(size_t)k * total + j] = v;
+                });
+            }
+            __syncthreads();
+            if (tid == 0) {
+                for (int c = 0; c <= k; ++c) sm.col[c] = out + (size_t)c * total;
+                sm.ncols = k + 1;
+                sm.rows = total;
+            }
+            __syncthreads();
+            continue;
+        }
         if (S.kind == GSMAT_STEP_FILTER) {
             int32_t *out = k > 0 ? cta_alloc(a, sm, sizeof(int32_t) * (size_t)n * k) : nullptr;
             if (k > 0 && !out) {
@@ -174,15 +244,21 @@ __device__ void run_query(const BatchArgs &a, CtaShared<BLOCK> &sm, int q) {
             }
             __syncthreads();
             const int32_t *val = sv.val;
-            for (int64_t j = tid; j < total; j += BLOCK) {
-                // parent: largest r with off[r] <= j
+            for (int64_t jg = (int64_t)tid * EPT; jg < total; jg += (int64_t)BLOCK * EPT) {
+                // parent of jg: largest r with off[r] <= jg
                 int64_t lo = 0, hi = n - 1;
                 while (lo < hi) {
                     const int64_t mid = (lo + hi + 1) >> 1;
-                    if (off[mid] <= j) lo = mid; else hi = mid - 1;
+                    if (off[mid] <= jg) lo = mid; else hi = mid - 1;
                 }
-                for (int c = 0; c < k; ++c) out[(size_t)c * total + j] = sm.col[c][lo];
-                out[(size_t)k * total + j] = val[fst[lo] + (j - off[lo])];
+#pragma unroll
+                for (int t = 0; t < EPT; ++t) {
+                    const int64_t j = jg + t;
+                    if (j >= total) break;
+                    while (lo + 1 < n && off[lo + 1] <= j) ++lo;
+                    for (int c = 0; c < k; ++c) out[(size_t)c * total + j] = sm.col[c][lo];
+                    out[(size_t)k * total + j] = val[fst[lo] + (j - off[lo])];
+                }
             }
             __syncthreads();
             if (tid == 0) {
@@ -357,7 +433,7 @@ __device__ void run_query(const BatchArgs &a, CtaShared<BLOCK> &sm, int q) {
     }
 }
 
-template <int BLOCK>
+template <int BLOCK, int EPT>
 __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs a) {
     __shared__ CtaShared<BLOCK> sm;
     while (true) {
@@ -366,7 +442,7 @@ __global__ void __launch_bounds__(BLOCK) batch_kernel(BatchArgs a) {
         const int q = sm.q;
         __syncthreads();
         if (q >= a.n_queries) break;
-        run_query<BLOCK>(a, sm, q);
+        run_query<BLOCK, EPT>(a, sm, q);
         __syncthreads();
     }
 }
@@ -511,13 +587,17 @@ int launch_seg_gather(const SegDesc *segs, int n_segs, int64_t total, const uint
     return GSMAT_OK;
 }
 
-int launch_batch_kernel(const BatchArgs &a, int block, int grid, cudaStream_t st) {
+int launch_batch_kernel(const BatchArgs &a, int block, int expand_slots, int grid, cudaStream_t st) {
+    const bool four = expand_slots == 4;
     if (block == 128) {
-        batch_kernel<128><<<grid, 128, 0, st>>>(a);
+        if (four) batch_kernel<128, 4><<<grid, 128, 0, st>>>(a);
+        else batch_kernel<128, 1><<<grid, 128, 0, st>>>(a);
     } else if (block == 512) {
-        batch_kernel<512><<<grid, 512, 0, st>>>(a);
+        if (four) batch_kernel<512, 4><<<grid, 512, 0, st>>>(a);
+        else batch_kernel<512, 1><<<grid, 512, 0, st>>>(a);
     } else {
-        batch_kernel<256><<<grid, 256, 0, st>>>(a);
+        if (four) batch_kernel<256, 4><<<grid, 256, 0, st>>>(a);
+        else batch_kernel<256, 1><<<grid, 256, 0, st>>>(a);
     }
     GS_LAUNCH_CHECK();
     return GSMAT_OK;

@@ -19,6 +19,14 @@ struct BStep {
     int32_t c_first;   // EXPAND from a constant: entry range of its row
     int32_t c_last;
     int32_t swap;      // CROSS of M_p: take it by object, columns (o, s)
+    // GSMAT_STEP_INTERSECT: an EXPAND from a bound variable whose new
+    // variable a later FILTER ties to a variable bound before it (or a
+    // constant); that FILTER's step has kind GSMAT_STEP_FUSED.
+    int32_t a_side;    // side of the EXPAND's row (0: by subject, 1: by object)
+    int32_t f_slot;    // the filter's predicate slot
+    int32_t f_side;    // side of the filter's row (1 when the new variable is its subject)
+    int32_t b_col;     // column of the filter's other end (-1: the constant b_const)
+    int32_t b_const;
 };
 
 struct BQuery {
@@ -56,7 +64,8 @@ struct BatchArgs {
     int64_t max_rows;        // per table; larger tables send the query to the plain path
 };
 
-int launch_batch_kernel(const BatchArgs &a, int block, int grid, cudaStream_t st);
+// expand_slots: output slots per thread per round of the expand loop (1 or 4)
+int launch_batch_kernel(const BatchArgs &a, int block, int expand_slots, int grid, cudaStream_t st);
 
 // Host resources a batch may borrow instead of creating its own (a server
 // keeps one set per in-flight slot and reuses it): a stream, four events and

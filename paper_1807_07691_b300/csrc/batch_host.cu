@@ -81,6 +81,7 @@ gsmat_batch_config default_config() {
     c.arena_bytes = (int64_t)8 << 30;
     c.max_rows = (int64_t)1 << 22;
     c.use_graph = 1;
+    c.expand_slots = 1;
     return c;
 }
 
@@ -96,6 +97,10 @@ int resolve_config(const gsmat_batch_config *in, gsmat_batch_config *out) {
         if (c.compact_results) c.use_graph = 0;  // the arena is re-allocated per run
         c.reorder_mode = in->reorder_mode;
         c.plan_cost = in->plan_cost;
+        if (in->expand_slots) c.expand_slots = in->expand_slots;
+    }
+    if (c.expand_slots != 1 && c.expand_slots != 4) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "bad batch expand_slots %d (1 or 4)", c.expand_slots);
     }
     if (c.plan_cost != 0 && c.plan_cost != 1) {
         return set_error(GSMAT_ERR_INVALID_ARG, "bad batch plan_cost %d (0 or 1)", c.plan_cost);
@@ -137,7 +142,7 @@ BatchArgs make_args(gsmat_batch *B) {
 int enqueue_device_work(gsmat_batch *B) {
     GS_CUDA(cudaMemsetAsync(B->ctrl.p, 0, 2 * sizeof(unsigned long long), B->priv));
     BatchArgs a = make_args(B);
-    GS_TRY(launch_batch_kernel(a, B->cfg.block, B->grid, B->priv));
+    GS_TRY(launch_batch_kernel(a, B->cfg.block, B->cfg.expand_slots, B->grid, B->priv));
     GS_CUDA(cudaMemcpyAsync(B->results_host, B->results_dev.p, sizeof(BResult) * B->n, cudaMemcpyDeviceToHost,
                             B->priv));
     GS_CUDA(cudaMemcpyAsync(B->ctrl_host, B->ctrl.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, B->priv));
@@ -267,6 +272,38 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
         Q.n_steps = np;
         Q.n_vars = bgps[i].n_vars;
         Q.absent = absent[i];
+        // intersect-expand fusion, as on the plain path: an EXPAND of a new
+        // variable v from a bound variable and a later FILTER joining v with
+        // a variable bound before the EXPAND (or a constant) run as one step
+        std::vector<int> partner(np, -1);
+        std::vector<char> fused(np, 0);
+        {
+            uint64_t bound = 0;
+            for (int s = 0; s < np; ++s) {
+                const gsmat_pattern &p = P[order[s]];
+                const bool from_var = (kinds[s] == GSMAT_STEP_EXPAND_S && p.s_var) ||
+                                      (kinds[s] == GSMAT_STEP_EXPAND_O && p.o_var);
+                if (from_var && !fused[s]) {
+                    const int32_t v = kinds[s] == GSMAT_STEP_EXPAND_S ? p.o : p.s;
+                    for (int t = s + 1; t < np; ++t) {
+                        if (kinds[t] != GSMAT_STEP_FILTER || fused[t]) continue;
+                        const gsmat_pattern &f = P[order[t]];
+                        if (f.s_var && f.o_var && f.s == f.o) continue;
+                        const bool v_is_s = f.s_var && f.s == v;
+                        const bool v_is_o = f.o_var && f.o == v;
+                        if (v_is_s == v_is_o) continue;
+                        const bool other_known = v_is_s ? (!f.o_var || ((bound >> f.o) & 1))
+                                                        : (!f.s_var || ((bound >> f.s) & 1));
+                        if (!other_known) continue;
+                        partner[s] = t;
+                        fused[t] = 1;
+                        break;
+                    }
+                }
+                if (p.s_var) bound |= uint64_t(1) << p.s;
+                if (p.o_var) bound |= uint64_t(1) << p.o;
+            }
+        }
         int col_of_var[32];
         for (int v = 0; v < 32; ++v) col_of_var[v] = -1;
         int ncols = 0;
@@ -277,6 +314,23 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
             BStep S1;
             memset(&S1, 0, sizeof(S1));
             S1.kind = kinds[s];
+            if (fused[s]) {
+                S1.kind = GSMAT_STEP_FUSED;  // runs inside the INTERSECT before it
+                B->hs.push_back(S1);
+                continue;
+            }
+            if (partner[s] >= 0) {
+                const gsmat_pattern &f = P[order[partner[s]]];
+                const int32_t v = S1.kind == GSMAT_STEP_EXPAND_S ? p.o : p.s;
+                const bool v_is_s = f.s_var && f.s == v;
+                const bool b_var = v_is_s ? f.o_var : f.s_var;
+                const int32_t b = v_is_s ? f.o : f.s;
+                S1.a_side = S1.kind == GSMAT_STEP_EXPAND_S ? 0 : 1;
+                S1.f_slot = slot[i][order[partner[s]]];
+                S1.f_side = v_is_s ? 1 : 0;
+                S1.b_col = b_var ? col_of_var[b] : -1;
+                S1.b_const = b_var ? 0 : b;
+            }
             S1.slot = slot[i][k] < 0 ? 0 : slot[i][k];
             S1.s_col = (p.s_var && col_of_var[p.s] >= 0) ? col_of_var[p.s] : -1;
             S1.o_col = (p.o_var && col_of_var[p.o] >= 0) ? col_of_var[p.o] : -1;
@@ -307,6 +361,7 @@ int prepare(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const gsmat_
                     pv.push_back(second);
                 }
             }
+            if (partner[s] >= 0) S1.kind = GSMAT_STEP_INTERSECT;
             B->hs.push_back(S1);
         }
         for (int v = 0; v < Q.n_vars; ++v) Q.col_of_var[v] = col_of_var[v];
@@ -568,6 +623,7 @@ int finish(gsmat_batch *B) {
     s.arena_used = (int64_t)std::min<unsigned long long>(B->ctrl_host[1], (unsigned long long)B->arena.bytes);
     s.block = B->cfg.block;
     s.grid = B->grid;
+    for (const BStep &st : B->hs) s.n_intersect += st.kind == GSMAT_STEP_INTERSECT ? 1 : 0;
     GS_CUDA(cudaEventRecord(B->ev_a, B->priv));
     GS_TRY(reorder_large_results(B));
     GS_CUDA(cudaEventRecord(B->ev_b, B->priv));
@@ -727,27 +783,33 @@ int batch_autotune(const gsmat_store *S, const gsmat_bgp *bgps, int32_t n, const
     GS_TRY(batch_prepare(S, bgps, n, &cfg, st, &B));
     const int blocks[3] = {128, 256, 512};
     const int per_sm[4] = {1, 2, 4, 8};
+    const int slots[2] = {1, 4};
     float best_ms = 3.4e38f;
     gsmat_batch_config pick = cfg;
     int rc = GSMAT_OK;
     for (int b : blocks) {
         for (int c : per_sm) {
             if (b * c > 2048) continue;  // threads per SM
-            B->cfg.block = b;
-            B->cfg.ctas_per_sm = c;
-            B->grid = device_sm_count() * c;
-            float t_min = 3.4e38f;
-            for (int rep = 0; rep < 3 && rc == GSMAT_OK; ++rep) {
-                float ms = 0;
-                rc = run_device(B, &ms);
-                if (rc == GSMAT_OK && rep > 0) t_min = std::min(t_min, ms);
+            for (int e : slots) {
+                B->cfg.block = b;
+                B->cfg.ctas_per_sm = c;
+                B->cfg.expand_slots = e;
+                B->grid = device_sm_count() * c;
+                float t_min = 3.4e38f;
+                for (int rep = 0; rep < 3 && rc == GSMAT_OK; ++rep) {
+                    float ms = 0;
+                    rc = run_device(B, &ms);
+                    if (rc == GSMAT_OK && rep > 0) t_min = std::min(t_min, ms);
+                }
+                if (rc != GSMAT_OK) break;
+                if (t_min < best_ms) {
+                    best_ms = t_min;
+                    pick.block = b;
+                    pick.ctas_per_sm = c;
+                    pick.expand_slots = e;
+                }
             }
             if (rc != GSMAT_OK) break;
-            if (t_min < best_ms) {
-                best_ms = t_min;
-                pick.block = b;
-                pick.ctas_per_sm = c;
-            }
         }
         if (rc != GSMAT_OK) break;
     }

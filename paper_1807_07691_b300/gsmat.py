@@ -75,7 +75,8 @@ class BGPStruct(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
                 ("max_rows", ctypes.c_int64), ("use_graph", ctypes.c_int32), ("compact_results", ctypes.c_int32),
-                ("reorder_mode", ctypes.c_int32), ("plan_cost", ctypes.c_int32)]
+                ("reorder_mode", ctypes.c_int32), ("plan_cost", ctypes.c_int32), ("expand_slots", ctypes.c_int32),
+                ("_pad", ctypes.c_int32)]
 
 
 class BatchStats(ctypes.Structure):
@@ -86,9 +87,13 @@ class BatchStats(ctypes.Structure):
                 ("_pad", ctypes.c_int32)]
 
 
+class Tiles(ctypes.Structure):
+    _fields_ = [("expand_items", ctypes.c_int32), ("short_row", ctypes.c_int32)]
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32), ("budget_bytes", ctypes.c_int64),
-                ("batch", BatchConfig), ("batch_lone", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+                ("batch", BatchConfig), ("batch_lone", ctypes.c_int32), ("lanes", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -165,6 +170,9 @@ def _load():
         "gsmat_exclusive_scan_i32_noalloc": ([vp, vp, i64, vp], c_int),
         "gsmat_exclusive_scan_i32_noalloc_max": ([], i64),
         "gsmat_selftest_wait_expiry": ([i32, vp], c_int),
+        "gsmat_store_set_tiles": ([vp, vp], c_int),
+        "gsmat_store_get_tiles": ([vp, vp], c_int),
+        "gsmat_store_tune": ([vp, vp, i32, vp, vp], c_int),
         "gsmat_profile_enable": ([c_int], c_int),
         "gsmat_profile_read": ([vp, i32, P(i32), c_int], c_int),
         "gsmat_launch_count": ([], i64),
@@ -399,6 +407,24 @@ class Store:
                                        ent.ctypes.data, _stream_ptr(stream)))
         return rid[:nr], ptr, ent[: st["nnz"]]
 
+    def tiles(self) -> dict:
+        """The store's tile shapes (gsmat_store_get_tiles)."""
+        t = Tiles()
+        _check(_lib.gsmat_store_get_tiles(self._h, ctypes.byref(t)))
+        return {"expand_items": t.expand_items, "short_row": t.short_row}
+
+    def set_tiles(self, expand_items: int = 2048, short_row: int = 64):
+        t = Tiles(int(expand_items), int(short_row))
+        _check(_lib.gsmat_store_set_tiles(self._h, ctypes.byref(t)))
+
+    def tune(self, bgps, stream=None) -> dict:
+        """Autotune the tile shapes on a sample of BGPs (gsmat_store_tune);
+        the fastest is kept on the store and returned."""
+        arr, keep = _bgp_array(bgps)
+        t = Tiles()
+        _check(_lib.gsmat_store_tune(self._h, arr, len(bgps), _stream_ptr(stream), ctypes.byref(t)))
+        return {"expand_items": t.expand_items, "short_row": t.short_row}
+
     @staticmethod
     def marshal(bgp, n_vars=None):
         """Pre-converted arguments for query_raw: (patterns, n, n_vars)."""
@@ -597,6 +623,7 @@ def _config(cfg):
     c.compact_results = int(cfg.get("compact_results", 0))
     c.reorder_mode = int(cfg.get("reorder_mode", 0))
     c.plan_cost = int(cfg.get("plan_cost", 0))
+    c.expand_slots = int(cfg.get("expand_slots", 0))
     return c
 
 
@@ -681,12 +708,13 @@ class Server:
     """Continuous-batching server over a resident store (gsmat_server_*)."""
 
     def __init__(self, store: "Store", max_batch: int = 0, slots: int = 0, budget_bytes: int = 0,
-                 batch: dict | None = None, batch_lone: bool = False):
+                 batch: dict | None = None, batch_lone: bool = False, lanes: int = 0):
         c = ServerConfig()
         c.max_batch = max_batch
         c.slots = slots
         c.budget_bytes = budget_bytes
         c.batch_lone = 1 if batch_lone else 0
+        c.lanes = lanes
         bc = _config(batch)
         if bc is not None:
             c.batch = bc
@@ -753,7 +781,8 @@ def batch_autotune(store: "Store", bgps, base: dict | None = None, stream=None) 
     _check(_lib.gsmat_batch_autotune(store.handle, arr, len(bgps), ctypes.byref(cfg) if cfg else None,
                                      _stream_ptr(stream), ctypes.byref(best)))
     return {"block": best.block, "ctas_per_sm": best.ctas_per_sm, "arena_bytes": best.arena_bytes,
-            "max_rows": best.max_rows, "use_graph": best.use_graph, "plan_cost": best.plan_cost}
+            "max_rows": best.max_rows, "use_graph": best.use_graph, "plan_cost": best.plan_cost,
+            "expand_slots": best.expand_slots}
 
 
 def plan(bgp, keys, stats, n_vars=None, cost: bool = False):

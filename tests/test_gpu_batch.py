@@ -135,7 +135,7 @@ def test_batch_autotune(gs, tiny):
     t, ix, S, qs = tiny
     cfg = gs.batch_autotune(S, qs)
     assert cfg["block"] in (128, 256, 512) and cfg["ctas_per_sm"] in (1, 2, 4, 8)
-    assert cfg["block"] * cfg["ctas_per_sm"] <= 2048
+    assert cfg["block"] * cfg["ctas_per_sm"] <= 2048 and cfg["expand_slots"] in (1, 4)
     B = gs.Batch(S, qs, config=cfg).execute()
     for i, q in enumerate(qs):
         assert np.array_equal(B.to_numpy(i), ix.query(q))
@@ -170,3 +170,45 @@ def test_batched_mix_on_medium_matches_plain_path(gs, reorder_mode, plan_cost):
         a = B.to_numpy(i)
         b = S.query(q).to_numpy()
         assert a.shape == b.shape and np.array_equal(a, b), q.name
+
+
+def test_whole_batched_mix_matches_plain_path_and_oracle(gs):
+    """All 4096 queries of the batched mix (medium graph) in one batch: every
+    result equals the plain path's; every 8th also equals the oracle's rows;
+    the mix's cycles run as intersect-expand steps inside the kernel."""
+    import torch
+
+    t = synth.make_graph("medium")
+    qs = synth.make_batched_queries(4096)
+    S = gs.Store(torch.from_numpy(np.array(t, copy=True)).cuda())
+    B = gs.Batch(S, qs).execute()
+    st = B.stats()
+    assert st["n_queries"] == 4096 and st["n_intersect"] > 0
+    ix = oracle.OracleIndex(t)
+    n_oracle = 0
+    for i, q in enumerate(qs):
+        a = B.to_numpy(i)
+        b = S.query(q).to_numpy()
+        assert a.shape == b.shape and np.array_equal(a, b), q.name
+        if i % 8 == 0:
+            try:
+                want = ix.query(q, row_limit=20_000_000)
+            except oracle.OracleError:
+                continue
+            assert np.array_equal(a, want), q.name
+            n_oracle += 1
+    assert n_oracle >= 480
+
+
+@pytest.mark.parametrize("block,expand_slots", [(128, 4), (512, 4), (256, 1)])
+def test_batch_expand_tile_shapes(gs, tiny, block, expand_slots):
+    """Both expand tile shapes the autotuner chooses between give the
+    oracle's rows, with every block size."""
+    t, ix, S, qs = tiny
+    items = [(q.patterns, q.n_vars) for q in qs] + _mixed_bgps(t, 60, 31 + block + expand_slots)
+    items = [it for it in items if _small(ix, it)]
+    B = gs.Batch(S, [p for p, _ in items], n_vars_list=[v for _, v in items],
+                 config={"block": block, "expand_slots": expand_slots}).execute()
+    _check_all(B, items, ix)
+    with pytest.raises(gs.GsmatError):
+        gs.Batch(S, qs, config={"expand_slots": 3})
