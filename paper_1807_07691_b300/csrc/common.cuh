@@ -429,6 +429,10 @@ int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
                    int *err_word = nullptr);
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
                    int *err_word = nullptr);
+// Keys only, with the caller's second buffer `alt` (n words): *sorted is
+// set to whichever of keys / alt holds the sorted keys (no copy back).
+int radix_sort_u64_pingpong(uint64_t *keys, uint64_t *alt, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
+                            int *err_word, uint64_t **sorted);
 // As radix_sort_u64 with a 64-bit payload (required).
 int radix_sort_u64_wide(uint64_t *keys, uint64_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
                         int *err_word = nullptr);

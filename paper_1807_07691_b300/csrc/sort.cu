@@ -524,10 +524,7 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
-        if (lane == leader) {
-            base = wh[d];
-            wh[d] = base + (uint32_t)__popc(peers);
-        }
+        if (lane == leader) base = atomicAdd(&wh[d], (uint32_t)__popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
         dr[j] = ((base + (uint32_t)__popc(peers & lt_mask)) << 8) | (uint32_t)d;
         __syncwarp();
@@ -617,13 +614,14 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
         }
         atomicExch(desc + (int64_t)tile * kBins + d, desc_pack(epoch, kDescPrefix, excl + real));
     }
-    if (dig) gbase[d] = (uint32_t)excl;
+    // global position of the tile's first key of digit d, minus that key's
+    // place in the staged tile: key i of digit d goes to gdelta[d] + i
+    if (dig) gbase[d] = (uint32_t)excl - (uint32_t)ts;
     __syncthreads();
     for (int i = threadIdx.x; i < valid; i += kPassBlock) {
         const K kk = skeys[i];
         const int dd = digit_of(kk, shift, mask);
-        const uint32_t dst = gbase[dd] + ((uint32_t)i - tstart[dd]);
-        sink.store(dst, kk, HasVals ? svals[i] : V(0));
+        sink.store(gbase[dd] + (uint32_t)i, kk, HasVals ? svals[i] : V(0));
     }
 }
 
@@ -716,18 +714,22 @@ struct SortMeta {
     }
 };
 
+// With alt_keys given, it is the second key buffer (nothing allocated for
+// it) and *sorted_out receives whichever buffer holds the result (no copy
+// back); otherwise the result is copied back into keys / vals.
 template <class K, bool HasVals, class V = uint32_t>
-int sort_passes(K *keys, V *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word) {
+int sort_passes(K *keys, V *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st, int *err_word,
+                K *alt_keys = nullptr, K **sorted_out = nullptr) {
     using SA = SrcArray<K, HasVals, V>;
     using KA = SinkArray<K, HasVals, V>;
     const int n_pass = (end_bit - begin_bit + 7) / 8;
     SortMeta meta;
     GS_TRY(meta.make(n, n_pass, kPassBlock * items_per_thread<K, HasVals, V>(), st, err_word));
     DevBuf alt_k, alt_v;
-    GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
+    if (!alt_keys) GS_TRY(alt_k.alloc(sizeof(K) * (size_t)n, st));
     if (HasVals) GS_TRY(alt_v.alloc(sizeof(V) * (size_t)n, st));
     GS_TRY((launch_histogram<K, SA>(SA{keys, vals}, n, begin_bit, end_bit, n_pass, meta.hist, st)));
-    K *src_k = keys, *dst_k = alt_k.as<K>();
+    K *src_k = keys, *dst_k = alt_keys ? alt_keys : alt_k.as<K>();
     V *src_v = vals, *dst_v = alt_v.as<V>();
     for (int p = 0; p < n_pass; ++p) {
         const int shift = begin_bit + 8 * p;
@@ -738,7 +740,9 @@ int sort_passes(K *keys, V *vals, int64_t n, int begin_bit, int end_bit, cudaStr
         K *tk = src_k; src_k = dst_k; dst_k = tk;
         V *tv = src_v; src_v = dst_v; dst_v = tv;
     }
-    if (src_k != keys) {
+    if (sorted_out) {
+        *sorted_out = src_k;
+    } else if (src_k != keys) {
         GS_CUDA(cudaMemcpyAsync(keys, src_k, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, st));
         if (HasVals) GS_CUDA(cudaMemcpyAsync(vals, src_v, sizeof(V) * (size_t)n, cudaMemcpyDeviceToDevice, st));
     }
@@ -803,6 +807,22 @@ int radix_sort_u64(uint64_t *keys, uint32_t *vals, int64_t n, int begin_bit, int
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
                    int *err_word) {
     return radix_sort_impl<uint32_t>(keys, vals, n, begin_bit, end_bit, st, "radix_sort_u32", err_word);
+}
+
+int radix_sort_u64_pingpong(uint64_t *keys, uint64_t *alt, int64_t n, int begin_bit, int end_bit, cudaStream_t st,
+                            int *err_word, uint64_t **sorted) {
+    if (n < 0 || !sorted || begin_bit < 0 || end_bit > 64 || begin_bit > end_bit) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "radix sort: bad arguments");
+    }
+    *sorted = keys;
+    if (n <= 1 || begin_bit == end_bit) return GSMAT_OK;
+    if (n > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "radix sort: n = %lld >= 2^32", (long long)n);
+    const int n_pass = (end_bit - begin_bit + 7) / 8;
+    KernelTimer t("radix_sort_u64", st, (double)n * 16.0 * n_pass, (double)n);
+    GS_TRY((sort_passes<uint64_t, false>(keys, static_cast<uint32_t *>(nullptr), n, begin_bit, end_bit, st, err_word,
+                                         alt, sorted)));
+    t.stop();
+    return GSMAT_OK;
 }
 
 int radix_sort_u64_wide(uint64_t *keys, uint64_t *vals, int64_t n, int begin_bit, int end_bit, cudaStream_t st,

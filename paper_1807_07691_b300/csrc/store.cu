@@ -136,6 +136,17 @@ __global__ void split_kernel(const int32_t *__restrict__ tri, int64_t n, const i
     }
 }
 
+// key = slot << (2 bits) | s << bits | o, straight from the triples
+__global__ void split_pack_kernel(const int32_t *__restrict__ tri, int64_t n, const int32_t *__restrict__ hkeys,
+                                  const int32_t *__restrict__ hvals, uint32_t hmask, int bits,
+                                  uint64_t *__restrict__ keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = (uint32_t)tri[3 * i], o = (uint32_t)tri[3 * i + 2];
+        const uint32_t slot = (uint32_t)hash_lookup(hkeys, hvals, hmask, tri[3 * i + 1]);
+        keys[i] = ((uint64_t)slot << (2 * bits)) | ((uint64_t)s << bits) | (uint64_t)o;
+    }
+}
+
 // key = slot << (2 bits) | a << bits | b
 __global__ void pack_kernel(const int32_t *__restrict__ a, const int32_t *__restrict__ b, const int32_t *__restrict__ c,
                             int64_t n, int bits, uint64_t *__restrict__ keys) {
@@ -197,6 +208,25 @@ struct DedupeOp {
     }
 };
 
+// Distinct keys of a sorted (slot, s, o) key array: side 0's columns (key
+// = s, val = o, slot) and side 1's key (slot, o, s), in one pass.
+struct DedupeKeysOp {
+    const uint64_t *keys;
+    int32_t *s0, *o0, *slot0;
+    uint64_t *k1;
+    int bits;
+    __device__ bool flag(int64_t i) const { return i == 0 || keys[i] != keys[i - 1]; }
+    __device__ void emit(int64_t i, int64_t j) const {
+        const uint64_t k = keys[i];
+        const uint64_t m = (1ull << bits) - 1;
+        const uint64_t o = k & m, s = (k >> bits) & m, slot = k >> (2 * bits);
+        s0[j] = (int32_t)s;
+        o0[j] = (int32_t)o;
+        slot0[j] = (int32_t)slot;
+        k1[j] = (slot << (2 * bits)) | (o << bits) | s;
+    }
+};
+
 // Non-zero rows: the first entry of every (slot, key) run.
 struct RowStartOp {
     const int32_t *key, *slot;
@@ -221,9 +251,14 @@ __global__ void pred_bounds_kernel(const int32_t *__restrict__ rowslot, const in
 
 // Dense row pointers of several predicates in one launch:
 // dense[dense_base + x] = first entry of row x (or of the next non-empty
-// row) for x in [0, max_entity + 1].  A warp fills kDenseChunk consecutive
-// x of one predicate: two binary searches bound the rows of the chunk, then
-// each lane searches its x inside that range and the writes are coalesced.
+// row) for x in [0, max_entity + 1].  The x of every predicate are cut into
+// chunks of kDenseChunk, and a warp takes kDenseRun consecutive chunks: one
+// binary search finds the first row of the run, then per chunk the warp
+// reads the chunk's row ids 32 at a time (coalesced; a ballot tells where
+// the chunk ends, so the next chunk starts there), marks them in shared
+// memory with their first entries, and an exclusive scan of the marks gives
+// every x the number of the chunk's rows below it -- the index of its row's
+// first entry; the writes are coalesced.
 struct DensePart {
     int32_t row_base;
     int32_t nrows;
@@ -233,6 +268,8 @@ struct DensePart {
     int64_t chunk0;     // first chunk of this predicate
 };
 constexpr int kDenseChunk = 256;
+constexpr int kDenseRun = 16;  // consecutive chunks per warp
+constexpr int kDenseWarps = kThreads / 32;
 
 __device__ __forceinline__ int lower_bound_i32(const int32_t *__restrict__ a, int lo, int hi, int64_t x) {
     while (lo < hi) {
@@ -242,29 +279,86 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *__restrict__ a, in
     return lo;
 }
 
-__global__ void dense_fill_kernel(const int32_t *__restrict__ rowid, const int32_t *__restrict__ rowoff,
-                                  const DensePart *__restrict__ parts, int n_parts, int64_t n_chunks, int64_t len,
-                                  int32_t *__restrict__ dense) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
-        int lo = 0, hi = n_parts;  // last part whose chunk0 <= c
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (parts[mid].chunk0 <= c) lo = mid; else hi = mid;
-        }
-        const DensePart P = parts[lo];
-        const int64_t x0 = (c - P.chunk0) * kDenseChunk;
-        const int32_t *ids = rowid + P.row_base;
-        const int r0 = lower_bound_i32(ids, 0, P.nrows, x0);
-        const int r1 = lower_bound_i32(ids, r0, P.nrows, x0 + kDenseChunk);
-#pragma unroll 4
-        for (int k = 0; k < kDenseChunk / 32; ++k) {
-            const int64_t x = x0 + lane + 32 * k;
-            if (x < len) {
-                const int r = lower_bound_i32(ids, r0, r1, x);
-                dense[P.dense_base + x] = r < P.nrows ? __ldg(rowoff + P.row_base + r) : P.end_entry;
+__global__ void __launch_bounds__(kThreads) dense_fill_kernel(const int32_t *__restrict__ rowid,
+                                                              const int32_t *__restrict__ rowoff,
+                                                              const DensePart *__restrict__ parts, int n_parts,
+                                                              int64_t n_chunks, int64_t len,
+                                                              int32_t *__restrict__ dense) {
+    __shared__ int32_t s_off[kDenseWarps][kDenseChunk + 1];  // first entries of the chunk's rows (+ the next row)
+    __shared__ int16_t s_pre[kDenseWarps][kDenseChunk];      // marks, then their exclusive prefix
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t *off = s_off[wid];
+    int16_t *pre = s_pre[wid];
+    const int64_t warps = (int64_t)gridDim.x * kDenseWarps;
+    const int64_t n_runs = (n_chunks + kDenseRun - 1) / kDenseRun;
+    for (int64_t run = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; run < n_runs; run += warps) {
+        int part = -1;
+        int r0 = 0;
+        DensePart P{};
+        for (int64_t c = run * kDenseRun; c < n_chunks && c < (run + 1) * kDenseRun; ++c) {
+            if (part < 0 || c >= P.chunk0 + (len + kDenseChunk - 1) / kDenseChunk) {
+                int lo = 0, hi = n_parts;  // last part whose chunk0 <= c
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (parts[mid].chunk0 <= c) lo = mid; else hi = mid;
+                }
+                part = lo;
+                P = parts[lo];
+                r0 = lower_bound_i32(rowid + P.row_base, 0, P.nrows, (c - P.chunk0) * kDenseChunk);
             }
+            const int64_t x0 = (c - P.chunk0) * kDenseChunk;
+            const int32_t *ids = rowid + P.row_base;
+            const int32_t *ro = rowoff + P.row_base;
+            for (int m = lane; m < kDenseChunk; m += 32) pre[m] = 0;
+            __syncwarp();
+            // the chunk's rows: [r0, r1)
+            int r1 = r0;
+            for (int i = 0;; i += 32) {
+                const int r = r0 + i + lane;
+                const int64_t id = r < P.nrows ? (int64_t)__ldg(ids + r) : INT64_MAX;
+                const bool in = id < x0 + kDenseChunk;
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    pre[id - x0] = 1;
+                    off[i + lane] = __ldg(ro + r);
+                }
+                if (m != 0xffffffffu) {
+                    r1 = r0 + i + __popc(m);
+                    break;
+                }
+            }
+            if (lane == 0) off[r1 - r0] = r1 < P.nrows ? __ldg(ro + r1) : P.end_entry;
+            __syncwarp();
+            // exclusive prefix of the marks: lane l holds x0 + 8 l .. 8 l + 7
+            int v[kDenseChunk / 32];
+            int sum = 0;
+#pragma unroll
+            for (int t = 0; t < kDenseChunk / 32; ++t) {
+                v[t] = pre[lane * (kDenseChunk / 32) + t];
+                sum += v[t];
+            }
+            int inc = sum;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += y;
+            }
+            int run_sum = inc - sum;
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kDenseChunk / 32; ++t) {
+                pre[lane * (kDenseChunk / 32) + t] = (int16_t)run_sum;
+                run_sum += v[t];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < kDenseChunk / 32; ++k) {
+                const int xi = lane + 32 * k;
+                const int64_t x = x0 + xi;
+                if (x < len) dense[P.dense_base + x] = off[pre[xi]];
+            }
+            __syncwarp();
+            r0 = r1;
         }
     }
 }
@@ -398,7 +492,8 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
         GS_TRY(d_parts.alloc(sizeof(DensePart) * parts.size(), st));
         GS_CUDA(cudaMemcpyAsync(d_parts.p, parts.data(), sizeof(DensePart) * parts.size(), cudaMemcpyHostToDevice, st));
         const int64_t n_chunks = per * (int64_t)parts.size();
-        int64_t g = (n_chunks * 32 + kThreads - 1) / kThreads;
+        const int64_t n_runs = (n_chunks + kDenseRun - 1) / kDenseRun;
+        int64_t g = (n_runs * 32 + kThreads - 1) / kThreads;
         const int64_t cap = (int64_t)device_sm_count() * 16;
         if (g > cap) g = cap;
         dense_fill_kernel<<<(unsigned)g, kThreads, 0, st>>>(S->rowid[side].as<int32_t>(), S->rowoff[side].as<int32_t>(),
@@ -409,6 +504,123 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     }
     S->key[side] = std::move(key);
     S->val[side] = std::move(val);
+    return GSMAT_OK;
+}
+
+// Both sides from (slot, s, o) columns, for ids too wide for one packed key
+// (the sorts then run as two stable passes over narrower keys).
+int build_columns(gsmat_store *S, const int32_t *tri, int64_t n, int id_bits, int slot_bits, DevBuf &d_tri_own,
+                  int *err, cudaStream_t st, PhaseTimer &pt, int64_t *h) {
+    // 3. side 0: sort by (slot, s, o) and drop repeats
+    DevBuf s_raw, o_raw, slot_raw, s_sorted, o_sorted, slot_sorted, cnt;
+    GS_TRY(s_raw.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(o_raw.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(slot_raw.alloc(sizeof(int32_t) * (size_t)n, st));
+    {
+        const uint32_t cap = S->hash_mask + 1;
+        split_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, S->hash_dev.as<int32_t>(), S->hash_dev.as<int32_t>() + cap,
+                                                       S->hash_mask, s_raw.as<int32_t>(), o_raw.as<int32_t>(),
+                                                       slot_raw.as<int32_t>());
+        GS_LAUNCH_CHECK();
+    }
+    d_tri_own.release();
+    GS_TRY(s_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(o_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(slot_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(sort_rows3(s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>(), n, id_bits, slot_bits, false,
+                      s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(), st, err));
+    // dedupe into the raw buffers (reused)
+    GS_TRY(cnt.alloc(sizeof(int64_t), st));
+    {
+        DedupeOp op{s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(),
+                    s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>()};
+        GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
+        GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        pt.pause();
+        GS_CUDA(cudaStreamSynchronize(st));
+        pt.resume();
+    }
+    const int64_t nu = h[0];
+    S->n_unique = nu;
+    pt.add_bytes(8.0 * (double)nu);  // the two sides' entry columns
+    // side 0 arrays: key = s, val = o (exact size)
+    DevBuf key0, val0, slot0;
+    GS_TRY(key0.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(val0.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(slot0.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_CUDA(cudaMemcpyAsync(key0.p, s_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(val0.p, o_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(slot0.p, slot_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
+    s_raw.release(); o_raw.release(); slot_raw.release();
+    // 4. side 1: sort the unique triples by (slot, o, s); they are sorted by
+    // (slot, s, o), so a stable sort on (slot, o) keeps s ascending
+    DevBuf key1, val1, slot1;
+    GS_TRY(key1.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)nu, st));
+    GS_TRY(sort_rows3(val0.as<int32_t>(), key0.as<int32_t>(), slot0.as<int32_t>(), nu, id_bits, slot_bits, true,
+                      key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st, err));
+    s_sorted.release(); o_sorted.release(); slot_sorted.release();
+    // 5. rows, predicate bounds, dense row pointers
+    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err, st, pt));
+    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err, st, pt));
+    return GSMAT_OK;
+}
+
+// Both sides from one packed key per triple when (slot, s, o) fits 64 bits:
+// sort by (slot, s, o); one selection pass drops repeats, writes side 0's
+// columns and side 1's key (slot, o, s); a stable sort of that key on
+// (slot, o) leaves s ascending inside every row (its input is in (slot, s)
+// order).  The sorts ping-pong between two key buffers, never copying back.
+int build_packed(gsmat_store *S, const int32_t *tri, int64_t n, int id_bits, int slot_bits, DevBuf &d_tri_own,
+                 int *err, cudaStream_t st, PhaseTimer &pt, int64_t *h) {
+    DevBuf ka, kb, cnt;
+    GS_TRY(ka.alloc(sizeof(uint64_t) * (size_t)n, st));
+    GS_TRY(kb.alloc(sizeof(uint64_t) * (size_t)n, st));
+    {
+        const uint32_t cap = S->hash_mask + 1;
+        split_pack_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, S->hash_dev.as<int32_t>(),
+                                                            S->hash_dev.as<int32_t>() + cap, S->hash_mask, id_bits,
+                                                            ka.as<uint64_t>());
+        GS_LAUNCH_CHECK();
+    }
+    d_tri_own.release();
+    const int key_bits = slot_bits + 2 * id_bits;
+    uint64_t *sorted0 = nullptr;
+    GS_TRY(radix_sort_u64_pingpong(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, key_bits, st, err, &sorted0));
+    uint64_t *k1 = sorted0 == ka.as<uint64_t>() ? kb.as<uint64_t>() : ka.as<uint64_t>();
+    // side 0 columns sized n (an upper bound of the distinct count)
+    DevBuf key0, val0, slot0;
+    GS_TRY(key0.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(val0.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(slot0.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(cnt.alloc(sizeof(int64_t), st));
+    {
+        DedupeKeysOp op{sorted0, key0.as<int32_t>(), val0.as<int32_t>(), slot0.as<int32_t>(), k1, id_bits};
+        GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
+        GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        pt.pause();
+        GS_CUDA(cudaStreamSynchronize(st));
+        pt.resume();
+    }
+    const int64_t nu = h[0];
+    S->n_unique = nu;
+    pt.add_bytes(8.0 * (double)nu);  // the two sides' entry columns
+    uint64_t *sorted1 = nullptr;
+    GS_TRY(radix_sort_u64_pingpong(k1, sorted0, nu, id_bits, key_bits, st, err, &sorted1));
+    DevBuf key1, val1, slot1;
+    GS_TRY(key1.alloc(sizeof(int32_t) * (size_t)(nu > 0 ? nu : 1), st));
+    GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)(nu > 0 ? nu : 1), st));
+    GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)(nu > 0 ? nu : 1), st));
+    if (nu > 0) {
+        unpack_kernel<<<grid_for(nu), kThreads, 0, st>>>(sorted1, nu, id_bits, key1.as<int32_t>(), val1.as<int32_t>(),
+                                                         slot1.as<int32_t>());
+        GS_LAUNCH_CHECK();
+    }
+    ka.release();
+    kb.release();
+    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err, st, pt));
+    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err, st, pt));
     return GSMAT_OK;
 }
 
@@ -508,59 +720,11 @@ int build_impl(const int32_t *triples, int64_t n, int on_device, cudaStream_t st
     }
     const int id_bits = std::max(1, bits_for((uint64_t)S->max_entity));
     const int slot_bits = bits_for((uint64_t)(S->n_pred - 1));
-    // 3. side 0: sort by (slot, s, o) and drop repeats
-    DevBuf s_raw, o_raw, slot_raw, s_sorted, o_sorted, slot_sorted, cnt;
-    GS_TRY(s_raw.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(o_raw.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(slot_raw.alloc(sizeof(int32_t) * (size_t)n, st));
-    {
-        const uint32_t cap = S->hash_mask + 1;
-        split_kernel<<<grid_for(n), kThreads, 0, st>>>(tri, n, S->hash_dev.as<int32_t>(), S->hash_dev.as<int32_t>() + cap,
-                                                       S->hash_mask, s_raw.as<int32_t>(), o_raw.as<int32_t>(),
-                                                       slot_raw.as<int32_t>());
-        GS_LAUNCH_CHECK();
+    if (slot_bits + 2 * id_bits <= 64) {
+        GS_TRY(build_packed(S, tri, n, id_bits, slot_bits, d_tri_own, err.as<int>(), st, pt, h));
+    } else {
+        GS_TRY(build_columns(S, tri, n, id_bits, slot_bits, d_tri_own, err.as<int>(), st, pt, h));
     }
-    d_tri_own.release();
-    GS_TRY(s_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(o_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(slot_sorted.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(sort_rows3(s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>(), n, id_bits, slot_bits, false,
-                      s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(), st, err.as<int>()));
-    // dedupe into the raw buffers (reused)
-    GS_TRY(cnt.alloc(sizeof(int64_t), st));
-    {
-        DedupeOp op{s_sorted.as<int32_t>(), o_sorted.as<int32_t>(), slot_sorted.as<int32_t>(),
-                    s_raw.as<int32_t>(), o_raw.as<int32_t>(), slot_raw.as<int32_t>()};
-        GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err.as<int>()));
-        GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        pt.pause();
-        GS_CUDA(cudaStreamSynchronize(st));
-        pt.resume();
-    }
-    const int64_t nu = h[0];
-    S->n_unique = nu;
-    pt.add_bytes(8.0 * (double)nu);  // the two sides' entry columns
-    // side 0 arrays: key = s, val = o (exact size)
-    DevBuf key0, val0, slot0;
-    GS_TRY(key0.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_TRY(val0.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_TRY(slot0.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_CUDA(cudaMemcpyAsync(key0.p, s_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(val0.p, o_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(slot0.p, slot_raw.p, sizeof(int32_t) * (size_t)nu, cudaMemcpyDeviceToDevice, st));
-    s_raw.release(); o_raw.release(); slot_raw.release();
-    // 4. side 1: sort the unique triples by (slot, o, s); they are sorted by
-    // (slot, s, o), so a stable sort on (slot, o) keeps s ascending
-    DevBuf key1, val1, slot1;
-    GS_TRY(key1.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)nu, st));
-    GS_TRY(sort_rows3(val0.as<int32_t>(), key0.as<int32_t>(), slot0.as<int32_t>(), nu, id_bits, slot_bits, true,
-                      key1.as<int32_t>(), val1.as<int32_t>(), slot1.as<int32_t>(), st, err.as<int>()));
-    s_sorted.release(); o_sorted.release(); slot_sorted.release();
-    // 5. rows, predicate bounds, dense row pointers
-    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err.as<int>(), st, pt));
-    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err.as<int>(), st, pt));
     // device copy of the per-predicate tables
     {
         const size_t P = (size_t)S->n_pred;
