@@ -385,6 +385,38 @@ GSMAT_API int gsmat_exclusive_scan_i32_noalloc(const int32_t *d_in, int64_t *d_o
 
 GSMAT_API int64_t gsmat_exclusive_scan_i32_noalloc_max(void) { return gs::exclusive_scan_i32_noalloc_max(); }
 
+GSMAT_API int gsmat_store_set_tiles(gsmat_store *store, const gsmat_tiles *tiles) {
+    gs::clear_error();
+    if (!store || !tiles) return gs::set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    gs::TileConfig tc;
+    tc.expand_items = tiles->expand_items;
+    tc.short_row = tiles->short_row;
+    GS_TRY(gs::tile_config_check(tc));
+    store->tiles = tc;
+    return GSMAT_OK;
+}
+
+GSMAT_API int gsmat_store_get_tiles(const gsmat_store *store, gsmat_tiles *tiles) {
+    gs::clear_error();
+    if (!store || !tiles) return gs::set_error(GSMAT_ERR_INVALID_ARG, "NULL argument");
+    tiles->expand_items = store->tiles.expand_items;
+    tiles->short_row = store->tiles.short_row;
+    return GSMAT_OK;
+}
+
+GSMAT_API int gsmat_store_tune(gsmat_store *store, const gsmat_bgp *bgps, int32_t n, gsmat_stream_t stream,
+                               gsmat_tiles *best) {
+    gs::clear_error();
+    if (!best) return gs::set_error(GSMAT_ERR_INVALID_ARG, "best is NULL");
+    gs::TileConfig tc;
+    const int rc = gs::store_tune(store, bgps, n, (cudaStream_t)stream, &tc);
+    gs::profile_flush();
+    if (rc != GSMAT_OK) return rc;
+    best->expand_items = tc.expand_items;
+    best->short_row = tc.short_row;
+    return GSMAT_OK;
+}
+
 GSMAT_API int gsmat_selftest_wait_expiry(int32_t poll_limit, gsmat_stream_t stream) {
     gs::clear_error();
     return gs::selftest_wait_expiry(poll_limit, (cudaStream_t)stream);

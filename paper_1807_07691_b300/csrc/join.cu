@@ -10,6 +10,8 @@
 // Rows whose other join variables must also match (Alg. 3, the "other join
 // variables" test) are kept by a membership filter with single-pass
 // prefix-sum compaction, which preserves row order.
+#include <atomic>
+
 #include "join.cuh"
 #include "select.cuh"
 
@@ -84,7 +86,6 @@ __global__ void __launch_bounds__(kCsBlock) count_scan_kernel(SideView sv, PredS
 // finds each slot's parent by a shared-memory binary search.
 
 constexpr int kExBlock = 256;
-constexpr int kExItems = 2048;  // rows + slots per CTA
 
 // Number of rows whose end off[r + 1] precedes output slot diag - a in the
 // merge, for the first `diag` merged items (rows win ties).
@@ -100,15 +101,16 @@ __device__ __forceinline__ int64_t merge_path(const int64_t *__restrict__ off, i
 }
 
 __global__ void expand_partition_kernel(const int64_t *__restrict__ off, int64_t n_rows, int64_t total, int64_t n_parts,
-                                        int64_t *__restrict__ cuts) {
+                                        int items, int64_t *__restrict__ cuts) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p > n_parts) return;
-    int64_t diag = p * kExItems;
+    int64_t diag = p * items;
     if (diag > n_rows + total) diag = n_rows + total;
     cuts[p] = merge_path(off, n_rows, total, diag);
 }
 
 struct ExpandArgs {
+    int items;           // rows + slots per CTA (dynamic shared memory sized for it)
     const int32_t *val;  // the side's entry array
     Cols in;
     int k;
@@ -120,11 +122,16 @@ struct ExpandArgs {
     OutCols out;
 };
 
+// Each thread writes groups of 4 consecutive output slots aligned to 4:
+// one binary search finds the group's first parent, the next slots step
+// forward through the offsets, and a group wholly inside the CTA's slab is
+// written with one 16-byte store per column (columns are 256-byte aligned).
 __global__ void __launch_bounds__(kExBlock) expand_kernel(ExpandArgs a) {
-    __shared__ int64_t soff[kExItems + 2];
-    __shared__ int32_t sfirst[kExItems + 1];
-    const int64_t d0 = (int64_t)blockIdx.x * kExItems;
-    const int64_t d1 = d0 + kExItems < a.n_in + a.total ? d0 + kExItems : a.n_in + a.total;
+    extern __shared__ __align__(16) unsigned char ex_smem[];
+    int64_t *soff = reinterpret_cast<int64_t *>(ex_smem);            // items + 2
+    int32_t *sfirst = reinterpret_cast<int32_t *>(soff + a.items + 2);  // items + 1
+    const int64_t d0 = (int64_t)blockIdx.x * a.items;
+    const int64_t d1 = d0 + a.items < a.n_in + a.total ? d0 + a.items : a.n_in + a.total;
     const int64_t r0 = __ldg(a.cuts + blockIdx.x);
     const int64_t r1 = __ldg(a.cuts + blockIdx.x + 1);
     const int64_t j0 = d0 - r0, j1 = d1 - r1;  // output slots [j0, j1)
@@ -137,16 +144,45 @@ __global__ void __launch_bounds__(kExBlock) expand_kernel(ExpandArgs a) {
     __syncthreads();
     const int k = a.k;
     const int32_t *__restrict__ val = a.val;
-    for (int64_t j = j0 + threadIdx.x; j < j1; j += kExBlock) {
-        // largest i in [0, nr) with soff[i] <= j
+    const int64_t g0 = j0 >> 2, g1 = (j1 + 3) >> 2;
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += kExBlock) {
+        const int64_t jb = g << 2;
+        const int64_t js = jb > j0 ? jb : j0;  // first slot of the group in the slab
+        // parent of js: largest i in [0, nr) with soff[i] <= js
         int lo = 0, hi = nr - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (soff[mid] <= j) lo = mid; else hi = mid - 1;
+            if (soff[mid] <= js) lo = mid; else hi = mid - 1;
         }
-        const int64_t r = r0 + lo;
-        for (int c = 0; c < k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + r);
-        a.out.c[k][j] = __ldg(val + sfirst[lo] + (j - soff[lo]));
+        int par[4];
+        int32_t nb[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t j = jb + t;
+            par[t] = lo;
+            nb[t] = 0;
+            if (j >= js && j < j1) {
+                while (lo + 1 < nr && soff[lo + 1] <= j) ++lo;
+                par[t] = lo;
+                nb[t] = __ldg(val + sfirst[lo] + (j - soff[lo]));
+            }
+        }
+        if (jb >= j0 && jb + 4 <= j1) {
+            for (int c = 0; c < k; ++c) {
+                const int32_t *col = a.in.c[c] + r0;
+                reinterpret_cast<int4 *>(a.out.c[c])[g] =
+                    make_int4(__ldg(col + par[0]), __ldg(col + par[1]), __ldg(col + par[2]), __ldg(col + par[3]));
+            }
+            reinterpret_cast<int4 *>(a.out.c[k])[g] = make_int4(nb[0], nb[1], nb[2], nb[3]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int64_t j = jb + t;
+                if (j < js || j >= j1) continue;
+                for (int c = 0; c < k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + r0 + par[t]);
+                a.out.c[k][j] = nb[t];
+            }
+        }
     }
 }
 
@@ -228,6 +264,7 @@ __global__ void __launch_bounds__(kPcBlock) product_count_scan_kernel(StoreView 
 }
 
 struct ProductArgs {
+    int items;  // rows + slots per CTA (dynamic shared memory sized for it)
     StoreView sv;
     ProdSpec spec;
     Cols in;
@@ -242,11 +279,31 @@ struct ProductArgs {
 };
 
 // Slots are partitioned as in expand_kernel (merge path of row ends and
-// slots, kExItems per CTA, the CTA's offsets staged in shared memory).
+// slots, kExItems per CTA, the CTA's offsets staged in shared memory) and
+// taken in groups of 4 aligned slots as there: one search per group, 16-byte
+// stores for a group wholly inside the slab.
+__device__ __forceinline__ int32_t product_value(const ProductArgs &a, const ProdFactor &f, int64_t r, uint32_t &q,
+                                                 int32_t *second) {
+    if (f.kind == kProdRow) {
+        const int64_t at = (int64_t)f.slot * a.n_in + r;
+        const uint32_t l = (uint32_t)__ldg(a.len + at);
+        const uint32_t qq = q / l;
+        const uint32_t idx = q - qq * l;
+        q = qq;
+        return __ldg(a.sv.side[f.side].val + __ldg(a.first + at) + idx);
+    }
+    const uint32_t qq = fastdiv_quot(q, f.div);
+    const uint32_t idx = q - qq * f.len;
+    q = qq;
+    if (f.kind == kProdPairs) *second = __ldg(f.b + idx);
+    return __ldg(f.a + idx);
+}
+
 __global__ void __launch_bounds__(kExBlock) product_kernel(ProductArgs a) {
-    __shared__ int64_t soff[kExItems + 2];
-    const int64_t d0 = (int64_t)blockIdx.x * kExItems;
-    const int64_t d1 = d0 + kExItems < a.n_in + a.total ? d0 + kExItems : a.n_in + a.total;
+    extern __shared__ __align__(16) unsigned char pr_smem[];
+    int64_t *soff = reinterpret_cast<int64_t *>(pr_smem);  // items + 2
+    const int64_t d0 = (int64_t)blockIdx.x * a.items;
+    const int64_t d1 = d0 + a.items < a.n_in + a.total ? d0 + a.items : a.n_in + a.total;
     const int64_t r0 = __ldg(a.cuts + blockIdx.x);
     const int64_t r1 = __ldg(a.cuts + blockIdx.x + 1);
     const int64_t j0 = d0 - r0, j1 = d1 - r1;
@@ -256,45 +313,95 @@ __global__ void __launch_bounds__(kExBlock) product_kernel(ProductArgs a) {
     for (int i = threadIdx.x; i <= nr; i += kExBlock) soff[i] = __ldg(a.off + r0 + i);
     __syncthreads();
     const int nf = a.spec.nf;
-    for (int64_t j = j0 + threadIdx.x; j < j1; j += kExBlock) {
+    const int64_t g0 = j0 >> 2, g1 = (j1 + 3) >> 2;
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += kExBlock) {
+        const int64_t jb = g << 2;
+        const int64_t js = jb > j0 ? jb : j0;
         int lo = 0, hi = nr - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (soff[mid] <= j) lo = mid; else hi = mid - 1;
+            if (soff[mid] <= js) lo = mid; else hi = mid - 1;
         }
-        const int64_t r = r0 + lo;
-        for (int c = 0; c < a.k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + r);
-        uint32_t q = (uint32_t)(j - soff[lo]);  // < N_r <= total < 2^32
-        for (int fi = nf - 1; fi >= 0; --fi) {
-            const ProdFactor &f = a.spec.f[fi];
-            if (f.kind == kProdRow) {
-                const int64_t at = (int64_t)f.slot * a.n_in + r;
-                const uint32_t l = (uint32_t)__ldg(a.len + at);
-                const uint32_t qq = q / l;
-                const uint32_t idx = q - qq * l;
-                q = qq;
-                a.out.c[f.out0][j] = __ldg(a.sv.side[f.side].val + __ldg(a.first + at) + idx);
-            } else {
-                const uint32_t qq = fastdiv_quot(q, f.div);
-                const uint32_t idx = q - qq * f.len;
-                q = qq;
-                a.out.c[f.out0][j] = __ldg(f.a + idx);
-                if (f.kind == kProdPairs) a.out.c[f.out0 + 1][j] = __ldg(f.b + idx);
+        int par[4];
+        uint32_t q0[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int64_t j = jb + t;
+            if (j >= js && j < j1) {
+                while (lo + 1 < nr && soff[lo + 1] <= j) ++lo;
+            }
+            par[t] = lo;
+            q0[t] = (uint32_t)(j - soff[lo]);  // < N_r <= total < 2^32 for the slab's slots
+        }
+        const bool full = jb >= j0 && jb + 4 <= j1;
+        if (full) {
+            for (int c = 0; c < a.k; ++c) {
+                const int32_t *col = a.in.c[c] + r0;
+                reinterpret_cast<int4 *>(a.out.c[c])[g] =
+                    make_int4(__ldg(col + par[0]), __ldg(col + par[1]), __ldg(col + par[2]), __ldg(col + par[3]));
+            }
+            uint32_t q[4] = {q0[0], q0[1], q0[2], q0[3]};
+            for (int fi = nf - 1; fi >= 0; --fi) {
+                const ProdFactor &f = a.spec.f[fi];
+                int32_t v[4], w[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) v[t] = product_value(a, f, r0 + par[t], q[t], &w[t]);
+                reinterpret_cast<int4 *>(a.out.c[f.out0])[g] = make_int4(v[0], v[1], v[2], v[3]);
+                if (f.kind == kProdPairs) reinterpret_cast<int4 *>(a.out.c[f.out0 + 1])[g] = make_int4(w[0], w[1], w[2], w[3]);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int64_t j = jb + t;
+                if (j < js || j >= j1) continue;
+                const int64_t r = r0 + par[t];
+                for (int c = 0; c < a.k; ++c) a.out.c[c][j] = __ldg(a.in.c[c] + r);
+                uint32_t q = q0[t];
+                for (int fi = nf - 1; fi >= 0; --fi) {
+                    const ProdFactor &f = a.spec.f[fi];
+                    int32_t w = 0;
+                    a.out.c[f.out0][j] = product_value(a, f, r, q, &w);
+                    if (f.kind == kProdPairs) a.out.c[f.out0 + 1][j] = w;
+                }
             }
         }
     }
 }
 
+// Row j of a product of fixed lists takes entry (j / inner_i) mod len_i of
+// factor i (inner_i = product of the lengths of the factors nested inside
+// it).  A thread writes 4 consecutive rows of every column with one 16-byte
+// store each (columns are 256-byte aligned); the last total mod 4 rows are
+// written one by one.
 __global__ void __launch_bounds__(256) product_fixed_kernel(ProdSpec spec, uint32_t total, OutCols out) {
     const int nf = spec.nf;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < (int64_t)total;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t q = (uint32_t)j;
-        for (int fi = nf - 1; fi >= 0; --fi) {
+    const int64_t n4 = (int64_t)(total >> 2);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += stride) {
+        const uint32_t j0 = (uint32_t)(g << 2);
+        for (int fi = 0; fi < nf; ++fi) {
             const ProdFactor &f = spec.f[fi];
-            const uint32_t qq = fastdiv_quot(q, f.div);
-            const uint32_t idx = q - qq * f.len;
-            q = qq;
+            int4 va, vb;
+            int32_t *pa = &va.x, *pb = &vb.x;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t q = fastdiv_quot(j0 + t, f.inner);
+                const uint32_t idx = q - fastdiv_quot(q, f.div) * f.len;
+                pa[t] = __ldg(f.a + idx);
+                if (f.kind == kProdPairs) pb[t] = __ldg(f.b + idx);
+            }
+            reinterpret_cast<int4 *>(out.c[f.out0])[g] = va;
+            if (f.kind == kProdPairs) reinterpret_cast<int4 *>(out.c[f.out0 + 1])[g] = vb;
+        }
+    }
+    const uint32_t rest = total & 3u;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < (int64_t)rest) {
+        const uint32_t j = (uint32_t)(n4 << 2) + (uint32_t)t;
+        for (int fi = 0; fi < nf; ++fi) {
+            const ProdFactor &f = spec.f[fi];
+            const uint32_t q = fastdiv_quot(j, f.inner);
+            const uint32_t idx = q - fastdiv_quot(q, f.div) * f.len;
             out.c[f.out0][j] = __ldg(f.a + idx);
             if (f.kind == kProdPairs) out.c[f.out0 + 1][j] = __ldg(f.b + idx);
         }
@@ -304,10 +411,8 @@ __global__ void __launch_bounds__(256) product_fixed_kernel(ProdSpec spec, uint3
 // ---------------------------------------------------------------------------
 // filter (membership test of (s, o) in the predicate) + compaction
 
-// Rows this short are searched directly, without looking up the other side.
-constexpr int kShortRow = 64;
-
 struct FilterOp {
+    int short_row;  // rows this short are searched directly, without looking up the other side
     SideView s0, s1;
     PredSide ps_s, ps_o;
     ValueSrc s, o;
@@ -319,7 +424,7 @@ struct FilterOp {
         const int2 a = row_range(s0, ps_s, x);
         const int la = a.y - a.x;
         if (la <= 0) return false;
-        if (la <= kShortRow) return sorted_contains(s0.val, a.x, a.y, y);
+        if (la <= short_row) return sorted_contains(s0.val, a.x, a.y, y);
         const int2 b = row_range(s1, ps_o, y);
         const int lb = b.y - b.x;
         if (lb <= 0) return false;
@@ -449,14 +554,48 @@ int launch_count_scan(const StoreView &sv, int side, const PredSide &ps, const i
     return GSMAT_OK;
 }
 
+// Dynamic shared memory of the expand / product kernels for `items` per CTA
+// (above the default 48 KB the limit is raised once per device).
+template <class Kernel>
+int prepare_items_smem(Kernel kernel, int items, size_t bytes, std::atomic<int> *done_bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (bytes > 48 * 1024 && done_bytes[dev].load(std::memory_order_acquire) < (int)bytes) {
+        GS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done_bytes[dev].store((int)bytes, std::memory_order_release);
+    }
+    (void)items;
+    return GSMAT_OK;
+}
+
+int tile_config_check(const TileConfig &tc) {
+    const int e = tc.expand_items;
+    if (e != 512 && e != 1024 && e != 2048 && e != 4096 && e != 8192) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "expand_items %d (512, 1024, 2048, 4096 or 8192)", e);
+    }
+    if (tc.short_row < 1 || tc.short_row > 4096) {
+        return set_error(GSMAT_ERR_INVALID_ARG, "short_row %d outside [1, 4096]", tc.short_row);
+    }
+    return GSMAT_OK;
+}
+
 int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t n_in, const int64_t *off,
-                  const int32_t *first, int64_t total, OutCols out, cudaStream_t st) {
+                  const int32_t *first, int64_t total, OutCols out, cudaStream_t st, const TileConfig &tc) {
     if (total <= 0 || n_in <= 0) return GSMAT_OK;
-    const int64_t n_parts = (n_in + total + kExItems - 1) / kExItems;
+    GS_TRY(tile_config_check(tc));
+    const int items = tc.expand_items;
+    const int64_t n_parts = (n_in + total + items - 1) / items;
     if (n_parts > INT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "expand into %lld rows", (long long)total);
+    for (int c = 0; c <= k; ++c) {
+        if (reinterpret_cast<uintptr_t>(out.c[c]) & 15u) {
+            return set_error(GSMAT_ERR_INVALID_ARG, "expand output column %d not 16-byte aligned", c);
+        }
+    }
     DevBuf cuts;
     GS_TRY(cuts.alloc(sizeof(int64_t) * (size_t)(n_parts + 1), st));
     ExpandArgs a;
+    a.items = items;
     a.val = sv.side[side].val;
     a.in = in;
     a.k = k;
@@ -471,10 +610,13 @@ int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t 
     // row, write k + 1 columns per output row.
     KernelTimer t("expand", st, (double)n_in * (4.0 * k + 8.0 + 4.0) + (double)total * (4.0 + 4.0 * (k + 1)),
                   (double)total);
-    expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts,
+    static std::atomic<int> smem_set[64];
+    const size_t smem = sizeof(int64_t) * (size_t)(items + 2) + sizeof(int32_t) * (size_t)(items + 1);
+    GS_TRY(prepare_items_smem(expand_kernel, items, smem, smem_set));
+    expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts, items,
                                                                                   cuts.as<int64_t>());
     GS_LAUNCH_CHECK();
-    expand_kernel<<<(unsigned)n_parts, kExBlock, 0, st>>>(a);
+    expand_kernel<<<(unsigned)n_parts, kExBlock, smem, st>>>(a);
     GS_LAUNCH_CHECK();
     t.stop();
     return GSMAT_OK;
@@ -508,13 +650,22 @@ static int product_out_cols(const ProdSpec &spec) {
 }
 
 int launch_product(const StoreView &sv, const ProdSpec &spec, const Cols &in, int k, int64_t n_in, const int64_t *off,
-                   const int32_t *first, const int32_t *len, int64_t total, OutCols out, cudaStream_t st) {
+                   const int32_t *first, const int32_t *len, int64_t total, OutCols out, cudaStream_t st,
+                   const TileConfig &tc) {
     if (total <= 0 || n_in <= 0) return GSMAT_OK;
+    GS_TRY(tile_config_check(tc));
+    const int items = tc.expand_items;
     if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
-    const int64_t n_parts = (n_in + total + kExItems - 1) / kExItems;
+    for (int c = 0; c < k + product_out_cols(spec); ++c) {
+        if (reinterpret_cast<uintptr_t>(out.c[c]) & 15u) {
+            return set_error(GSMAT_ERR_INVALID_ARG, "product output column %d not 16-byte aligned", c);
+        }
+    }
+    const int64_t n_parts = (n_in + total + items - 1) / items;
     DevBuf cuts;
     GS_TRY(cuts.alloc(sizeof(int64_t) * (size_t)(n_parts + 1), st));
     ProductArgs a;
+    a.items = items;
     a.sv = sv;
     a.spec = spec;
     a.in = in;
@@ -532,21 +683,36 @@ int launch_product(const StoreView &sv, const ProdSpec &spec, const Cols &in, in
     const int fc = product_out_cols(spec);
     KernelTimer t("product", st, (double)n_in * (4.0 * k + 8.0 + 8.0 * spec.nrow) + (double)total * (4.0 + 4.0 * (k + fc)),
                   (double)total);
-    expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts,
+    static std::atomic<int> smem_set[64];
+    const size_t smem = sizeof(int64_t) * (size_t)(items + 2);
+    GS_TRY(prepare_items_smem(product_kernel, items, smem, smem_set));
+    expand_partition_kernel<<<(unsigned)((n_parts + 1 + 255) / 256), 256, 0, st>>>(off, n_in, total, n_parts, items,
                                                                                   cuts.as<int64_t>());
     GS_LAUNCH_CHECK();
-    product_kernel<<<(unsigned)n_parts, kExBlock, 0, st>>>(a);
+    product_kernel<<<(unsigned)n_parts, kExBlock, smem, st>>>(a);
     GS_LAUNCH_CHECK();
     t.stop();
     return GSMAT_OK;
 }
 
-int launch_product_fixed(const ProdSpec &spec, int64_t total, OutCols out, cudaStream_t st) {
+int launch_product_fixed(const ProdSpec &spec_in, int64_t total, OutCols out, cudaStream_t st) {
     if (total <= 0) return GSMAT_OK;
     if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+    ProdSpec spec = spec_in;
+    uint64_t inner = 1;  // product of the lengths inside factor i (< 2^32: it divides total)
+    for (int i = spec.nf - 1; i >= 0; --i) {
+        spec.f[i].inner = make_fastdiv((uint32_t)inner);
+        inner *= spec.f[i].len;
+    }
+    for (int c = 0; c < kMaxCols; ++c) {
+        if (out.c[c] && (reinterpret_cast<uintptr_t>(out.c[c]) & 15u)) {
+            return set_error(GSMAT_ERR_INVALID_ARG, "product output column %d not 16-byte aligned", c);
+        }
+    }
     const int fc = product_out_cols(spec);
     KernelTimer t("product", st, (double)total * (4.0 + 4.0 * fc), (double)total);
-    int64_t g = (total + 255) / 256;
+    int64_t g = (total / 4 + 255) / 256;
+    if (g < 1) g = 1;
     const int64_t cap = (int64_t)device_sm_count() * 16;
     if (g > cap) g = cap;
     product_fixed_kernel<<<(unsigned)g, 256, 0, st>>>(spec, (uint32_t)total, out);
@@ -556,8 +722,11 @@ int launch_product_fixed(const ProdSpec &spec, int64_t total, OutCols out, cudaS
 }
 
 int launch_filter(const StoreView &sv, const PredSide &ps_s, const PredSide &ps_o, ValueSrc s, ValueSrc o,
-                  const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st) {
+                  const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st,
+                  const TileConfig &tc) {
+    GS_TRY(tile_config_check(tc));
     FilterOp op;
+    op.short_row = tc.short_row;
     op.s0 = sv.side[0];
     op.s1 = sv.side[1];
     op.ps_s = ps_s;

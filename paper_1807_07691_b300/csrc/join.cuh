@@ -15,6 +15,17 @@ struct OutCols {
     int32_t *c[kMaxCols];
 };
 
+// Tile shapes of the plain path's join kernels, chosen per store (by
+// gsmat_store_tune or gsmat_store_set_tiles): output slots plus parent rows
+// per CTA of the expand and product kernels (their merge-path pieces), and
+// the row length up to which the membership filter searches the subject's
+// row directly instead of looking at the object's row as well.
+struct TileConfig {
+    int expand_items = 2048;  // 512, 1024, 2048, 4096 or 8192
+    int short_row = 64;       // 1 .. 4096
+};
+int tile_config_check(const TileConfig &tc);
+
 // A value that comes from a table column or is a constant.
 struct ValueSrc {
     const int32_t *col;  // null -> constant
@@ -79,13 +90,15 @@ int launch_count_scan(const StoreView &sv, int side, const PredSide &ps, const i
 // off[r+1]) with its k columns copied, plus the new column
 // val[first_r + j - off[r]] appended as column k.
 int launch_expand(const StoreView &sv, int side, const Cols &in, int k, int64_t n_in, const int64_t *off,
-                  const int32_t *first, int64_t total, OutCols out, cudaStream_t st);
+                  const int32_t *first, int64_t total, OutCols out, cudaStream_t st,
+                  const TileConfig &tc = TileConfig());
 
 // Membership filter + compaction: keep row i iff (s_i, o_i) is an entry of
 // the predicate (s_i, o_i from columns or constants); surviving rows' k
 // columns are written in order to `out`; *d_count = survivors.
 int launch_filter(const StoreView &sv, const PredSide &ps_s, const PredSide &ps_o, ValueSrc s, ValueSrc o,
-                  const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st);
+                  const Cols &in, int k, int64_t n_in, OutCols out, int64_t *d_count, int *err, cudaStream_t st,
+                  const TileConfig &tc = TileConfig());
 
 // Intersect-expand, count phase: counts[i] = |row(a_i) of predicate side
 // (side_a, pa)  intersected with  row(b_i) of (side_b, pb)|.
@@ -154,6 +167,7 @@ struct ProdFactor {
     const int32_t *b;  // kProdPairs: second column
     uint32_t len;      // kProdList / kProdPairs: length
     FastDiv div;       // kProdList / kProdPairs: divisor len
+    FastDiv inner;     // fixed products only: divisor = product of the inner factors' lengths
     int out0;          // output column of the factor's (first) value
 };
 struct ProdSpec {
@@ -173,7 +187,8 @@ int launch_product_count_scan(const StoreView &sv, const ProdSpec &spec, const C
 // mixed radix over the factors (innermost factor fastest) to pick each
 // factor's entry.
 int launch_product(const StoreView &sv, const ProdSpec &spec, const Cols &in, int k, int64_t n_in, const int64_t *off,
-                   const int32_t *first, const int32_t *len, int64_t total, OutCols out, cudaStream_t st);
+                   const int32_t *first, const int32_t *len, int64_t total, OutCols out, cudaStream_t st,
+                  const TileConfig &tc = TileConfig());
 // The product of fixed lists only (no input columns, one input row):
 // total = product of the factors' lengths (< 2^32).
 int launch_product_fixed(const ProdSpec &spec, int64_t total, OutCols out, cudaStream_t st);

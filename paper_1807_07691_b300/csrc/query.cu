@@ -354,7 +354,8 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
             OutCols oc;
             const int keep = (count_only && last) ? 0 : cur.ncols;
             GS_TRY(alloc_cols(nxt, cur.ncols, cur.rows, st, &oc));
-            GS_TRY(launch_filter(S->view, ps0, ps1, vs, vo, cur.cols(), keep, cur.rows, oc, cx.d_count(), cx.d_err(), st));
+            GS_TRY(launch_filter(S->view, ps0, ps1, vs, vo, cur.cols(), keep, cur.rows, oc, cx.d_count(), cx.d_err(), st,
+                                 S->tiles));
             int64_t cnt = 0;
             GS_TRY(cx.read_count(&cnt));
             nxt.rows = cnt;
@@ -406,7 +407,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
                     OutCols oc;
                     GS_TRY(alloc_cols(nxt, cur.ncols + 1, total, st, &oc));
                     GS_TRY(launch_expand(S->view, side, cur.cols(), cur.ncols, cur.rows, off.as<int64_t>(),
-                                         fst.as<int32_t>(), total, oc, st));
+                                         fst.as<int32_t>(), total, oc, st, S->tiles));
                 }
                 for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
                 nxt.vars[cur.ncols] = newv;
@@ -575,7 +576,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
                 OutCols oc;
                 GS_TRY(alloc_cols(nxt, col, total, st, &oc));
                 GS_TRY(launch_product(S->view, spec, cur.cols(), cur.ncols, cur.rows, off.as<int64_t>(),
-                                      fr.as<int32_t>(), ln.as<int32_t>(), total, oc, st));
+                                      fr.as<int32_t>(), ln.as<int32_t>(), total, oc, st, S->tiles));
             }
             // intermediates of the fused steps are not built
             for (int s = tail; s < n_pats; ++s) {
@@ -662,6 +663,67 @@ int query_run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n
     }
     T->storage.st = nullptr;  // freed on the legacy stream later
     *out = T;
+    return GSMAT_OK;
+}
+
+int store_tune(gsmat_store *S, const gsmat_bgp *bgps, int32_t n, cudaStream_t st, TileConfig *best) {
+    if (!S || !bgps || n < 1 || !best) return set_error(GSMAT_ERR_INVALID_ARG, "store tune: bad arguments");
+    for (int32_t i = 0; i < n; ++i) GS_TRY(validate_bgp(bgps[i].pats, bgps[i].n_pats, bgps[i].n_vars));
+    const TileConfig keep = S->tiles;
+    std::vector<TileConfig> cands;
+    cands.push_back(TileConfig());  // the default first: a tie keeps it
+    for (int e : {512, 1024, 2048, 4096, 8192}) {
+        for (int r : {16, 64, 256}) {
+            TileConfig c;
+            c.expand_items = e;
+            c.short_row = r;
+            if (c.expand_items != cands[0].expand_items || c.short_row != cands[0].short_row) cands.push_back(c);
+        }
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return set_error(GSMAT_ERR_CUDA, "store tune: events");
+    }
+    auto run_all = [&]() -> int {
+        for (int32_t i = 0; i < n; ++i) {
+            gsmat_table *T = nullptr;
+            GS_TRY(query_run(S, bgps[i].pats, bgps[i].n_pats, bgps[i].n_vars, GSMAT_SORTED, st, &T, 0, 1));
+            delete T;
+        }
+        return GSMAT_OK;
+    };
+    int rc = GSMAT_OK;
+    double best_ms = 1e300;
+    TileConfig pick = cands[0];
+    for (const TileConfig &c : cands) {
+        S->tiles = c;
+        if ((rc = run_all()) != GSMAT_OK) break;  // warm-up (allocator pool, caches)
+        double ms_min = 1e300;
+        for (int rep = 0; rep < 2 && rc == GSMAT_OK; ++rep) {
+            cudaEventRecord(a, st);
+            rc = run_all();
+            cudaEventRecord(b, st);
+            float ms = 0;
+            if (rc == GSMAT_OK && (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess)) {
+                rc = set_error(GSMAT_ERR_CUDA, "store tune: timing");
+            }
+            ms_min = std::min(ms_min, (double)ms);
+        }
+        if (rc != GSMAT_OK) break;
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc != GSMAT_OK) {
+        S->tiles = keep;
+        return rc;
+    }
+    S->tiles = pick;
+    *best = pick;
     return GSMAT_OK;
 }
 

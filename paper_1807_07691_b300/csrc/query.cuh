@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "join.cuh"
 
 struct gsmat_table {
     int64_t rows = 0;
@@ -27,6 +28,9 @@ int table_copy(const gsmat_table *T, int32_t *dst, int dst_on_device, cudaStream
 // to variable order, rows ascending; the result owns its columns.
 int reorder_view(const gsmat_store *S, const int32_t *const *plan_cols, const int32_t *plan_vars, int V, int64_t rows,
                  cudaStream_t st, gsmat_table **out);
+// Time the BGPs under every candidate tile shape and keep the fastest on the
+// store (gsmat_store_tune).
+int store_tune(gsmat_store *S, const gsmat_bgp *bgps, int32_t n, cudaStream_t st, TileConfig *best);
 // Projection / DISTINCT of a table (gsmat_table_project).
 int table_project(const gsmat_table *T, const int32_t *vars, int32_t n, int distinct, cudaStream_t st,
                   gsmat_table **out);

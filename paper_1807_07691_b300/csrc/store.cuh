@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "join.cuh"
 
 struct gsmat_store {
     int64_t n_input = 0;
@@ -28,6 +29,7 @@ struct gsmat_store {
     gs::DevBuf pred_side_dev;  // PredSide[2][n_pred] (device copy)
     gs::DevBuf hash_dev;       // int32 keys[cap], vals[cap] (device copy of the hash index)
     gs::StoreView view{};
+    gs::TileConfig tiles;  // tile shapes of the plain path's joins on this store
 
     int64_t device_bytes() const {
         int64_t b = 0;

@@ -183,3 +183,10 @@ def test_wait_expiry_selftest_rejects_bad_poll_limits(gs):
     for bad in (0, -1, (1 << 22) + 1):
         assert lib.gsmat_selftest_wait_expiry(bad, None) == 1  # GSMAT_ERR_INVALID_ARG
         assert b"poll limit" in lib.gsmat_last_error()
+
+
+def test_tile_setters_check_their_arguments_on_the_host(gs):
+    lib = gs.lib()
+    assert lib.gsmat_store_set_tiles(None, None) == 1
+    assert lib.gsmat_store_get_tiles(None, None) == 1
+    assert lib.gsmat_store_tune(None, None, 0, None, None) == 1

@@ -296,3 +296,35 @@ def test_cost_plan_random_small_graphs(gs, seed):
     want = oracle.oracle_query(t, pats, V)
     got = gs.Store(t).query(pats, V, flags=gs.PLAN_COST).to_numpy()
     assert got.shape == want.shape and np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("expand_items,short_row", [(512, 1), (1024, 16), (4096, 256), (8192, 4096)])
+def test_tile_shapes_leave_results_unchanged(gs, tiny, expand_items, short_row):
+    """Every tile shape the tuner may pick gives the oracle's rows (the
+    tiny workload, random BGPs, the cycles' filters)."""
+    t, ix, S, qs = tiny
+    S.set_tiles(expand_items, short_row)
+    try:
+        assert S.tiles() == {"expand_items": expand_items, "short_row": short_row}
+        for q in qs:
+            assert np.array_equal(S.query(q).to_numpy(), ix.query(q)), q.name
+        rng = np.random.default_rng(expand_items + short_row)
+        for pats, V in _cyclic_bgps(t, rng, 10):
+            want = ix.query(pats, V, row_limit=20_000_000)
+            assert np.array_equal(S.query(pats, V).to_numpy(), want)
+    finally:
+        S.set_tiles()
+
+
+def test_store_tune_keeps_the_fastest_shape(gs, tiny):
+    t, ix, S, qs = tiny
+    with pytest.raises(gs.GsmatError):
+        S.set_tiles(3000, 64)
+    with pytest.raises(gs.GsmatError):
+        S.set_tiles(2048, 0)
+    best = S.tune(qs)
+    assert best["expand_items"] in (512, 1024, 2048, 4096, 8192) and best["short_row"] in (16, 64, 256)
+    assert S.tiles() == best
+    for q in qs:
+        assert np.array_equal(S.query(q).to_numpy(), ix.query(q)), q.name
+    S.set_tiles()
