@@ -162,9 +162,16 @@ def plain_leg(args, gs, torch, name, triples, queries, stream, ws, local, steps,
     d_tri = torch.from_numpy(np.array(triples, copy=True)).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     marsh = [gs.Store.marshal(q) for q in queries]  # BGPs converted to the C layout once
+    # tile shapes: tuned once on this workload (untimed), set on every step's store
+    S0 = gs.Store(d_tri, stream=stream)
+    t0 = time.perf_counter()
+    tiles = S0.tune(queries, stream=stream)
+    tune_s = time.perf_counter() - t0
+    S0.free()
 
     def step(lat=None):
         S = gs.Store(d_tri, stream=stream)
+        S.set_tiles(**tiles)
         tabs = []
         rows = 0
         for q in marsh:
@@ -234,6 +241,7 @@ def plain_leg(args, gs, torch, name, triples, queries, stream, ws, local, steps,
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         S = gs.Store(h_tri.numpy(), stream=stream)
+        S.set_tiles(**tiles)
         d2h = 0
         held = []
         for qi, q in enumerate(marsh):
@@ -269,6 +277,7 @@ def plain_leg(args, gs, torch, name, triples, queries, stream, ws, local, steps,
                 "h2d_bytes_per_step": int(np.asarray(triples).nbytes), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": round(float(np.median(e2e_ms)), 3)},
         "d_tri": d_tri,
+        "tiles": dict(tiles, tune_s=round(tune_s, 2)),
         "nq": nq,
         "n_triples": int(np.asarray(triples).shape[0]),
     }
@@ -329,6 +338,7 @@ def leg_summary(leg, peak, peak_kind, ws):
         "roofline": roofline(leg["prof"], ws, peak, peak_kind),
         "kernels": kernel_table(leg["prof"]),
         "clocks": leg["clocks"],
+        "tiles": leg["tiles"],
     }
 
 
@@ -412,6 +422,7 @@ def run_gsmat(args):
         "roofline": hs["roofline"],
         "kernels": hs["kernels"],
         "clocks": hs["clocks"],
+        "tiles": hs["tiles"],
         "generation_s": round(gen_s, 1),
     }
     if medium is not None:
@@ -496,22 +507,34 @@ def run_batched(args, gs, torch, d_tri, stream):
     st = B.stats()
     rows_batch = sum(B.result(i)[0] for i in range(len(bq)))
     assert rows_batch == rows_plain, (rows_batch, rows_plain)
+    # every result equal to the plain path's (compared on the device)
+    mismatched = 0
+    for i, q in enumerate(bmarsh):
+        T = S.query_raw(q, stream=stream)
+        a = torch.from_numpy(B.to_numpy(i))
+        b = torch.from_numpy(T.to_numpy())
+        mismatched += int(a.shape != b.shape or not torch.equal(a, b))
+        T.free()
     batch_ms = float(np.median(runs))
     out = {
         "workload": f"{len(bq)} BGPs, 2-8 patterns, star:chain:snowflake:cycle 4:3:2:1, medium graph",
         "queries_per_s": round(len(bq) / (batch_ms / 1e3), 1),
+        "queries_per_s_with_prepare": round(len(bq) / ((batch_ms + prep_ms) / 1e3), 1),
         "plain_queries_per_s": round(len(bq) / (plain_ms / 1e3), 1),
         "speedup_vs_plain": round(plain_ms / batch_ms, 2),
+        "speedup_vs_plain_with_prepare": round(plain_ms / (batch_ms + prep_ms), 2),
+        "results_equal_to_plain": len(bq) - mismatched,
         "batch_ms": round(batch_ms, 3),
         "plain_ms": round(plain_ms, 3),
         "prepare_ms": round(prep_ms, 2),
+        "intersect_steps": st["n_intersect"],
         "kernel_ms": round(st["kernel_ms"], 3),
         "reorder_ms": round(st["reorder_ms"], 3),
         "in_kernel": st["n_in_kernel"],
         "reordered": st["n_reordered"],
         "fallback": st["n_fallback"],
         "result_rows": int(rows_batch),
-        "tuned": {"block": tuned["block"], "ctas_per_sm": tuned["ctas_per_sm"]},
+        "tuned": {"block": tuned["block"], "ctas_per_sm": tuned["ctas_per_sm"], "expand_slots": tuned["expand_slots"]},
         "generation_s": round(gen_s, 1),
     }
     B.free()
@@ -1019,11 +1042,12 @@ def run_micro(args):
     if args.micro == "sort":
         src = torch.randint(0, 1 << min(args.bits, 62), (n,), device="cuda", dtype=torch.int64, generator=g)
         keys = src.clone()
-        vals = torch.arange(n, device="cuda", dtype=torch.int32)
+        vals = None if args.keys_only else torch.arange(n, device="cuda", dtype=torch.int32)
         ms = []
         for it in range(args.warmup + args.steps):
             keys.copy_(src)
-            vals.copy_(torch.arange(n, device="cuda", dtype=torch.int32))
+            if vals is not None:
+                vals.copy_(torch.arange(n, device="cuda", dtype=torch.int32))
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
@@ -1033,7 +1057,7 @@ def run_micro(args):
             if it >= args.warmup:
                 ms.append(a.elapsed_time(b))
         passes = (args.bits + 7) // 8
-        algo = n * 12.0 * 2 * passes
+        algo = n * (8.0 if args.keys_only else 12.0) * 2 * passes
         t = float(np.median(ms))
         out.update({"bits": args.bits, "passes": passes, "ms": round(t, 4),
                     "algo_GBps": round(algo / 1e9 / (t / 1e3), 1), "Mkeys_per_s": round(n / 1e3 / t, 1)})
@@ -1085,6 +1109,44 @@ def run_micro(args):
                     "algo_GBps": round(prof["algo_bytes"] / 1e9 / (prof["total_ms"] / 1e3), 1) if prof else None,
                     "algo_bytes_per_row": round(prof["algo_bytes"] / prof["items"], 2) if prof else None,
                     "Mrows_per_s": round(n / 1e3 / t, 1)})
+    elif args.micro == "product":
+        # a star around one constant: `cols` predicates with rows of length
+        # L = round(n^(1/cols)), so the result is a product of about n rows
+        # (written by the product step, no reorder)
+        V = args.cols
+        L = max(2, int(round(n ** (1.0 / V))))
+        c = 5
+        tri = []
+        for p in range(V):
+            objs = np.arange(L, dtype=np.int64) * 7 + p  # distinct, ascending
+            tri.append(np.stack([np.full(L, c), np.full(L, 100 + p), objs], axis=1))
+        tri = np.concatenate(tri).astype(np.int32)
+        S = gs.Store(torch.from_numpy(tri).cuda())
+        # variables numbered against the plan's order of equal-length rows
+        pats = [(c, 100 + p, V - 1 - p, False, True) for p in range(V)]
+        ms = []
+        gs.profile_read(reset=True)
+        rows = 0
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                gs.profile_read(reset=True)
+                gs.profile_enable(True)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            T = S.query(pats, V)
+            b.record()
+            b.synchronize()
+            rows = T.rows
+            T.free()
+            if it >= args.warmup:
+                ms.append(a.elapsed_time(b))
+        gs.profile_enable(False)
+        prof = gs.profile_read(reset=True).get("product")
+        t = float(np.median(ms))
+        out.update({"cols": V, "row_len": L, "rows": rows, "query_ms": round(t, 4),
+                    "product_ms_per_launch": round(prof["total_ms"] / prof["launches"], 4) if prof else None,
+                    "algo_GBps": round(prof["algo_bytes"] / 1e9 / (prof["total_ms"] / 1e3), 1) if prof else None})
     elif args.micro == "query":
         triples, queries, _ = _workload(args.workload)
         S = gs.Store(torch.from_numpy(np.array(triples, copy=True)).cuda())
@@ -1109,10 +1171,11 @@ def run_micro(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--query-index", type=int, default=14)
-    ap.add_argument("--micro", choices=["sort", "scan", "rows", "query"], default=None,
+    ap.add_argument("--micro", choices=["sort", "scan", "rows", "product", "query"], default=None,
                     help="time one primitive on a synthetic input instead of the workload")
     ap.add_argument("--n", type=int, default=1 << 25)
     ap.add_argument("--bits", type=int, default=40)
+    ap.add_argument("--keys-only", action="store_true", help="--micro sort: no payload")
     ap.add_argument("--cols", type=int, default=4, help="--micro rows: columns")
     ap.add_argument("--key-cols", type=int, default=2, help="--micro rows: leading sort columns")
     ap.add_argument("--row-bits", type=int, default=20, help="--micro rows: bits per value")
