@@ -440,16 +440,16 @@ int reorder_group(gsmat_batch *B, const std::vector<int> &qs, int m, int bits) {
     GS_TRY(err.alloc(sizeof(int), B->priv));
     GS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), B->priv));
     // The other variables travel with the key when they fit 64 bits, the
-    // key (with the segment index) one word of at most five passes, and the
+    // key (with the segment index) one word of at most 40 bits, and the
     // rows are well beyond L2 (as the plain reorder decides): no gather.
     int max_rest = 0;
     for (const SegDesc &d : segs) max_rest = std::max(max_rest, d.V - m);
     const int kb_all = m * bits;
-    const int n_pass_all = (kb_all + seg_bits + 7) / 8;
+    const int key_bits_all = kb_all + seg_bits;
     const bool can_carry = kb_all + seg_bits <= 64 && max_rest > 0 && max_rest * bits <= 64;
     const int mode = B->cfg.reorder_mode;
     const bool carry = mode == GSMAT_SORT_CARRY ||
-                       (mode == 0 && n_pass_all <= 5 && (double)total * max_rest * 4.0 > 256.0 * (1 << 20));
+                       (mode == 0 && key_bits_all <= 40 && (double)total * max_rest * 4.0 > 256.0 * (1 << 20));
     if (can_carry && carry) {
         DevBuf pay;
         GS_TRY(keys.alloc(sizeof(uint64_t) * (size_t)total, B->priv));
