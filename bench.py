@@ -165,7 +165,7 @@ def plain_leg(args, gs, torch, name, triples, queries, stream, ws, local, steps,
     # tile shapes: tuned once on this workload (untimed), set on every step's store
     S0 = gs.Store(d_tri, stream=stream)
     t0 = time.perf_counter()
-    tiles = S0.tune(queries, stream=stream)
+    tiles = S0.tiles() if args.no_tune else S0.tune(queries, stream=stream)
     tune_s = time.perf_counter() - t0
     S0.free()
 
@@ -341,6 +341,9 @@ TRAFFIC_RATIO = {
     # profiles/reorder_sort_q14_traffic.md: the 62 M-row reorder of the medium
     # chain query q14, 11719.0 MB of DRAM traffic against 10917.8 MB algorithmic
     "reorder_sort": (11719.0 / 10917.8, "profiles/reorder_sort_q14_traffic.md (one call: medium q14)"),
+    # profiles/radix_sort_keys60_traffic.md: a 2^28-key, 60-bit keys-only sort
+    # (the store build's shape), 42.1 GB of DRAM traffic against 34.4 GB
+    "radix_sort_u64": (42.1 / 34.4, "profiles/radix_sort_keys60_traffic.md (one call: 2^28 keys, 60 bits)"),
     # profiles/product_fixed_star4_traffic.md: a 40.96 M-row product of four
     # constant rows, 592.4 MB of DRAM traffic against 819.2 MB algorithmic
     "product": (592.4 / 819.2, "profiles/product_fixed_star4_traffic.md (one call: 40.96 M-row star)"),
@@ -1245,6 +1248,7 @@ def main():
     ap.add_argument("--workload", default="large", choices=["large", "medium", "tiny"],
                     help="the headline plain-path workload (large: the largest configuration)")
     ap.add_argument("--no-medium", action="store_true", help="skip the medium plain-path line")
+    ap.add_argument("--no-tune", action="store_true", help="plain-path steps: default tile shapes (no tuning pass)")
     ap.add_argument("--query-streams", type=int, default=1,
                     help="plain-path steps: host threads (each with its own stream) running the step's queries")
     ap.add_argument("--no-cpu-baseline", action="store_true")
