@@ -201,6 +201,79 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         qs.est_cost += qs.est_rows[s];
         qs.rows[s] = -1;
     }
+    // Constant rows first: when every pattern with one constant end and one
+    // new variable can run first (its row depends on nothing) and every
+    // other pattern then expands a variable those rows bind, the result is
+    // the product of the constant rows (in variable order) joined with a
+    // product per row of the expansions -- two product steps, no final
+    // reorder.  Taken only when the constant rows' product (its size is
+    // exact: the rows are known) stays within twice the estimated result and
+    // 2^27 rows, so no intermediate appears that Alg. 1's order would keep
+    // small.  Off for GSMAT_NO_INTERSECT, GSMAT_PLAN_ORDER and row shards.
+    int fixed_prefix = 0;
+    if (!(flags & (GSMAT_NO_INTERSECT | GSMAT_PLAN_ORDER)) && !absent && n_shards == 1 && n_pats >= 3) {
+        std::vector<int32_t> fx, rest;
+        uint64_t fvars = 0;
+        bool ok = true;
+        double prefix_rows = 1.0;
+        for (int s = 0; s < n_pats && ok; ++s) {
+            const int i = qs.order[s];
+            const gsmat_pattern &p = pats[i];
+            if (p.s_var != p.o_var) {  // one constant end, one variable
+                const int32_t v = p.s_var ? p.s : p.o;
+                if ((fvars >> v) & 1) ok = false;  // a second constant row for the same variable
+                fvars |= uint64_t(1) << v;
+                fx.push_back(i);
+                prefix_rows *= (double)keys[i];
+            } else {
+                rest.push_back(i);
+            }
+        }
+        double final_rows = prefix_rows;
+        uint64_t bound = fvars;
+        for (int32_t i : rest) {
+            if (!ok) break;
+            const gsmat_pattern &p = pats[i];
+            const int kind = step_kind(p, bound);
+            const bool from_prefix = (kind == GSMAT_STEP_EXPAND_S && p.s_var && ((fvars >> p.s) & 1)) ||
+                                     (kind == GSMAT_STEP_EXPAND_O && p.o_var && ((fvars >> p.o) & 1));
+            if (!from_prefix) {
+                ok = false;
+                break;
+            }
+            const double nr = kind == GSMAT_STEP_EXPAND_S ? (double)stats[i].nr_s : (double)stats[i].nr_o;
+            final_rows *= nr > 0 ? (double)stats[i].nnz / nr : 0.0;
+            bound |= uint64_t(1) << (kind == GSMAT_STEP_EXPAND_S ? p.o : p.s);
+        }
+        if (ok && fx.size() >= 2 && fx.size() <= (size_t)kMaxProdFactors && !rest.empty() && prefix_rows <= 2.0 * final_rows &&
+            prefix_rows <= (double)(int64_t(1) << 27)) {
+            uint64_t bnd = 0;
+            double est = 1.0;
+            int s = 0;
+            for (const std::vector<int32_t> *part : {&fx, &rest}) {
+                for (int32_t i : *part) {
+                    const gsmat_pattern &p = pats[i];
+                    const int kind = step_kind(p, bnd);
+                    qs.order[s] = i;
+                    qs.kind[s] = kind;
+                    if (part == &fx) {
+                        est *= (double)keys[i];
+                    } else {
+                        const double nr = kind == GSMAT_STEP_EXPAND_S ? (double)stats[i].nr_s : (double)stats[i].nr_o;
+                        est *= nr > 0 ? (double)stats[i].nnz / nr : 0.0;
+                    }
+                    qs.est_rows[s] = est;
+                    if (p.s_var) bnd |= uint64_t(1) << p.s;
+                    if (p.o_var) bnd |= uint64_t(1) << p.o;
+                    ++s;
+                }
+            }
+            qs.est_cost = 0;
+            for (int k = 0; k < n_pats; ++k) qs.est_cost += qs.est_rows[k];
+            fixed_prefix = (int)fx.size();
+        }
+    }
+
     // variables in the order the plan binds them
     std::vector<int32_t> plan_vars;
     {
@@ -283,13 +356,144 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         if (n_shards > 1 && tail == 0) tail = 1;  // shards split the first step's relation
         if (n_pats - tail > kMaxProdFactors) tail = n_pats - kMaxProdFactors;
         if (n_pats - tail < 2) tail = n_pats;
+        if (fixed_prefix > 0) {
+            // the constant rows run as one product; the rest (expansions of
+            // their variables) as the tail, or step by step if it is one step
+            tail = (n_pats - fixed_prefix >= 2 && n_pats - fixed_prefix <= kMaxProdFactors) ? fixed_prefix : n_pats;
+        }
     }
 
     Tbl cur;
     cur.rows = absent ? 0 : 1;  // one empty assignment
     cur.ncols = 0;
     const bool count_only = (flags & GSMAT_COUNT_ONLY) != 0;
-    for (int step = 0; step < tail && cur.rows > 0; ++step) {
+    // Steps [a, b) as one product step on `cur` (see launch_product);
+    // count_rows: only the row count is needed (the query's last step).
+    auto product_segment = [&](int a, int b, bool count_rows) -> int {
+        struct Fac {
+            int32_t v0, v1;  // the factor's variables (v1 = -1 for one)
+            ProdFactor f;
+        };
+        std::vector<Fac> facs;
+        for (int s = a; s < b; ++s) {
+            const gsmat_pattern &p = pats[qs.order[s]];
+            const int sl = slot[qs.order[s]];
+            Fac x;
+            memset(&x, 0, sizeof(x));
+            x.v1 = -1;
+            if (qs.kind[s] == GSMAT_STEP_CROSS) {
+                // M_p from the side that puts the lower variable first, as a CROSS step does
+                const int sd = p.o < p.s ? 1 : 0;
+                const PredSide &pss = S->side[sd][sl];
+                x.f.kind = kProdPairs;
+                x.f.a = S->view.side[sd].key + pss.ent_base;
+                x.f.b = S->view.side[sd].val + pss.ent_base;
+                x.f.len = (uint32_t)pss.nnz;
+                x.v0 = sd == 0 ? p.s : p.o;
+                x.v1 = sd == 0 ? p.o : p.s;
+            } else {
+                const int side = qs.kind[s] == GSMAT_STEP_EXPAND_S ? 0 : 1;
+                x.v0 = side == 0 ? p.o : p.s;
+                if (side == 0 ? p.s_var : p.o_var) {
+                    x.f.kind = kProdRow;
+                    x.f.side = side;
+                    x.f.xcol = cur.col_of(side == 0 ? p.s : p.o);
+                    x.f.ps = S->side[side][sl];
+                } else {
+                    const int r = side == 0 ? req_s[qs.order[s]] : req_o[qs.order[s]];
+                    x.f.kind = kProdList;
+                    x.f.a = S->view.side[side].val + rng[2 * r];
+                    x.f.len = (uint32_t)row_len(r);
+                }
+            }
+            facs.push_back(x);
+        }
+        // outermost factor = smallest variable: inside every input row the
+        // product's rows then ascend in variable order
+        std::stable_sort(facs.begin(), facs.end(), [](const Fac &a, const Fac &b) { return a.v0 < b.v0; });
+        ProdSpec spec;
+        memset(&spec, 0, sizeof(spec));
+        spec.nf = (int)facs.size();
+        Tbl nxt;
+        int col = cur.ncols;
+        for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
+        uint64_t fixed = 1;  // product of the fixed factors' lengths, saturating
+        const uint64_t kSat = uint64_t(1) << 40;
+        for (int i = 0; i < spec.nf; ++i) {
+            ProdFactor &f = spec.f[i];
+            f = facs[i].f;
+            f.out0 = col;
+            nxt.vars[col++] = facs[i].v0;
+            if (f.kind == kProdPairs) nxt.vars[col++] = facs[i].v1;
+            if (f.kind == kProdRow) {
+                f.slot = spec.nrow++;
+            } else {
+                f.div = make_fastdiv(f.len);
+                fixed = (f.len != 0 && fixed > kSat / f.len) ? kSat : fixed * f.len;
+            }
+        }
+        int64_t total = 0;
+        const bool unit = cur.rows == 1 && cur.ncols == 0;
+        if (unit) {
+            // fixed lists only (a row factor needs a column of the table)
+            total = (int64_t)fixed;
+            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+            if (!count_rows && total > 0) {
+                OutCols oc;
+                GS_TRY(alloc_cols(nxt, col, total, st, &oc));
+                GS_TRY(launch_product_fixed(spec, total, oc, st));
+            }
+            // the plan-order intermediates are known exactly: running products
+            uint64_t run_rows = 1;
+            for (int s = a; s < b; ++s) {
+                const gsmat_pattern &p = pats[qs.order[s]];
+                const int sl = slot[qs.order[s]];
+                uint64_t l;
+                if (qs.kind[s] == GSMAT_STEP_CROSS) {
+                    l = (uint64_t)S->side[p.o < p.s ? 1 : 0][sl].nnz;
+                } else {
+                    const bool sd0 = qs.kind[s] == GSMAT_STEP_EXPAND_S;
+                    l = (uint64_t)row_len(sd0 ? req_s[qs.order[s]] : req_o[qs.order[s]]);
+                }
+                run_rows = (l != 0 && run_rows > kSat / l) ? kSat : run_rows * l;
+                qs.rows[s] = (int64_t)run_rows;
+                qs.kind[s] = GSMAT_STEP_PRODUCT;
+            }
+        } else {
+            DevBuf off, fr, ln;
+            GS_TRY(off.alloc(sizeof(int64_t) * (size_t)(cur.rows + 1), st));
+            if (spec.nrow > 0) {
+                GS_TRY(fr.alloc(sizeof(int32_t) * (size_t)spec.nrow * (size_t)cur.rows, st));
+                GS_TRY(ln.alloc(sizeof(int32_t) * (size_t)spec.nrow * (size_t)cur.rows, st));
+            }
+            GS_TRY(launch_product_count_scan(S->view, spec, cur.cols(), cur.rows, off.as<int64_t>(), fr.as<int32_t>(),
+                                             ln.as<int32_t>(), cx.d_count(), cx.d_err(), st));
+            GS_TRY(cx.read_count(&total));
+            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
+            if (!count_rows && total > 0) {
+                OutCols oc;
+                GS_TRY(alloc_cols(nxt, col, total, st, &oc));
+                GS_TRY(launch_product(S->view, spec, cur.cols(), cur.ncols, cur.rows, off.as<int64_t>(),
+                                      fr.as<int32_t>(), ln.as<int32_t>(), total, oc, st, S->tiles));
+            }
+            // intermediates of the fused steps are not built
+            for (int s = a; s < b; ++s) {
+                qs.rows[s] = s == b - 1 ? total : -1;
+                qs.kind[s] = GSMAT_STEP_PRODUCT;
+            }
+        }
+        nxt.rows = total;
+        nxt.ncols = col;
+        cur = std::move(nxt);
+        return GSMAT_OK;
+    };
+    int first = 0;
+    if (fixed_prefix >= 2 && cur.rows > 0) {
+        // the constant rows' product, in variable order
+        GS_TRY(product_segment(0, fixed_prefix, false));
+        first = fixed_prefix;
+    }
+    for (int step = first; step < tail && cur.rows > 0; ++step) {
         const gsmat_pattern &p = pats[qs.order[step]];
         const int kind = qs.kind[step];
         const PredSide &ps0 = S->side[0][slot[qs.order[step]]];
@@ -471,123 +675,7 @@ int run(const gsmat_store *S, const gsmat_pattern *pats, int n_pats, int n_vars,
         qs.rows[step] = cur.rows;
     }
 
-    if (tail < n_pats && cur.rows > 0) {
-        struct Fac {
-            int32_t v0, v1;  // the factor's variables (v1 = -1 for one)
-            ProdFactor f;
-        };
-        std::vector<Fac> facs;
-        for (int s = tail; s < n_pats; ++s) {
-            const gsmat_pattern &p = pats[qs.order[s]];
-            const int sl = slot[qs.order[s]];
-            Fac x;
-            memset(&x, 0, sizeof(x));
-            x.v1 = -1;
-            if (qs.kind[s] == GSMAT_STEP_CROSS) {
-                // M_p from the side that puts the lower variable first, as a CROSS step does
-                const int sd = p.o < p.s ? 1 : 0;
-                const PredSide &pss = S->side[sd][sl];
-                x.f.kind = kProdPairs;
-                x.f.a = S->view.side[sd].key + pss.ent_base;
-                x.f.b = S->view.side[sd].val + pss.ent_base;
-                x.f.len = (uint32_t)pss.nnz;
-                x.v0 = sd == 0 ? p.s : p.o;
-                x.v1 = sd == 0 ? p.o : p.s;
-            } else {
-                const int side = qs.kind[s] == GSMAT_STEP_EXPAND_S ? 0 : 1;
-                x.v0 = side == 0 ? p.o : p.s;
-                if (side == 0 ? p.s_var : p.o_var) {
-                    x.f.kind = kProdRow;
-                    x.f.side = side;
-                    x.f.xcol = cur.col_of(side == 0 ? p.s : p.o);
-                    x.f.ps = S->side[side][sl];
-                } else {
-                    const int r = side == 0 ? req_s[qs.order[s]] : req_o[qs.order[s]];
-                    x.f.kind = kProdList;
-                    x.f.a = S->view.side[side].val + rng[2 * r];
-                    x.f.len = (uint32_t)row_len(r);
-                }
-            }
-            facs.push_back(x);
-        }
-        // outermost factor = smallest variable: inside every input row the
-        // product's rows then ascend in variable order
-        std::stable_sort(facs.begin(), facs.end(), [](const Fac &a, const Fac &b) { return a.v0 < b.v0; });
-        ProdSpec spec;
-        memset(&spec, 0, sizeof(spec));
-        spec.nf = (int)facs.size();
-        Tbl nxt;
-        int col = cur.ncols;
-        for (int c = 0; c < cur.ncols; ++c) nxt.vars[c] = cur.vars[c];
-        uint64_t fixed = 1;  // product of the fixed factors' lengths, saturating
-        const uint64_t kSat = uint64_t(1) << 40;
-        for (int i = 0; i < spec.nf; ++i) {
-            ProdFactor &f = spec.f[i];
-            f = facs[i].f;
-            f.out0 = col;
-            nxt.vars[col++] = facs[i].v0;
-            if (f.kind == kProdPairs) nxt.vars[col++] = facs[i].v1;
-            if (f.kind == kProdRow) {
-                f.slot = spec.nrow++;
-            } else {
-                f.div = make_fastdiv(f.len);
-                fixed = (f.len != 0 && fixed > kSat / f.len) ? kSat : fixed * f.len;
-            }
-        }
-        int64_t total = 0;
-        const bool unit = cur.rows == 1 && cur.ncols == 0;
-        if (unit) {
-            // fixed lists only (a row factor needs a column of the table)
-            total = (int64_t)fixed;
-            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
-            if (!count_only && total > 0) {
-                OutCols oc;
-                GS_TRY(alloc_cols(nxt, col, total, st, &oc));
-                GS_TRY(launch_product_fixed(spec, total, oc, st));
-            }
-            // the plan-order intermediates are known exactly: running products
-            uint64_t run_rows = 1;
-            for (int s = tail; s < n_pats; ++s) {
-                const gsmat_pattern &p = pats[qs.order[s]];
-                const int sl = slot[qs.order[s]];
-                uint64_t l;
-                if (qs.kind[s] == GSMAT_STEP_CROSS) {
-                    l = (uint64_t)S->side[p.o < p.s ? 1 : 0][sl].nnz;
-                } else {
-                    const bool sd0 = qs.kind[s] == GSMAT_STEP_EXPAND_S;
-                    l = (uint64_t)row_len(sd0 ? req_s[qs.order[s]] : req_o[qs.order[s]]);
-                }
-                run_rows = (l != 0 && run_rows > kSat / l) ? kSat : run_rows * l;
-                qs.rows[s] = (int64_t)run_rows;
-                qs.kind[s] = GSMAT_STEP_PRODUCT;
-            }
-        } else {
-            DevBuf off, fr, ln;
-            GS_TRY(off.alloc(sizeof(int64_t) * (size_t)(cur.rows + 1), st));
-            if (spec.nrow > 0) {
-                GS_TRY(fr.alloc(sizeof(int32_t) * (size_t)spec.nrow * (size_t)cur.rows, st));
-                GS_TRY(ln.alloc(sizeof(int32_t) * (size_t)spec.nrow * (size_t)cur.rows, st));
-            }
-            GS_TRY(launch_product_count_scan(S->view, spec, cur.cols(), cur.rows, off.as<int64_t>(), fr.as<int32_t>(),
-                                             ln.as<int32_t>(), cx.d_count(), cx.d_err(), st));
-            GS_TRY(cx.read_count(&total));
-            if (total > (int64_t)UINT32_MAX) return set_error(GSMAT_ERR_CAPACITY, "product of %lld rows", (long long)total);
-            if (!count_only && total > 0) {
-                OutCols oc;
-                GS_TRY(alloc_cols(nxt, col, total, st, &oc));
-                GS_TRY(launch_product(S->view, spec, cur.cols(), cur.ncols, cur.rows, off.as<int64_t>(),
-                                      fr.as<int32_t>(), ln.as<int32_t>(), total, oc, st, S->tiles));
-            }
-            // intermediates of the fused steps are not built
-            for (int s = tail; s < n_pats; ++s) {
-                qs.rows[s] = s == n_pats - 1 ? total : -1;
-                qs.kind[s] = GSMAT_STEP_PRODUCT;
-            }
-        }
-        nxt.rows = total;
-        nxt.ncols = col;
-        cur = std::move(nxt);
-    }
+    if (tail < n_pats && cur.rows > 0) GS_TRY(product_segment(tail, n_pats, count_only));
 
     // result
     const int64_t rows = cur.rows;

@@ -156,3 +156,64 @@ def test_product_shards_partition_the_result(gs, tiny):
         parts = [S.query_shard(pats, k, n_shards, n_vars=len(preds)) for k in range(n_shards)]
         assert sum(p.rows for p in parts) == want.shape[0]
         assert np.array_equal(gs.merge_tables(parts).to_numpy(), want)
+
+
+def _rows_by(t, side):
+    """{(entity, predicate): sorted other ends} for one side (0: by subject)."""
+    by = {}
+    a, b = (0, 2) if side == 0 else (2, 0)
+    for row in t.tolist():
+        by.setdefault((row[a], row[1]), []).append(row[b])
+    return {k: sorted(v) for k, v in by.items()}
+
+
+def test_constant_rows_first_then_their_expansions(gs, tiny):
+    """Two or three constant rows (c_i p_i ?a_i) and expansions of their
+    variables (?a_i q ?x): the constant rows run first as one product in
+    variable order, then the expansions as a product per row.  Variable
+    ids are shuffled so that the final order differs from the binding
+    order in some cases."""
+    t, ix, S = tiny
+    rng = np.random.default_rng(11)
+    by_s = _rows_by(t, 0)
+    starts = [(k, v) for k, v in by_s.items() if 2 <= len(v) <= 40]
+    preds_of = {}
+    for (e, p) in by_s:
+        preds_of.setdefault(e, []).append(p)
+    hoisted = checked = 0
+    while checked < 40:
+        n_fix = int(rng.integers(2, 4))
+        pick = [starts[i] for i in rng.choice(len(starts), size=n_fix, replace=False)]
+        pats, V = [], 0
+        fix_vars = []
+        for (c, p), _ in pick:
+            pats.append((c, p, V, False, True))
+            fix_vars.append(V)
+            V += 1
+        # expansions from the constant rows' variables, by a predicate one of
+        # their values has
+        for k, ((c, p), objs) in enumerate(pick):
+            for _ in range(int(rng.integers(1, 3))):
+                o = objs[int(rng.integers(0, len(objs)))]
+                if o not in preds_of:
+                    continue
+                q = preds_of[o][int(rng.integers(0, len(preds_of[o])))]
+                pats.append((fix_vars[k], q, V, True, True))
+                V += 1
+        if len(pats) == n_fix:
+            continue
+        perm = rng.permutation(V)
+        pats = [(int(perm[s]) if sv else s, p, int(perm[o]) if ov else o, sv, ov) for s, p, o, sv, ov in pats]
+        try:
+            ix.query(pats, V, row_limit=20_000_000)
+        except oracle.OracleError:
+            continue
+        st, want = _check(gs, S, ix, pats, V)
+        order = st["order"]
+        if all(k == PRODUCT for k in st["kind"][:n_fix]) and sorted(order[:n_fix]) == list(range(n_fix)):
+            hoisted += 1
+            # the constant rows' product is exact: the running products of their lengths
+            lens = [len(pick[i][1]) for i in order[:n_fix]]
+            assert st["rows"][:n_fix] == list(np.cumprod(lens))
+        checked += 1
+    assert hoisted >= 20
