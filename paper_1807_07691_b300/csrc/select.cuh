@@ -7,6 +7,10 @@
 
 #include "common.cuh"
 
+#ifndef GSMAT_SELECT_ITEMS
+#define GSMAT_SELECT_ITEMS 8  // indices per thread and tile
+#endif
+
 namespace gs {
 
 // Op must provide:
@@ -14,33 +18,63 @@ namespace gs {
 //   __device__ void emit(int64_t i, int64_t j) const; // write hit i at output j
 template <int BLOCK, int ITEMS, class Op>
 __global__ void __launch_bounds__(BLOCK) select_kernel(Op op, int64_t n, LookbackScratch ls, int64_t *d_count) {
+    constexpr int W = BLOCK / 32;
     __shared__ int tile_sm;
-    __shared__ int64_t scan_sm[BLOCK / 32 + 1];
     __shared__ int64_t prefix_sm;
+    __shared__ int wsum[W + 1];
     const int tile = acquire_tile_id(ls, &tile_sm);
-    const int64_t i0 = (int64_t)tile * (BLOCK * ITEMS) + (int64_t)threadIdx.x * ITEMS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp-striped: warp w takes 32 * ITEMS consecutive indices, lane l the
+    // l-th of every 32, so reads and the compacted writes are coalesced
+    const int64_t wbase = (int64_t)tile * (BLOCK * ITEMS) + (int64_t)warp * (32 * ITEMS);
+    // all predicates first (their loads in flight together), then the votes
     bool f[ITEMS];
+    if (wbase + 32 * ITEMS <= n) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) f[j] = op.flag(wbase + j * 32 + lane);
+    } else {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int64_t i = wbase + j * 32 + lane;
+            f[j] = i < n && op.flag(i);
+        }
+    }
+    unsigned hit[ITEMS];
     int cnt = 0;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const int64_t i = i0 + j;
-        f[j] = (i < n) && op.flag(i);
-        cnt += f[j] ? 1 : 0;
+        hit[j] = __ballot_sync(0xffffffffu, f[j]);
+        cnt += __popc(hit[j]);
     }
-    int64_t tot;
-    const int64_t ex = block_exclusive_sum<BLOCK>(cnt, scan_sm, &tot);
+    if (lane == 0) wsum[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        const int c = lane < W ? wsum[lane] : 0;
+        int inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane < W) wsum[lane] = inc - c;
+        if (lane == W - 1) wsum[W] = inc;
+    }
+    __syncthreads();
+    const int64_t tot = wsum[W];
     const int64_t pre = tile_lookback(ls, tile, tot, &prefix_sm);
-    int64_t out = pre + ex;
+    int64_t out = pre + wsum[warp];
+    const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        if (f[j]) op.emit(i0 + j, out++);
+        if ((hit[j] >> lane) & 1u) op.emit(wbase + j * 32 + lane, out + __popc(hit[j] & lt));
+        out += __popc(hit[j]);
     }
     if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) *d_count = pre + tot;
 }
 
 // Launch select_kernel over [0, n); *d_count receives the number of hits.
 // A bounded wait that expires sets *err_word (device int) when given.
-template <class Op, int BLOCK = 256, int ITEMS = 4>
+template <class Op, int BLOCK = 256, int ITEMS = GSMAT_SELECT_ITEMS>
 int run_select(const Op &op, int64_t n, int64_t *d_count, cudaStream_t st, int *err_word) {
     if (n <= 0) {
         GS_CUDA(cudaMemsetAsync(d_count, 0, sizeof(int64_t), st));

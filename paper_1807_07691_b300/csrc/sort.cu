@@ -36,21 +36,26 @@ namespace {
 #ifndef GSMAT_PASS_MIN_BLOCKS
 #define GSMAT_PASS_MIN_BLOCKS 4
 #endif
+#ifndef GSMAT_PASS_MIN_BLOCKS_KEYS
+#define GSMAT_PASS_MIN_BLOCKS_KEYS 3  // 64-bit keys without a payload
+#endif
 #ifndef GSMAT_PASS_ITEMS_U64
 #define GSMAT_PASS_ITEMS_U64 12
 #endif
 #ifndef GSMAT_PASS_ITEMS_U64_KEYS
-#define GSMAT_PASS_ITEMS_U64_KEYS 16
+#define GSMAT_PASS_ITEMS_U64_KEYS 20
 #endif
 #ifndef GSMAT_PASS_ITEMS_WIDE
 #define GSMAT_PASS_ITEMS_WIDE 10
+#endif
+#ifndef GSMAT_RANK_BALLOT
+#define GSMAT_RANK_BALLOT 1  // peers of a digit from 8 ballots (0: match_any)
 #endif
 #ifndef GSMAT_LOOKBACK_WINDOW
 #define GSMAT_LOOKBACK_WINDOW 8
 #endif
 constexpr int kBlock = 256;               // histogram kernel
 constexpr int kPassBlock = 256;           // pass kernel (a multiple of kBins)
-constexpr int kPassMinBlocks = GSMAT_PASS_MIN_BLOCKS;  // pass CTAs resident per SM (register budget)
 constexpr int kPassWarps = kPassBlock / 32;
 constexpr int kBins = 256;
 constexpr int kMaxPasses = 8;
@@ -73,6 +78,12 @@ struct SortTraits<uint32_t> {
 template <class K, bool HasVals, class V = uint32_t>
 __host__ __device__ constexpr int items_per_thread() {
     return HasVals ? (sizeof(V) == 8 ? GSMAT_PASS_ITEMS_WIDE : SortTraits<K>::kItems) : SortTraits<K>::kItemsKeysOnly;
+}
+
+// Pass CTAs resident per SM (the register budget of the launch bounds).
+template <class K, bool HasVals, class V = uint32_t>
+__host__ __device__ constexpr int pass_min_blocks() {
+    return (!HasVals && sizeof(K) == 8) ? GSMAT_PASS_MIN_BLOCKS_KEYS : GSMAT_PASS_MIN_BLOCKS;
 }
 
 template <class K>
@@ -475,7 +486,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_histogram(Src src, int64_t n,
 }
 
 template <class K, bool HasVals, class Src, class Sink>
-__global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src src, Sink sink, int64_t n, int shift, int mask,
+__global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typename Src::Val>())) onesweep_pass(Src src, Sink sink, int64_t n, int shift, int mask,
                                                        const uint32_t *__restrict__ hist_pass,
                                                        unsigned long long *__restrict__ desc,
                                                        unsigned int *__restrict__ tile_counter, uint32_t epoch,
@@ -521,7 +532,18 @@ __global__ void __launch_bounds__(kPassBlock, kPassMinBlocks) onesweep_pass(Src 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int d = (int)dr[j];
+#if GSMAT_RANK_BALLOT
+        // lanes whose digit agrees with this lane's in every bit
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const bool bit = (d >> b) & 1;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+#else
         const unsigned peers = __match_any_sync(0xffffffffu, d);
+#endif
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
         if (lane == leader) base = atomicAdd(&wh[d], (uint32_t)__popc(peers));

@@ -111,7 +111,10 @@ __global__ void extract_pred_kernel(const int32_t *__restrict__ tri, int64_t n, 
 struct DistinctU32Op {
     const uint32_t *a;
     int32_t *out;
-    __device__ bool flag(int64_t i) const { return i == 0 || a[i] != a[i - 1]; }
+    __device__ bool flag(int64_t i) const {
+        const int64_t h = i > 0 ? i - 1 : 0;  // branch-free: both loads issue at once
+        return (i == 0) | (a[i] != a[h]);
+    }
     __device__ void emit(int64_t i, int64_t j) const { out[j] = (int32_t)a[i]; }
 };
 
@@ -199,7 +202,8 @@ struct DedupeOp {
     const int32_t *a, *b, *c;
     int32_t *oa, *ob, *oc;
     __device__ bool flag(int64_t i) const {
-        return i == 0 || a[i] != a[i - 1] || b[i] != b[i - 1] || c[i] != c[i - 1];
+        const int64_t h = i > 0 ? i - 1 : 0;
+        return (i == 0) | (a[i] != a[h]) | (b[i] != b[h]) | (c[i] != c[h]);
     }
     __device__ void emit(int64_t i, int64_t j) const {
         oa[j] = a[i];
@@ -215,7 +219,10 @@ struct DedupeKeysOp {
     int32_t *s0, *o0, *slot0;
     uint64_t *k1;
     int bits;
-    __device__ bool flag(int64_t i) const { return i == 0 || keys[i] != keys[i - 1]; }
+    __device__ bool flag(int64_t i) const {
+        const int64_t h = i > 0 ? i - 1 : 0;
+        return (i == 0) | (keys[i] != keys[h]);
+    }
     __device__ void emit(int64_t i, int64_t j) const {
         const uint64_t k = keys[i];
         const uint64_t m = (1ull << bits) - 1;
@@ -230,23 +237,38 @@ struct DedupeKeysOp {
 // Non-zero rows: the first entry of every (slot, key) run.
 struct RowStartOp {
     const int32_t *key, *slot;
-    int32_t *rowid, *rowoff, *rowslot;
-    __device__ bool flag(int64_t i) const { return i == 0 || key[i] != key[i - 1] || slot[i] != slot[i - 1]; }
+    int32_t *rowid, *rowoff;
+    __device__ bool flag(int64_t i) const {
+        const int64_t h = i > 0 ? i - 1 : 0;
+        return (i == 0) | (key[i] != key[h]) | (slot[i] != slot[h]);
+    }
     __device__ void emit(int64_t i, int64_t j) const {
         rowid[j] = key[i];
         rowoff[j] = (int32_t)i;
-        rowslot[j] = slot[i];
     }
 };
 
-__global__ void pred_bounds_kernel(const int32_t *__restrict__ rowslot, const int32_t *__restrict__ rowoff, int64_t R,
-                                   int32_t *__restrict__ ent_base, int32_t *__restrict__ row_base) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < R; j += (int64_t)gridDim.x * blockDim.x) {
-        if (j == 0 || rowslot[j] != rowslot[j - 1]) {
-            ent_base[rowslot[j]] = rowoff[j];
-            row_base[rowslot[j]] = (int32_t)j;
-        }
+// Per predicate p in [0, P]: its first entry (the first index of the
+// ascending slot column at or above p) and its first row (the first row
+// starting at or after that entry).
+__global__ void pred_bounds_kernel(const int32_t *__restrict__ slot, int64_t n, const int32_t *__restrict__ rowoff,
+                                   int64_t R, int P, int32_t *__restrict__ ent_base, int32_t *__restrict__ row_base) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > P) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (slot[mid] < p) lo = mid + 1; else hi = mid;
     }
+    const int32_t e = (int32_t)lo;
+    lo = 0;
+    hi = R;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (rowoff[mid] < e) lo = mid + 1; else hi = mid;
+    }
+    ent_base[p] = e;
+    row_base[p] = (int32_t)lo;
 }
 
 // Dense row pointers of several predicates in one launch:
@@ -284,8 +306,9 @@ __global__ void __launch_bounds__(kThreads) dense_fill_kernel(const int32_t *__r
                                                               const DensePart *__restrict__ parts, int n_parts,
                                                               int64_t n_chunks, int64_t len,
                                                               int32_t *__restrict__ dense) {
-    __shared__ int32_t s_off[kDenseWarps][kDenseChunk + 1];  // first entries of the chunk's rows (+ the next row)
-    __shared__ int16_t s_pre[kDenseWarps][kDenseChunk];      // marks, then their exclusive prefix
+    __shared__ int32_t s_off[kDenseWarps][kDenseChunk + 1];            // first entries of the chunk's rows (+ the next row)
+    __shared__ __align__(16) int16_t s_pre[kDenseWarps][kDenseChunk];  // marks, then their exclusive prefix
+    constexpr int kPer = kDenseChunk / 32;                              // x values (and candidate rows) per lane
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int32_t *off = s_off[wid];
     int16_t *pre = s_pre[wid];
@@ -309,34 +332,47 @@ __global__ void __launch_bounds__(kThreads) dense_fill_kernel(const int32_t *__r
             const int64_t x0 = (c - P.chunk0) * kDenseChunk;
             const int32_t *ids = rowid + P.row_base;
             const int32_t *ro = rowoff + P.row_base;
-            for (int m = lane; m < kDenseChunk; m += 32) pre[m] = 0;
-            __syncwarp();
-            // the chunk's rows: [r0, r1)
-            int r1 = r0;
-            for (int i = 0;; i += 32) {
-                const int r = r0 + i + lane;
-                const int64_t id = r < P.nrows ? (int64_t)__ldg(ids + r) : INT64_MAX;
-                const bool in = id < x0 + kDenseChunk;
-                const unsigned m = __ballot_sync(0xffffffffu, in);
-                if (in) {
-                    pre[id - x0] = 1;
-                    off[i + lane] = __ldg(ro + r);
-                }
-                if (m != 0xffffffffu) {
-                    r1 = r0 + i + __popc(m);
-                    break;
-                }
+            // The chunk's rows are a prefix of [r0, r0 + 256) (ids ascend and
+            // are distinct): all 256 candidates' ids and first entries are
+            // loaded at once, so a chunk costs one memory latency.
+            int32_t id[kPer], fo[kPer];
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const int r = r0 + 32 * k + lane;
+                const bool ok = r < P.nrows;
+                id[k] = ok ? __ldg(ids + r) : INT32_MAX;
+                fo[k] = ok ? __ldg(ro + r) : 0;
             }
-            if (lane == 0) off[r1 - r0] = r1 < P.nrows ? __ldg(ro + r1) : P.end_entry;
+            *reinterpret_cast<int4 *>(pre + 8 * lane) = make_int4(0, 0, 0, 0);
+            __syncwarp();
+            int in_rows = 0;
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) {
+                const bool in = (int64_t)id[k] < x0 + kDenseChunk;
+                if (in) {
+                    pre[id[k] - x0] = 1;
+                    off[32 * k + lane] = fo[k];
+                }
+                in_rows += __popc(__ballot_sync(0xffffffffu, in));
+            }
+            const int r1 = r0 + in_rows;
+            if (lane == 0) off[in_rows] = r1 < P.nrows ? __ldg(ro + r1) : P.end_entry;
             __syncwarp();
             // exclusive prefix of the marks: lane l holds x0 + 8 l .. 8 l + 7
-            int v[kDenseChunk / 32];
+            // (one 16-byte shared-memory access each way)
+            const int4 q = *reinterpret_cast<const int4 *>(pre + 8 * lane);
+            int v[kPer];
+            {
+                const int32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    v[2 * t] = (int16_t)(w[t] & 0xffff);
+                    v[2 * t + 1] = (int16_t)((uint32_t)w[t] >> 16);
+                }
+            }
             int sum = 0;
 #pragma unroll
-            for (int t = 0; t < kDenseChunk / 32; ++t) {
-                v[t] = pre[lane * (kDenseChunk / 32) + t];
-                sum += v[t];
-            }
+            for (int t = 0; t < kPer; ++t) sum += v[t];
             int inc = sum;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -344,15 +380,20 @@ __global__ void __launch_bounds__(kThreads) dense_fill_kernel(const int32_t *__r
                 if (lane >= d) inc += y;
             }
             int run_sum = inc - sum;
-            __syncwarp();
+            int32_t w[4];
 #pragma unroll
-            for (int t = 0; t < kDenseChunk / 32; ++t) {
-                pre[lane * (kDenseChunk / 32) + t] = (int16_t)run_sum;
-                run_sum += v[t];
+            for (int t = 0; t < 4; ++t) {
+                const int lo16 = run_sum;
+                run_sum += v[2 * t];
+                const int hi16 = run_sum;
+                run_sum += v[2 * t + 1];
+                w[t] = (int32_t)(((uint32_t)hi16 << 16) | ((uint32_t)lo16 & 0xffffu));
             }
             __syncwarp();
+            *reinterpret_cast<int4 *>(pre + 8 * lane) = make_int4(w[0], w[1], w[2], w[3]);
+            __syncwarp();
 #pragma unroll
-            for (int k = 0; k < kDenseChunk / 32; ++k) {
+            for (int k = 0; k < kPer; ++k) {
                 const int xi = lane + 32 * k;
                 const int64_t x = x0 + xi;
                 if (x < len) dense[P.dense_base + x] = off[pre[xi]];
@@ -403,12 +444,11 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
 int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t *slot, int64_t n, int *err,
                cudaStream_t st, PhaseTimer &pt) {
     const int P = S->n_pred;
-    DevBuf rid, roff, rslot, cnt, bases;
+    DevBuf rid, roff, cnt, bases;
     GS_TRY(rid.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(roff.alloc(sizeof(int32_t) * (size_t)(n + 1), st));
-    GS_TRY(rslot.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(cnt.alloc(sizeof(int64_t), st));
-    RowStartOp op{key.as<int32_t>(), slot, rid.as<int32_t>(), roff.as<int32_t>(), rslot.as<int32_t>()};
+    RowStartOp op{key.as<int32_t>(), slot, rid.as<int32_t>(), roff.as<int32_t>()};
     GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
     int64_t *h = pinned_scratch(4);
     if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
@@ -418,23 +458,18 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     pt.resume();
     const int64_t R = h[0];
     pt.add_bytes(8.0 * (double)R);  // Row and Rpos of the side's non-zero rows
-    // exact-size auxiliary arrays, rowoff with its sentinel
-    GS_TRY(S->rowid[side].alloc(sizeof(int32_t) * (size_t)R, st));
-    GS_TRY(S->rowoff[side].alloc(sizeof(int32_t) * (size_t)(R + 1), st));
-    if (R > 0) {
-        GS_CUDA(cudaMemcpyAsync(S->rowid[side].p, rid.p, sizeof(int32_t) * (size_t)R, cudaMemcpyDeviceToDevice, st));
-        GS_CUDA(cudaMemcpyAsync(S->rowoff[side].p, roff.p, sizeof(int32_t) * (size_t)R, cudaMemcpyDeviceToDevice, st));
-    }
+    // the selection's buffers become the side's row arrays (sized for n
+    // rows: no copy to exact size); rowoff gets its sentinel
+    S->rowid[side] = std::move(rid);
+    S->rowoff[side] = std::move(roff);
     const int32_t sentinel = (int32_t)n;
     GS_CUDA(cudaMemcpyAsync(S->rowoff[side].as<int32_t>() + R, &sentinel, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     // per predicate: first entry and first row
     GS_TRY(bases.alloc(sizeof(int32_t) * 2 * (size_t)(P + 1), st));
     int32_t *ent_base = bases.as<int32_t>(), *row_base = ent_base + (P + 1);
-    if (R > 0) {
-        pred_bounds_kernel<<<grid_for(R), kThreads, 0, st>>>(rslot.as<int32_t>(), roff.as<int32_t>(), R, ent_base,
-                                                             row_base);
-        GS_LAUNCH_CHECK();
-    }
+    pred_bounds_kernel<<<(P + 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(slot, n, S->rowoff[side].as<int32_t>(), R,
+                                                                                P, ent_base, row_base);
+    GS_LAUNCH_CHECK();
     std::vector<int32_t> hb(2 * (size_t)(P + 1));
     GS_CUDA(cudaMemcpyAsync(hb.data(), bases.p, sizeof(int32_t) * hb.size(), cudaMemcpyDeviceToHost, st));
     pt.pause();
@@ -451,10 +486,12 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
         ps.nrows = hb[(P + 1) + p + 1] - hb[(P + 1) + p];
         ps.dense_base = -1;
     }
-    // Dense row pointers (max_entity + 2 words each) for the predicates with
-    // the most entries, while their total stays within 4x the side's entry
-    // bytes (16 bytes per entry); the others find rows by binary search.
+    // Dense row pointers (max_entity + 2 words each, at a multiple of 4
+    // words) for the predicates with the most entries, while their total
+    // stays within 4x the side's entry bytes (16 bytes per entry); the
+    // others find rows by binary search.
     const int64_t len = (int64_t)S->max_entity + 2;
+    const int64_t stride = (len + 3) & ~int64_t(3);
     std::vector<int> by_nnz(P);
     for (int p = 0; p < P; ++p) by_nnz[p] = p;
     std::stable_sort(by_nnz.begin(), by_nnz.end(),
@@ -464,9 +501,9 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     if (S->max_entity >= 0) {
         for (int p : by_nnz) {
             PredSide &ps = S->side[side][p];
-            if (ps.nnz == 0 || (total + len) * 4 > budget) continue;
+            if (ps.nnz == 0 || (total + stride) * 4 > budget) continue;
             ps.dense_base = total;
-            total += len;
+            total += stride;
         }
     }
     S->n_dense[side] = 0;
