@@ -37,19 +37,26 @@ namespace {
 #define GSMAT_PASS_MIN_BLOCKS 4
 #endif
 #ifndef GSMAT_PASS_MIN_BLOCKS_KEYS
-#define GSMAT_PASS_MIN_BLOCKS_KEYS 3  // 64-bit keys without a payload
+#define GSMAT_PASS_MIN_BLOCKS_KEYS 2  // 64-bit keys without a payload
 #endif
 #ifndef GSMAT_PASS_ITEMS_U64
 #define GSMAT_PASS_ITEMS_U64 12
 #endif
 #ifndef GSMAT_PASS_ITEMS_U64_KEYS
-#define GSMAT_PASS_ITEMS_U64_KEYS 20
+#define GSMAT_PASS_ITEMS_U64_KEYS 24
 #endif
 #ifndef GSMAT_PASS_ITEMS_WIDE
 #define GSMAT_PASS_ITEMS_WIDE 10
 #endif
-#ifndef GSMAT_RANK_BALLOT
-#define GSMAT_RANK_BALLOT 1  // peers of a digit from 8 ballots (0: match_any)
+// How a warp finds the lanes whose key has its digit ("peers"): 1 from
+// eight ballots, 2 by a shared-memory atomicOr of lane bits per digit, 0 by
+// match_any.  Measured on B300: 2 is the fastest for 64-bit keys without a
+// payload (8 % over 1), 1 for the rest (2-3 % over 2, 10 % over 0).
+#ifndef GSMAT_RANK_KEYS
+#define GSMAT_RANK_KEYS 2
+#endif
+#ifndef GSMAT_RANK_PAIRS
+#define GSMAT_RANK_PAIRS 1
 #endif
 #ifndef GSMAT_LOOKBACK_WINDOW
 #define GSMAT_LOOKBACK_WINDOW 8
@@ -78,6 +85,11 @@ struct SortTraits<uint32_t> {
 template <class K, bool HasVals, class V = uint32_t>
 __host__ __device__ constexpr int items_per_thread() {
     return HasVals ? (sizeof(V) == 8 ? GSMAT_PASS_ITEMS_WIDE : SortTraits<K>::kItems) : SortTraits<K>::kItemsKeysOnly;
+}
+
+template <class K, bool HasVals, class V = uint32_t>
+__host__ __device__ constexpr int rank_mode() {
+    return (!HasVals && sizeof(K) == 8) ? GSMAT_RANK_KEYS : GSMAT_RANK_PAIRS;
 }
 
 // Pass CTAs resident per SM (the register budget of the launch bounds).
@@ -454,15 +466,24 @@ __global__ void __launch_bounds__(256) gather_rest_kernel(Cols rest, OutCols out
     gather_columns(rest, out, n_rest, perm, n);
 }
 
-// Digit counts of every pass in one read of the keys: a CTA-wide shared
-// histogram per pass, each thread keeping kHistItems keys' loads in flight.
+// Digit counts of every pass in one read of the keys: CTA-wide shared
+// histograms, each thread keeping kHistItems keys' loads in flight.  With
+// kHistCopies > 1 lane l counts into copy l % kHistCopies, the copies a
+// bank apart, so lanes with the same digit contend fewer ways on one word.
 constexpr int kHistItems = 8;
+#ifndef GSMAT_HIST_COPIES
+#define GSMAT_HIST_COPIES 1
+#endif
+constexpr int kHistCopies = GSMAT_HIST_COPIES;
+__host__ __device__ constexpr int hist_stride(int n_pass) { return n_pass * kBins + 1; }
 template <class K, class Src>
 __global__ void __launch_bounds__(kBlock) onesweep_histogram(Src src, int64_t n, int begin_bit, int end_bit,
                                                             int n_pass, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t hsm[kMaxPasses * kBins];
-    for (int i = threadIdx.x; i < n_pass * kBins; i += kBlock) hsm[i] = 0;
+    extern __shared__ uint32_t hsm[];  // [kHistCopies][hist_stride(n_pass)]
+    const int stride = hist_stride(n_pass);
+    for (int i = threadIdx.x; i < kHistCopies * stride; i += kBlock) hsm[i] = 0;
     __syncthreads();
+    uint32_t *mine = hsm + (threadIdx.x % kHistCopies) * stride;
     const int64_t span = (int64_t)kBlock * kHistItems;
     for (int64_t base = blockIdx.x * span + threadIdx.x; base < n; base += (int64_t)gridDim.x * span) {
         K k[kHistItems];
@@ -473,14 +494,16 @@ __global__ void __launch_bounds__(kBlock) onesweep_histogram(Src src, int64_t n,
                 for (int p = 0; p < n_pass; ++p) {
                     const int shift = begin_bit + 8 * p;
                     const int width = end_bit - shift < 8 ? end_bit - shift : 8;
-                    atomicAdd(&hsm[p * kBins + digit_of(k[j], shift, (1 << width) - 1)], 1u);
+                    atomicAdd(&mine[p * kBins + digit_of(k[j], shift, (1 << width) - 1)], 1u);
                 }
             }
         }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_pass * kBins; i += kBlock) {
-        const uint32_t c = hsm[i];
+        uint32_t c = 0;
+#pragma unroll
+        for (int cp = 0; cp < kHistCopies; ++cp) c += hsm[cp * stride + i];
         if (c) atomicAdd(hist + i, c);
     }
 }
@@ -500,12 +523,17 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
     uint32_t *whist = reinterpret_cast<uint32_t *>(svals + (HasVals ? TILE : 0));  // [kPassWarps][kBins]
     uint32_t *tstart = whist + kPassWarps * kBins;
     uint32_t *gbase = tstart + kBins;
+    constexpr int RANK = rank_mode<K, HasVals, V>();
+    uint32_t *wmask = gbase + kBins;  // RANK 2: [kPassWarps][kBins] lane masks by digit
     __shared__ int64_t scan_tmp[kPassWarps + 1];
     __shared__ int tile_sm;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) tile_sm = (int)atomicAdd(tile_counter, 1u);
     for (int i = threadIdx.x; i < kPassWarps * kBins; i += kPassBlock) whist[i] = 0;
+    if (RANK == 2) {
+        for (int i = threadIdx.x; i < kPassWarps * kBins; i += kPassBlock) wmask[i] = 0;
+    }
     __syncthreads();
     const int tile = tile_sm;
     const int64_t t0 = (int64_t)tile * TILE;
@@ -532,18 +560,27 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int d = (int)dr[j];
-#if GSMAT_RANK_BALLOT
-        // lanes whose digit agrees with this lane's in every bit
-        unsigned peers = 0xffffffffu;
+        unsigned peers;
+        if (RANK == 2) {
+            // every lane sets its bit in its digit's word; the word then holds the peers
+            uint32_t *wm = wmask + warp * kBins;
+            atomicOr(&wm[d], 1u << lane);
+            __syncwarp();
+            peers = wm[d];
+            __syncwarp();
+            if ((peers & lt_mask) == 0) wm[d] = 0;  // the leader clears it for the next round
+        } else if (RANK == 1) {
+            // lanes whose digit agrees with this lane's in every bit
+            peers = 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const bool bit = (d >> b) & 1;
-            const unsigned bal = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bal : ~bal;
+            for (int b = 0; b < 8; ++b) {
+                const bool bit = (d >> b) & 1;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
+        } else {
+            peers = __match_any_sync(0xffffffffu, d);
         }
-#else
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-#endif
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
         if (lane == leader) base = atomicAdd(&wh[d], (uint32_t)__popc(peers));
@@ -666,7 +703,8 @@ int sm_count() {
 template <class K, bool HasVals, class V>
 int pass_smem_bytes() {
     constexpr int TILE = kPassBlock * items_per_thread<K, HasVals, V>();
-    return TILE * (int)sizeof(K) + (HasVals ? TILE * (int)sizeof(V) : 0) + (kPassWarps * kBins + 2 * kBins) * 4;
+    return TILE * (int)sizeof(K) + (HasVals ? TILE * (int)sizeof(V) : 0) +
+           (kPassWarps * kBins * (rank_mode<K, HasVals, V>() == 2 ? 2 : 1) + 2 * kBins) * 4;
 }
 
 int current_device() {
@@ -703,10 +741,21 @@ int launch_histogram(const Src &src, int64_t n, int begin_bit, int end_bit, int 
                      cudaStream_t st) {
     const int64_t span = (int64_t)kBlock * kHistItems;
     int64_t g = (n + span - 1) / span;
-    const int64_t cap = (int64_t)sm_count() * 8;
+    const int smem = kHistCopies * hist_stride(n_pass) * (int)sizeof(uint32_t);
+    const int64_t per_sm = std::max(1, std::min(8, (200 * 1024) / smem));  // resident CTAs
+    const int64_t cap = (int64_t)sm_count() * per_sm;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    onesweep_histogram<K, Src><<<(unsigned)g, kBlock, 0, st>>>(src, n, begin_bit, end_bit, n_pass, hist);
+    if (smem > 48 * 1024) {
+        static std::atomic<bool> done[64];  // attribute set (once per device)
+        const int dev = current_device();
+        if (!done[dev].load(std::memory_order_acquire)) {
+            GS_CUDA(cudaFuncSetAttribute(onesweep_histogram<K, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kHistCopies * hist_stride(kMaxPasses) * (int)sizeof(uint32_t)));
+            done[dev].store(true, std::memory_order_release);
+        }
+    }
+    onesweep_histogram<K, Src><<<(unsigned)g, kBlock, smem, st>>>(src, n, begin_bit, end_bit, n_pass, hist);
     GS_LAUNCH_CHECK();
     return GSMAT_OK;
 }
