@@ -212,25 +212,54 @@ struct DedupeOp {
     }
 };
 
-// Distinct keys of a sorted (slot, s, o) key array: side 0's columns (key
-// = s, val = o, slot) and side 1's key (slot, o, s), in one pass.
-struct DedupeKeysOp {
+// Distinct keys of a sorted (slot, s, o) key array and, among them, the
+// first of every (slot, s) row, in one pass (two nested selections): side
+// 0's columns (key = s, val = o) and rows (Row = s, Rpos = first entry),
+// and side 1's key (slot, o, s) for every distinct key.
+struct DedupeRowsOp {
     const uint64_t *keys;
-    int32_t *s0, *o0, *slot0;
+    int32_t *s0, *o0, *rowid, *rowoff;
     uint64_t *k1;
     int bits;
-    __device__ bool flag(int64_t i) const {
+    __device__ void flags(int64_t i, bool &f1, bool &f2) const {
         const int64_t h = i > 0 ? i - 1 : 0;
-        return (i == 0) | (keys[i] != keys[h]);
+        const uint64_t k = keys[i], kp = keys[h];
+        f1 = (i == 0) | (k != kp);
+        f2 = (i == 0) | ((k >> bits) != (kp >> bits));
     }
-    __device__ void emit(int64_t i, int64_t j) const {
+    __device__ void emit(int64_t i, int64_t j1, int64_t j2) const {
         const uint64_t k = keys[i];
         const uint64_t m = (1ull << bits) - 1;
         const uint64_t o = k & m, s = (k >> bits) & m, slot = k >> (2 * bits);
-        s0[j] = (int32_t)s;
-        o0[j] = (int32_t)o;
-        slot0[j] = (int32_t)slot;
-        k1[j] = (slot << (2 * bits)) | (o << bits) | s;
+        s0[j1] = (int32_t)s;
+        o0[j1] = (int32_t)o;
+        k1[j1] = (slot << (2 * bits)) | (o << bits) | s;
+        if (j2 >= 0) {
+            rowid[j2] = (int32_t)s;
+            rowoff[j2] = (int32_t)j1;
+        }
+    }
+};
+
+// Side 1 from its sorted (slot, o, s) keys in one pass: every entry's
+// columns (key = o, val = s) and the first entry of every (slot, o) row.
+struct RowsUnpackOp {
+    const uint64_t *keys;
+    int32_t *o1, *s1, *rowid, *rowoff;
+    int bits;
+    __device__ bool flag(int64_t i) const {
+        const int64_t h = i > 0 ? i - 1 : 0;
+        return (i == 0) | ((keys[i] >> bits) != (keys[h] >> bits));
+    }
+    __device__ void visit(int64_t i) const {
+        const uint64_t k = keys[i];
+        const uint64_t m = (1ull << bits) - 1;
+        o1[i] = (int32_t)((k >> bits) & m);
+        s1[i] = (int32_t)(k & m);
+    }
+    __device__ void emit(int64_t i, int64_t j) const {
+        rowid[j] = (int32_t)((keys[i] >> bits) & ((1ull << bits) - 1));
+        rowoff[j] = (int32_t)i;
     }
 };
 
@@ -248,17 +277,26 @@ struct RowStartOp {
     }
 };
 
-// Per predicate p in [0, P]: its first entry (the first index of the
-// ascending slot column at or above p) and its first row (the first row
-// starting at or after that entry).
-__global__ void pred_bounds_kernel(const int32_t *__restrict__ slot, int64_t n, const int32_t *__restrict__ rowoff,
-                                   int64_t R, int P, int32_t *__restrict__ ent_base, int32_t *__restrict__ row_base) {
+// The predicate slot of entry i: a slot column, or the top bits of packed
+// keys.  Either is ascending.
+struct SlotSrc {
+    const int32_t *col;
+    const uint64_t *keys;
+    int shift;
+    __device__ int32_t at(int64_t i) const { return col ? col[i] : (int32_t)(keys[i] >> shift); }
+};
+
+// Per predicate p in [0, P]: its first entry (the first index whose slot is
+// at or above p) and its first row (the first row starting at or after that
+// entry).
+__global__ void pred_bounds_kernel(SlotSrc slot, int64_t n, const int32_t *__restrict__ rowoff, int64_t R, int P,
+                                   int32_t *__restrict__ ent_base, int32_t *__restrict__ row_base) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p > P) return;
     int64_t lo = 0, hi = n;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (slot[mid] < p) lo = mid + 1; else hi = mid;
+        if (slot.at(mid) < p) lo = mid + 1; else hi = mid;
     }
     const int32_t e = (int32_t)lo;
     lo = 0;
@@ -443,23 +481,13 @@ int sort_rows3(const int32_t *a, const int32_t *b, const int32_t *c, int64_t n, 
     return GSMAT_OK;
 }
 
-// Build one side from entries sorted by (slot, key, val).
-int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t *slot, int64_t n, int *err,
-               cudaStream_t st, PhaseTimer &pt) {
+// A side's predicate bounds and dense row pointers once its columns and
+// row arrays (R rows; rid and roff sized for n rows, roff + 1) are built;
+// the buffers move into the store.
+int finish_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, DevBuf &rid, DevBuf &roff, int64_t R, SlotSrc slot,
+                int64_t n, cudaStream_t st, PhaseTimer &pt) {
     const int P = S->n_pred;
-    DevBuf rid, roff, cnt, bases;
-    GS_TRY(rid.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(roff.alloc(sizeof(int32_t) * (size_t)(n + 1), st));
-    GS_TRY(cnt.alloc(sizeof(int64_t), st));
-    RowStartOp op{key.as<int32_t>(), slot, rid.as<int32_t>(), roff.as<int32_t>()};
-    GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
-    int64_t *h = pinned_scratch(4);
-    if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
-    GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    pt.pause();
-    GS_CUDA(cudaStreamSynchronize(st));
-    pt.resume();
-    const int64_t R = h[0];
+    DevBuf bases;
     pt.add_bytes(8.0 * (double)R);  // Row and Rpos of the side's non-zero rows
     // the selection's buffers become the side's row arrays (sized for n
     // rows: no copy to exact size); rowoff gets its sentinel
@@ -550,6 +578,24 @@ int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t
     return GSMAT_OK;
 }
 
+// Build one side from entries sorted by (slot, key, val) in columns.
+int build_side(gsmat_store *S, int side, DevBuf &key, DevBuf &val, const int32_t *slot, int64_t n, int *err,
+               cudaStream_t st, PhaseTimer &pt) {
+    DevBuf rid, roff, cnt;
+    GS_TRY(rid.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(roff.alloc(sizeof(int32_t) * (size_t)(n + 1), st));
+    GS_TRY(cnt.alloc(sizeof(int64_t), st));
+    RowStartOp op{key.as<int32_t>(), slot, rid.as<int32_t>(), roff.as<int32_t>()};
+    GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
+    int64_t *h = pinned_scratch(4);
+    if (!h) return set_error(GSMAT_ERR_CUDA, "pinned host scratch");
+    GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    pt.pause();
+    GS_CUDA(cudaStreamSynchronize(st));
+    pt.resume();
+    return finish_side(S, side, key, val, rid, roff, h[0], SlotSrc{slot, nullptr, 0}, n, st, pt);
+}
+
 // Both sides from (slot, s, o) columns, for ids too wide for one packed key
 // (the sorts then run as two stable passes over narrower keys).
 int build_columns(gsmat_store *S, const int32_t *tri, int64_t n, int id_bits, int slot_bits, DevBuf &d_tri_own,
@@ -632,38 +678,48 @@ int build_packed(gsmat_store *S, const int32_t *tri, int64_t n, int id_bits, int
     uint64_t *sorted0 = nullptr;
     GS_TRY(radix_sort_u64_pingpong(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, key_bits, st, err, &sorted0));
     uint64_t *k1 = sorted0 == ka.as<uint64_t>() ? kb.as<uint64_t>() : ka.as<uint64_t>();
-    // side 0 columns sized n (an upper bound of the distinct count)
-    DevBuf key0, val0, slot0;
+    // side 0: columns and rows sized n (an upper bound of the distinct count)
+    DevBuf key0, val0, rid0, roff0;
     GS_TRY(key0.alloc(sizeof(int32_t) * (size_t)n, st));
     GS_TRY(val0.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(slot0.alloc(sizeof(int32_t) * (size_t)n, st));
-    GS_TRY(cnt.alloc(sizeof(int64_t), st));
+    GS_TRY(rid0.alloc(sizeof(int32_t) * (size_t)n, st));
+    GS_TRY(roff0.alloc(sizeof(int32_t) * (size_t)(n + 1), st));
+    GS_TRY(cnt.alloc(2 * sizeof(int64_t), st));
     {
-        DedupeKeysOp op{sorted0, key0.as<int32_t>(), val0.as<int32_t>(), slot0.as<int32_t>(), k1, id_bits};
-        GS_TRY(run_select(op, n, cnt.as<int64_t>(), st, err));
+        DedupeRowsOp op{sorted0, key0.as<int32_t>(), val0.as<int32_t>(), rid0.as<int32_t>(), roff0.as<int32_t>(), k1,
+                        id_bits};
+        GS_TRY(run_select2(op, n, cnt.as<int64_t>(), st, err));
+        GS_CUDA(cudaMemcpyAsync(h, cnt.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        pt.pause();
+        GS_CUDA(cudaStreamSynchronize(st));
+        pt.resume();
+    }
+    const int64_t nu = h[0], R0 = h[1];
+    S->n_unique = nu;
+    pt.add_bytes(8.0 * (double)nu);  // the two sides' entry columns
+    // side 0's bounds read the slots from k1 (still in side 0's order)
+    GS_TRY(finish_side(S, 0, key0, val0, rid0, roff0, R0, SlotSrc{nullptr, k1, 2 * id_bits}, nu, st, pt));
+    uint64_t *sorted1 = nullptr;
+    GS_TRY(radix_sort_u64_pingpong(k1, sorted0, nu, id_bits, key_bits, st, err, &sorted1));
+    // side 1: columns and rows from the sorted keys in one pass
+    const size_t m = (size_t)(nu > 0 ? nu : 1);
+    DevBuf key1, val1, rid1, roff1;
+    GS_TRY(key1.alloc(sizeof(int32_t) * m, st));
+    GS_TRY(val1.alloc(sizeof(int32_t) * m, st));
+    GS_TRY(rid1.alloc(sizeof(int32_t) * m, st));
+    GS_TRY(roff1.alloc(sizeof(int32_t) * (m + 1), st));
+    {
+        RowsUnpackOp op{sorted1, key1.as<int32_t>(), val1.as<int32_t>(), rid1.as<int32_t>(), roff1.as<int32_t>(), id_bits};
+        GS_TRY(run_select(op, nu, cnt.as<int64_t>(), st, err));
         GS_CUDA(cudaMemcpyAsync(h, cnt.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         pt.pause();
         GS_CUDA(cudaStreamSynchronize(st));
         pt.resume();
     }
-    const int64_t nu = h[0];
-    S->n_unique = nu;
-    pt.add_bytes(8.0 * (double)nu);  // the two sides' entry columns
-    uint64_t *sorted1 = nullptr;
-    GS_TRY(radix_sort_u64_pingpong(k1, sorted0, nu, id_bits, key_bits, st, err, &sorted1));
-    DevBuf key1, val1, slot1;
-    GS_TRY(key1.alloc(sizeof(int32_t) * (size_t)(nu > 0 ? nu : 1), st));
-    GS_TRY(val1.alloc(sizeof(int32_t) * (size_t)(nu > 0 ? nu : 1), st));
-    GS_TRY(slot1.alloc(sizeof(int32_t) * (size_t)(nu > 0 ? nu : 1), st));
-    if (nu > 0) {
-        unpack_kernel<<<grid_for(nu), kThreads, 0, st>>>(sorted1, nu, id_bits, key1.as<int32_t>(), val1.as<int32_t>(),
-                                                         slot1.as<int32_t>());
-        GS_LAUNCH_CHECK();
-    }
+    const int64_t R1 = h[0];
+    GS_TRY(finish_side(S, 1, key1, val1, rid1, roff1, R1, SlotSrc{nullptr, sorted1, 2 * id_bits}, nu, st, pt));
     ka.release();
     kb.release();
-    GS_TRY(build_side(S, 0, key0, val0, slot0.as<int32_t>(), nu, err, st, pt));
-    GS_TRY(build_side(S, 1, key1, val1, slot1.as<int32_t>(), nu, err, st, pt));
     return GSMAT_OK;
 }
 
