@@ -521,8 +521,7 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
     K *skeys = reinterpret_cast<K *>(smem_raw);
     V *svals = reinterpret_cast<V *>(skeys + TILE);
     uint32_t *whist = reinterpret_cast<uint32_t *>(svals + (HasVals ? TILE : 0));  // [kPassWarps][kBins]
-    uint32_t *tstart = whist + kPassWarps * kBins;
-    uint32_t *gbase = tstart + kBins;
+    uint32_t *gbase = whist + kPassWarps * kBins;
     constexpr int RANK = rank_mode<K, HasVals, V>();
     uint32_t *wmask = gbase + kBins;  // RANK 2: [kPassWarps][kBins] lane masks by digit
     __shared__ int64_t scan_tmp[kPassWarps + 1];
@@ -619,13 +618,18 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
     }
     // tile-local start of every digit, then the tile staged in shared memory
     // in digit order (the keys leave the registers before the look-back)
+    // (each warp's counter of digit d becomes the staged position of its
+    // first key of d: the digit's tile start plus the earlier warps' keys)
     const int64_t ts = block_exclusive_sum<kPassBlock>((int64_t)cnt, scan_tmp, &tot);
-    if (dig) tstart[d] = (uint32_t)ts;
+    if (dig) {
+#pragma unroll
+        for (int w = 0; w < kPassWarps; ++w) whist[w * kBins + d] += (uint32_t)ts;
+    }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const uint32_t dd = dr[j] & 0xffu;
-        const uint32_t pos = tstart[dd] + wh[dd] + (dr[j] >> 8);
+        const uint32_t pos = wh[dd] + (dr[j] >> 8);
         skeys[pos] = k[j];
         if (HasVals) svals[pos] = v[j];
     }
@@ -704,7 +708,7 @@ template <class K, bool HasVals, class V>
 int pass_smem_bytes() {
     constexpr int TILE = kPassBlock * items_per_thread<K, HasVals, V>();
     return TILE * (int)sizeof(K) + (HasVals ? TILE * (int)sizeof(V) : 0) +
-           (kPassWarps * kBins * (rank_mode<K, HasVals, V>() == 2 ? 2 : 1) + 2 * kBins) * 4;
+           (kPassWarps * kBins * (rank_mode<K, HasVals, V>() == 2 ? 2 : 1) + kBins) * 4;
 }
 
 int current_device() {
