@@ -339,11 +339,11 @@ def plain_leg(args, gs, torch, name, triples, queries, stream, ws, local, steps,
 # named give the captures.
 TRAFFIC_RATIO = {
     # profiles/reorder_sort_q14_traffic.md: the 62 M-row reorder of the medium
-    # chain query q14, 11719.0 MB of DRAM traffic against 10917.8 MB algorithmic
-    "reorder_sort": (11719.0 / 10917.8, "profiles/reorder_sort_q14_traffic.md (one call: medium q14)"),
+    # chain query q14, 11621.2 MB of DRAM traffic against 10917.8 MB algorithmic
+    "reorder_sort": (11621.2 / 10917.8, "profiles/reorder_sort_q14_traffic.md (one call: medium q14)"),
     # profiles/radix_sort_keys60_traffic.md: a 2^28-key, 60-bit keys-only sort
-    # (the store build's shape), 42.1 GB of DRAM traffic against 34.4 GB
-    "radix_sort_u64": (42.1 / 34.4, "profiles/radix_sort_keys60_traffic.md (one call: 2^28 keys, 60 bits)"),
+    # (the store build's shape), 37.52 GB of DRAM traffic against 34.36 GB
+    "radix_sort_u64": (37.52 / 34.36, "profiles/radix_sort_keys60_traffic.md (one call: 2^28 keys, 60 bits)"),
     # profiles/product_fixed_star4_traffic.md: a 40.96 M-row product of four
     # constant rows, 592.4 MB of DRAM traffic against 819.2 MB algorithmic
     "product": (592.4 / 819.2, "profiles/product_fixed_star4_traffic.md (one call: 40.96 M-row star)"),
