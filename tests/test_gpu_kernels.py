@@ -138,3 +138,36 @@ def test_launch_count_counts_kernels(env):
     g.radix_sort_u64(keys, None, 0, 40)
     torch.cuda.synchronize()
     assert g.launch_count() - c0 == 1 + 5  # digit histogram + five 8-bit passes
+
+
+# Sorts of at least 2^23 keys with a payload run the large-sort pass shape
+# (larger tiles, atomicOr ranking); both sides of the threshold, and the
+# row reorder's carried (64-bit payload) and gathered (row-index payload)
+# paths above it.
+@pytest.mark.parametrize("n", [(1 << 23) - 1, (1 << 23) + 12_345])
+def test_radix_sort_pairs_large_shape(env, n):
+    g, torch = env
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 1 << 40, size=n, dtype=np.int64)
+    keys[: n // 4] = keys[7]  # a long run of equal keys: stability
+    vals = np.arange(n, dtype=np.uint32)
+    dk = torch.from_numpy(keys.copy()).cuda()
+    dv = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    g.radix_sort_u64(dk, dv, 0, 40)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(dk.cpu().numpy(), keys[order])
+    assert np.array_equal(dv.cpu().numpy().view(np.uint32), vals[order])
+
+
+@pytest.mark.parametrize("flags", [1, 2])  # carried, gathered
+def test_sort_rows_large_shape(env, flags):
+    g, torch = env
+    n, V, m, bits = 9_000_001, 4, 2, 21  # 42 key bits + a 24-bit row index exceed one word
+    rng = np.random.default_rng(77 + flags)
+    cols = [rng.integers(0, 1 << bits, size=n, dtype=np.int64).astype(np.int32) for _ in range(V)]
+    cols[0][: n // 3] = 5  # equal leading keys
+    d = [torch.from_numpy(c.copy()).cuda() for c in cols]
+    out = g.sort_rows(d, m, bits, flags=flags)
+    order = np.lexsort(cols[m - 1::-1])
+    for v in range(V):
+        assert np.array_equal(out[v].cpu().numpy(), cols[v][order]), v
