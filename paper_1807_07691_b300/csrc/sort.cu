@@ -58,6 +58,9 @@ namespace {
 #ifndef GSMAT_RANK_PAIRS
 #define GSMAT_RANK_PAIRS 1
 #endif
+#ifndef GSMAT_RANK_PAIRWISE
+#define GSMAT_RANK_PAIRWISE 1  // atomicOr ranking: two items per round, one mask table each
+#endif
 #ifndef GSMAT_LOOKBACK_WINDOW
 #define GSMAT_LOOKBACK_WINDOW 8
 #endif
@@ -550,7 +553,7 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
     uint32_t *whist = reinterpret_cast<uint32_t *>(svals + (HasVals ? TILE : 0));  // [kPassWarps][kBins]
     uint32_t *gbase = whist + kPassWarps * kBins;
     constexpr int RANK = rank_mode<K, HasVals, V, SHAPE>();
-    uint32_t *wmask = gbase + kBins;  // RANK 2: [kPassWarps][kBins] lane masks by digit
+    uint32_t *wmask = gbase + kBins;  // RANK 2: [kPassWarps][2][kBins] lane masks by digit
     __shared__ int64_t scan_tmp[kPassWarps + 1];
     __shared__ int tile_sm;
 
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
     if (threadIdx.x == 0) tile_sm = (int)atomicAdd(tile_counter, 1u);
     for (int i = threadIdx.x; i < kPassWarps * kBins; i += kPassBlock) whist[i] = 0;
     if (RANK == 2) {
-        for (int i = threadIdx.x; i < kPassWarps * kBins; i += kPassBlock) wmask[i] = 0;
+        for (int i = threadIdx.x; i < 2 * kPassWarps * kBins; i += kPassBlock) wmask[i] = 0;
     }
     __syncthreads();
     const int tile = tile_sm;
@@ -583,13 +586,40 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
             dr[j] = kBins - 1;  // padding ranks last in the last bucket
         }
     }
+    if constexpr (RANK == 2 && GSMAT_RANK_PAIRWISE && ITEMS % 2 == 0) {
+        // Two items per round, their lane bits in two tables, so the two
+        // chains of shared-memory operations overlap.  Item j's counter
+        // update is issued before item j + 1's, so equal digits keep the
+        // order (j, lane).
+        uint32_t *wa = wmask + warp * 2 * kBins, *wb = wa + kBins;
+#pragma unroll
+        for (int j = 0; j < ITEMS; j += 2) {
+            const int d0 = (int)dr[j], d1 = (int)dr[j + 1];
+            atomicOr(&wa[d0], 1u << lane);
+            atomicOr(&wb[d1], 1u << lane);
+            __syncwarp();
+            const unsigned p0 = wa[d0], p1 = wb[d1];
+            __syncwarp();
+            if ((p0 & lt_mask) == 0) wa[d0] = 0;  // each leader clears its word for the next round
+            if ((p1 & lt_mask) == 0) wb[d1] = 0;
+            const int l0 = __ffs(p0) - 1, l1 = __ffs(p1) - 1;
+            uint32_t b0 = 0, b1 = 0;
+            if (lane == l0) b0 = atomicAdd(&wh[d0], (uint32_t)__popc(p0));
+            if (lane == l1) b1 = atomicAdd(&wh[d1], (uint32_t)__popc(p1));
+            b0 = __shfl_sync(0xffffffffu, b0, l0);
+            b1 = __shfl_sync(0xffffffffu, b1, l1);
+            dr[j] = ((b0 + (uint32_t)__popc(p0 & lt_mask)) << 8) | (uint32_t)d0;
+            dr[j + 1] = ((b1 + (uint32_t)__popc(p1 & lt_mask)) << 8) | (uint32_t)d1;
+            __syncwarp();
+        }
+    } else {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
         const int d = (int)dr[j];
         unsigned peers;
         if (RANK == 2) {
             // every lane sets its bit in its digit's word; the word then holds the peers
-            uint32_t *wm = wmask + warp * kBins;
+            uint32_t *wm = wmask + warp * 2 * kBins;
             atomicOr(&wm[d], 1u << lane);
             __syncwarp();
             peers = wm[d];
@@ -613,6 +643,7 @@ __global__ void __launch_bounds__(kPassBlock, (pass_min_blocks<K, HasVals, typen
         base = __shfl_sync(0xffffffffu, base, leader);
         dr[j] = ((base + (uint32_t)__popc(peers & lt_mask)) << 8) | (uint32_t)d;
         __syncwarp();
+    }
     }
     __syncthreads();
     // per digit (thread d < kBins): cross-warp prefix and the tile's count
@@ -735,7 +766,7 @@ template <class K, bool HasVals, class V, int SHAPE = 0>
 int pass_smem_bytes() {
     constexpr int TILE = kPassBlock * items_per_thread<K, HasVals, V, SHAPE>();
     return TILE * (int)sizeof(K) + (HasVals ? TILE * (int)sizeof(V) : 0) +
-           (kPassWarps * kBins * (rank_mode<K, HasVals, V, SHAPE>() == 2 ? 2 : 1) + kBins) * 4;
+           (kPassWarps * kBins * (rank_mode<K, HasVals, V, SHAPE>() == 2 ? 3 : 1) + kBins) * 4;
 }
 
 int current_device() {
