@@ -52,7 +52,7 @@ def test_expired_wait_is_reported_and_the_stream_stays_usable(env):
     assert np.array_equal(out.cpu().numpy(), want)
     t = synth.make_graph("tiny")
     q = synth.make_queries("tiny", t)[0]
-    S = gs.Store(torch.from_numpy(np.ascontiguousarray(t)).cuda())
+    S = gs.Store(torch.from_numpy(np.array(t, copy=True)).cuda())
     assert np.array_equal(S.query(q).to_numpy(), oracle.OracleIndex(t).query(q))
     S.free()
 
@@ -94,7 +94,7 @@ def test_allocation_failure_at_every_call_returns_oom_without_leaks(env):
     t = synth.make_graph("tiny")
     qs = synth.make_queries("tiny", t)
     ix = oracle.OracleIndex(t)
-    d_t = torch.from_numpy(np.ascontiguousarray(t)).cuda()
+    d_t = torch.from_numpy(np.array(t, copy=True)).cuda()
     hook = _FailingHook(gs, torch)
     try:
         # store build: count its allocations, then fail each one in turn

@@ -99,7 +99,7 @@ def test_device_input(gs):
     import torch
 
     t = synth.make_graph("tiny")
-    S = gs.Store(torch.from_numpy(np.ascontiguousarray(t)).cuda())
+    S = gs.Store(torch.from_numpy(np.array(t, copy=True)).cuda())
     assert S.info()["n_unique"] == len(t)
 
 
