@@ -13,7 +13,7 @@ _BINDING_NAMES = {
     "Server", "exclusive_scan_i32", "exclusive_scan_i32_noalloc", "exclusive_scan_i32_noalloc_max",
     "header_functions", "launch_count", "lib", "plan", "profile_enable", "profile_read", "radix_sort_u64", "sort_rows",
     "SORT_CARRY", "SORT_GATHER", "use_torch_allocator", "Dictionary", "Sparql",
-    "merge_tables", "gather_rows",
+    "merge_tables", "gather_rows", "gather_shards",
 }
 
 

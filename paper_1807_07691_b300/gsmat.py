@@ -493,6 +493,41 @@ def gather_rows(rows: np.ndarray, dst: int = 0, group=None):
     return np.concatenate([p.reshape(-1, rows.shape[1]) for p in parts], axis=0)
 
 
+def gather_shards(rows, dst: int = 0, group=None):
+    """Row sharding across ranks with tensor collectives: rank r passes the
+    rows of shard r as a (rows, cols) int32 tensor (e.g. ``Table.to_torch()``
+    of ``query_shard`` in plan order, a device tensor under NCCL, a host one
+    under gloo); rank `dst` returns every rank's rows back to back in rank
+    order -- for plan-order shards, the full plan-order result -- and the
+    other ranks return None.  The shard sizes are exchanged first, then each
+    shard, padded to the largest, is all-gathered on the tensors' device:
+    the rows never pass through host objects."""
+    import torch
+    import torch.distributed as dist
+
+    if rows.dim() != 2:
+        raise ValueError("gather_shards: rows must be a (rows, cols) tensor")
+    rank = dist.get_rank(group)
+    world = dist.get_world_size(group)
+    n, c = rows.shape
+    shape = torch.tensor([n, c], dtype=torch.int64, device=rows.device)
+    shapes = [torch.empty_like(shape) for _ in range(world)]
+    dist.all_gather(shapes, shape, group=group)
+    ns = [int(x[0]) for x in shapes]
+    if len({int(x[1]) for x in shapes}) != 1:
+        raise ValueError("gather_shards: the shards have different column counts")
+    m = max(ns)
+    if m == 0 or c == 0:
+        return rows.new_empty((sum(ns), c)) if rank == dst else None
+    buf = rows.new_zeros((m, c))
+    buf[:n] = rows
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf, group=group)
+    if rank != dst:
+        return None
+    return torch.cat([part[:k] for part, k in zip(parts, ns)], dim=0)
+
+
 # ----------------------------------------------------------------------------
 
 

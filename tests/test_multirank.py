@@ -98,3 +98,50 @@ def test_two_rank_row_shards_gather_gloo():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res[0][1] is True and res[1][1] is None and res[0][2] > 0
+
+
+def _tensor_shard_worker(rank, world, port, q):
+    import sys
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    import synth
+    from paper_1807_07691_b300 import gsmat
+
+    t = synth.make_graph("tiny")
+    full = oracle.OracleIndex(t).query(synth.make_queries("tiny", t)[1])
+    out = []
+    # near-equal shards as the library splits them, then uneven ones with an
+    # empty shard, gathered once on rank 0 and once on the last rank
+    for cuts, dst in (([full.shape[0] * r // world for r in range(world + 1)], 0),
+                      ([0, 0] + [full.shape[0]] * (world - 1), world - 1)):
+        part = torch.from_numpy(np.ascontiguousarray(full[cuts[rank]:cuts[rank + 1]]))
+        got = gsmat.gather_shards(part, dst=dst)
+        out.append(None if got is None else bool(np.array_equal(got.numpy(), full)))
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, out, full.shape[0]))
+
+
+def test_two_rank_tensor_shard_gather_gloo():
+    """gsmat.gather_shards: shard sizes exchanged, padded shards all-gathered
+    as tensors (gloo here; NCCL with device tensors on GPUs)."""
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_tensor_shard_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=180) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] == [True, None] and res[1][1] == [None, True] and res[0][2] > 0
