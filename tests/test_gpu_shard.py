@@ -90,3 +90,57 @@ def test_shard_arguments_and_merge_errors(gs, tiny):
     # shard k keeps rows [2k/5, 2(k+1)/5) of the two: 0, 0, 1, 0, 1 rows
     assert [p.rows for p in parts] == [0, 0, 1, 0, 1]
     assert gs.merge_tables(parts).to_numpy().tolist() == [[1, 2], [2, 3]]
+
+
+def _rank_worker(rank, world, port, q):
+    """One rank: its shard of each tiny query on the device, copied to a host
+    tensor and gathered to rank 0 over gloo (the ranks' kernels never wait
+    on one another; only the host collectives do)."""
+    import os
+    import sys
+
+    import torch
+    import torch.distributed as dist
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    import synth as sy
+    import paper_1807_07691_b300 as g
+
+    t = sy.make_graph("tiny")
+    S = g.Store(t)
+    ok = []
+    for qq in sy.make_queries("tiny", t):
+        part = S.query_shard(qq.patterns, rank, world, n_vars=qq.n_vars, flags=g.PLAN_ORDER).to_torch().cpu()
+        got = g.gather_shards(part, dst=0)
+        if rank == 0:
+            whole = S.query(qq.patterns, qq.n_vars, flags=g.PLAN_ORDER).to_numpy()
+            ok.append(bool(np.array_equal(got.numpy(), whole)))
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, ok))
+
+
+def test_rank_shards_gathered_over_gloo(gs):
+    import socket
+
+    import torch.multiprocessing as mp
+
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] and all(res[0][1]) and res[1][1] == []
